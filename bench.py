@@ -1,0 +1,361 @@
+"""Benchmark of the sparse-lattice D3Q19 TRT stream-collide step on one GB300.
+
+Workload (the paper's fixed-bed-reactor stand-in): a 256^3 bed of radius-12
+non-overlapping spheres placed by random sequential addition (seed 1,
+stopped after 20000 consecutive rejections), periodic in x, bounce-back
+walls elsewhere, body force g = 1e-6 in x, TRT with omega+ = 1 and magic
+3/16, FP64, fluid nodes in plain lexicographic order.  One timed step is
+one even + one odd step of the AA pattern with RIA (two lattice updates of
+every fluid node, the paper's AA-R/AA-RP kernel pair, Sect. 4.1-4.2).
+
+Printed: one JSON line with GFLUP/s (value), the roofline of the dominant
+kernel, per-variant numbers (OS-NT / OS-NT-R / AA / AA-R, FP64 / FP32 /
+FP16 storage), the oracle timed on the host cores (cpu_baseline) and an
+end-to-end figure through host buffers.
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
+same workload instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import geometry  # noqa: E402
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+# FP64 pipe of GB300: 152 SMs x 2 DP lanes/clk x 2.07 GHz (measured 0.60 T DFMA/s burst)
+FP64_PEAK_GINSTR = 152 * 2 * 2.07e9 / 1e9
+# FP64-pipe instructions of one TRT collision with body force in the library's
+# pair form (adds, multiplies and FMAs each take one FP64 issue slot).
+COLL_DP_INSTR = 169
+
+WORKLOAD = dict(name="packed_bed_256_rsa_r12", X=256, Y=256, Z=256, radius=12.0, seed=1, rejections=20000,
+                periodic=(1, 0, 0), g=(1e-6, 0.0, 0.0), omega_plus=1.0, magic=3.0 / 16.0)
+
+
+def loop_balance(variant: str, p: int, r: float) -> float:
+    """Algorithmic bytes per fluid-node update (Sect. 4, "Loop Balance"; Sect. 4.1).
+
+    D_pdf = 2*19*p, D_idx = 72 (18 x 4 B), D_block = 4 B per run.
+    """
+    dpdf = 2 * 19 * p
+    if variant == "osnt":
+        return dpdf + 72
+    if variant == "osnt_r":
+        return dpdf + 76 * r
+    if variant == "aa":
+        return dpdf + 36            # even step dpdf, odd step dpdf + 72
+    if variant == "aa_r":
+        return dpdf + 38 * r        # even step dpdf, odd step dpdf + 76 r
+    if variant == "aa_even":
+        return dpdf
+    if variant == "aa_odd":
+        return dpdf + 72
+    if variant == "aa_odd_r":
+        return dpdf + 76 * r
+    raise ValueError(variant)
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def make_geometry(box=None):
+    w = WORKLOAD
+    n = box or w["X"]
+    solid, _ = geometry.rsa_spheres(n, n, n, w["radius"], w["seed"], periodic=w["periodic"],
+                                    max_consecutive_rejections=w["rejections"])
+    return solid
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"lbm_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9], float(parts[3])))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[3] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+def cpu_oracle_sample(solid, steps_pairs=1, zslab=16):
+    """Time the FP64 oracle (AA even + odd) on a z-slab of the same bed; GFLUP/s."""
+    import torch
+    from oracle import lbm as olbm, tables as otables
+
+    w = WORKLOAD
+    crop = np.ascontiguousarray(solid[:zslab])
+    T = otables.Tables(crop, periodic=w["periodic"], enum="lex", B=1)
+    p = olbm.Params(omega_plus=w["omega_plus"], magic=w["magic"], g=w["g"])
+    A = olbm.from_canonical(olbm.uniform_state(T.N, p), 1, T.adj, p)
+    adj = torch.as_tensor(T.adj.astype(np.int64))
+    t0 = time.perf_counter()
+    for _ in range(steps_pairs):
+        A = olbm.aa_even(A, p)
+        A = olbm.aa_odd(A, adj, p)
+    dt = time.perf_counter() - t0
+    return {"value": 2 * T.N * steps_pairs / dt / 1e9, "unit": "GFLUP/s", "cores": torch.get_num_threads(),
+            "kind": "oracle", "seconds": dt,
+            "sample": f"{steps_pairs} AA even+odd pair(s) of the FP64 oracle on the z < {zslab} slab of the "
+                      f"256^3 bed ({T.N} fluid nodes)"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle on a bounded sample, same metric and unit."""
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    solid = make_geometry()
+    torch.set_num_threads(len(os.sched_getaffinity(0)))
+    for _ in range(args.warmup):
+        cpu_oracle_sample(solid, 1, zslab=32)
+    times, nodes = [], 0
+    for _ in range(args.steps):
+        r = cpu_oracle_sample(solid, 1, zslab=32)
+        times.append(r["seconds"])
+        nodes = r["value"] * r["seconds"] * 1e9 / 2
+    total = sum(times)
+    value = 2 * nodes * args.steps / total / 1e9
+    line = {"impl": "reference", "metric": "sparse D3Q19 TRT AA-R FP64 lattice updates per second",
+            "value": value, "unit": "GFLUP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "sample": "z < 32 slab", "step": "AA even+odd pair"},
+            "cpu_baseline": {"value": value, "unit": "GFLUP/s", "cores": torch.get_num_threads(),
+                             "kind": "oracle", "sample": f"z < 32 slab of the 256^3 bed ({int(nodes)} nodes), "
+                                                         "one AA even+odd pair per step"},
+            "e2e": {"value": value, "unit": "GFLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--box", type=int, default=None, help="smaller cubic bed (profiling only)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    import paper_1410_0412_gb300 as lbm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = WORKLOAD
+    t0 = time.time()
+    solid = make_geometry(args.box)
+    lat = lbm.Lattice(solid, periodic=w["periodic"], enum="lex", B=1)
+    lat.upload(lbm.LBM_TABLES_ADJ | lbm.LBM_TABLES_RIA, device=dev)
+    setup_s = time.time() - t0
+    N, R = lat.N, lat.R
+    r = R / N
+    params = lbm.Params(omega_plus=w["omega_plus"], magic=w["magic"], g=w["g"])
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---- headline: AA-R FP64, one even+odd pair per step ---------------------------------------------
+    solver = lbm.Solver(lat, "f64", params, form="aa", ria=True)
+    solver.init_equilibrium(1.0)
+    for _ in range(args.warmup):
+        solver.step(2)
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with Clocks(local) as clk:
+        start.record(stream)
+        for k in range(K):
+            ev[k][0].record(stream)
+            lbm.lbm_step_aa(lat, "f64", params, solver.pdf, 0, None, True)
+            ev[k][1].record(stream)
+            lbm.lbm_step_aa(lat, "f64", params, solver.pdf, 1, None, True)
+            ev[k][2].record(stream)
+        stop.record(stream)
+        barrier()
+    solver.t += 2 * (args.warmup + K)
+    ms = start.elapsed_time(stop)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t)
+    even_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / K
+    odd_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / K
+    value = world * 2 * N * K / (ms / 1e3) / 1e9
+    # mass check of the timed run (walls + periodic faces conserve mass)
+    _, _, sums = solver.macroscopic(fields=False)
+    mass = float(sums[0])
+
+    hbm, hbm_kind = peaks()
+    p = 8
+    dom_ms, dom_name, dom_bl = (odd_ms, "aa_odd_ria_f64", loop_balance("aa_odd_r", p, r)) if odd_ms >= even_ms \
+        else (even_ms, "aa_even_f64", loop_balance("aa_even", p, r))
+    achieved_gbs = dom_bl * N / (dom_ms / 1e3) / 1e9
+    dp_rate = COLL_DP_INSTR * N / (dom_ms / 1e3) / 1e9
+    roofline = {"kernel": dom_name, "bound": "alu", "achieved": dp_rate, "peak": FP64_PEAK_GINSTR,
+                "unit": "G FP64-instr/s", "frac": dp_rate / FP64_PEAK_GINSTR, "traffic": None,
+                "peak_kind": "FP64 pipe from unit counts: 152 SM x 2 DP lanes/clk x 2.07 GHz",
+                "dp_instr_per_node": COLL_DP_INSTR}
+    roofline_hbm = {"kernel": dom_name, "bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved_gbs / hbm, "peak_kind": hbm_kind, "bytes_per_node": dom_bl,
+                    "kernel_ms": {"even": even_ms, "odd": odd_ms}}
+
+    # ---- end to end through host buffers: H2D state, one pair, D2H state -------------------------------
+    e2e = None
+    if rank == 0 or world > 1:
+        host = torch.empty((19, lat.Npad), dtype=torch.float64, pin_memory=True)
+        host.copy_(solver.pdf)
+        Ke = max(3, K // 2)
+        barrier()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(Ke):
+            solver.pdf.copy_(host, non_blocking=True)
+            lbm.lbm_step_aa(lat, "f64", params, solver.pdf, 0, None, True)
+            lbm.lbm_step_aa(lat, "f64", params, solver.pdf, 1, None, True)
+            host.copy_(solver.pdf, non_blocking=True)
+        s1.record(stream)
+        barrier()
+        ems = s0.elapsed_time(s1)
+        nb = 19 * lat.Npad * 8
+        e2e = {"value": world * 2 * N * Ke / (ems / 1e3) / 1e9, "unit": "GFLUP/s", "h2d_bytes_per_step": nb,
+               "d2h_bytes_per_step": nb, "what": "per step: pinned-host -> device copy of the FP64 state, "
+                                                 "AA even+odd, device -> pinned-host copy of the state"}
+        del host
+
+    # ---- per-variant numbers ------------------------------------------------------------------------
+    variants = {}
+    if not args.no_variants:
+        del solver
+        torch.cuda.empty_cache()
+        Kv = max(4, K // 2)
+        for prec, pb in (("f64", 8), ("f32", 4), ("f16s", 2)):
+            vp = lbm.Params(omega_plus=w["omega_plus"], magic=w["magic"], g=w["g"], shifted=(prec != "f64"))
+            for form, ria in (("osnt", False), ("osnt", True), ("aa", False), ("aa", True)):
+                name = f"{form}{'_r' if ria else ''}"
+                sv = lbm.Solver(lat, prec, vp, form=form, ria=ria)
+                sv.init_equilibrium(1.0)
+                sv.step(4)
+                barrier()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                sv.step(2 * Kv)
+                b.record(stream)
+                barrier()
+                vms = a.elapsed_time(b)
+                g = 2 * N * Kv / (vms / 1e3) / 1e9
+                bl = loop_balance(name, pb, r)
+                variants[f"{name}_{prec}"] = {"GFLUPs": g, "B_l": bl, "GBs_model": g * bl,
+                                              "frac_hbm": g * bl / hbm, "roof_GFLUPs_8TBs": 8000 / bl}
+                del sv
+                torch.cuda.empty_cache()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        try:
+            import torch as _t
+            _t.set_num_threads(len(os.sched_getaffinity(0)))
+            cpu = cpu_oracle_sample(solid, 3, zslab=64)
+            cpu.pop("seconds", None)
+        except Exception as e:  # the baseline must never hide the GPU number
+            cpu = {"error": str(e)}
+
+    line = {
+        "metric": "sparse D3Q19 TRT AA-R FP64 lattice updates per second",
+        "value": value, "unit": "GFLUP/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"] if not args.box else f"packed_bed_{args.box}_rsa_r12",
+                   "box": [solid.shape[2], solid.shape[1], solid.shape[0]], "fluid_nodes": N, "runs": R,
+                   "r": r, "porosity": geometry.porosity(solid), "enumeration": "lex B=1",
+                   "step": "AA even + odd with RIA (2 lattice updates)", "parallelism": "replicas" if world > 1
+                   else "single GPU", "l2": "inputs larger than L2 (state %.2f GB)" % (19 * lat.Npad * 8 / 1e9),
+                   "setup_s": setup_s, "mass_after": mass},
+        "roofline": roofline, "roofline_hbm": roofline_hbm, "variants": variants, "cpu_baseline": cpu,
+        "e2e": e2e, "gpu_launches": 2 * K, "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

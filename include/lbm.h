@@ -1,0 +1,248 @@
+/*
+ * lbm.h -- C ABI of the sparse-lattice D3Q19 TRT stream-collide library.
+ *
+ * The library implements the propagation-plus-collision step of the lattice
+ * Boltzmann method on a sparse lattice with indirect addressing, as studied in
+ * Wittmann, Zeiser, Hager, Wellein, "Modeling and analyzing performance for
+ * highly optimized propagation steps of the lattice Boltzmann method on sparse
+ * lattices": only fluid nodes are stored, in a 1-D vector ordered by an
+ * enumeration function (Sect. 1, Sect. 5.6); an adjacency list gives the 18
+ * neighbours of every node (Sect. 4, "Loop Balance"); reduced indirect
+ * addressing (RIA) replaces it by a run-length table where consecutive nodes
+ * share a shifted access pattern (Sect. 4.1).  Two storage forms are offered:
+ * the two-grid one-step form OS-NT and the single-grid AA pattern (Sect. 4).
+ *
+ * Conventions that hold for every call below:
+ *  - Every function returns an int status (LBM_OK = 0 on success).  Errors
+ *    are never fatal; lbm_last_error() returns a message for the calling
+ *    thread's most recent failure.
+ *  - Device memory is always owned by the caller and passed as a raw device
+ *    pointer.  Host-side tables are owned by the opaque lbm_lattice handle.
+ *  - Device work is enqueued on `stream` (a cudaStream_t passed as void*;
+ *    NULL selects the legacy default stream) and is asynchronous: a call
+ *    returns once the kernels are queued.  Launch errors are reported as
+ *    LBM_ERR_CUDA.
+ *  - D3Q19 directions: 0 = rest; 1..6 = +x,-x,+y,-y,+z,-z; then the face
+ *    diagonals in opposite pairs 7 (1,1,0) 8 (-1,-1,0) 9 (1,-1,0) 10 (-1,1,0)
+ *    11 (1,0,1) 12 (-1,0,-1) 13 (1,0,-1) 14 (-1,0,1) 15 (0,1,1) 16 (0,-1,-1)
+ *    17 (0,1,-1) 18 (0,-1,1).  The opposite of 2k-1 is 2k.
+ *  - PDF arrays are structure-of-arrays: element (i, n) of a grid lives at
+ *    pdf[i * Npad + n], Npad = N rounded up to a multiple of 128.  The element
+ *    type is double (LBM_F64), float (LBM_F32) or a 16-bit IEEE half
+ *    (LBM_F16S).  With params->shifted the stored value is f_i - w_i * rho0
+ *    (LBM_F16S always stores half((f_i - w_i rho0) * f16_scale)).
+ *  - "Canonical" state F[i][n]: the pre-collision PDFs after the last step,
+ *    FP64, unshifted, dense [19][N].
+ *  - Grid layouts: LBM_LAYOUT_OSNT = an OS-NT grid (holds post-collision
+ *    PDFs; the canonical state is one pull gather away); LBM_LAYOUT_AA_EVEN =
+ *    the AA grid after an even number of steps (holds the canonical state);
+ *    LBM_LAYOUT_AA_ODD = the AA grid after an odd number of steps.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------- */
+#define LBM_OK 0
+#define LBM_ERR_ARG 1          /* invalid argument, size, pointer or state        */
+#define LBM_ERR_ALLOC 2        /* host allocation failed                           */
+#define LBM_ERR_CUDA 3         /* a CUDA runtime call or kernel launch failed      */
+#define LBM_ERR_TABLE 4        /* lattice tables violate an invariant             */
+#define LBM_ERR_UNSUPPORTED 5  /* valid request this build does not implement     */
+#define LBM_ERR_NONFINITE 6    /* a reduction met NaN or Inf                       */
+
+/* ---- enumerations ----------------------------------------------------------- */
+#define LBM_ENUM_LEX 0       /* lexicographic order with blocking factor B (Sect. 5.6) */
+#define LBM_ENUM_HILBERT 1   /* Hilbert space-filling curve (Sect. 5.6)                */
+
+#define LBM_F64 0            /* double storage, double collision                     */
+#define LBM_F32 1            /* float storage, float collision                       */
+#define LBM_F16S 2           /* half storage of (f - w rho0) * f16_scale, float math */
+
+#define LBM_LAYOUT_OSNT 0
+#define LBM_LAYOUT_AA_EVEN 1
+#define LBM_LAYOUT_AA_ODD 2
+
+#define LBM_TABLES_ADJ 1     /* full adjacency list, 18 x int32 per node (Sect. 4)   */
+#define LBM_TABLES_RIA 2     /* RIA run table (Sect. 4.1)                            */
+
+#define LBM_MARK_WALL (-1)   /* adjacency marker: halfway bounce-back               */
+#define LBM_MARK_INLET (-2)  /* adjacency marker: pressure inlet face x = -1         */
+#define LBM_MARK_OUTLET (-3) /* adjacency marker: pressure outlet face x = X         */
+
+typedef struct lbm_lattice lbm_lattice;   /* opaque, owned by the library */
+
+/* Boundary conditions of the box faces.  periodic[a] wraps axis a (x, y, z).
+ * A non-periodic face is a halfway bounce-back wall, except the two x faces
+ * when x_pressure is set: then x = -1 is a pressure inlet and x = X an outlet
+ * (anti-bounce-back).  x may not be both periodic and a pressure axis. */
+typedef struct {
+  int periodic[3];
+  int x_pressure;
+} lbm_bc;
+
+/* Physical and storage parameters of a step.
+ *  omega_plus  TRT even relaxation rate lambda+ (0 < omega_plus < 2)
+ *  magic       TRT magic parameter Lambda = (1/l+ - 1/2)(1/l- - 1/2) > 0
+ *  g[3]        body-force density per unit mass (force = rho g)
+ *  rho0        reference density of the shifted storage and of init
+ *  rho_in, rho_out  densities imposed at the pressure inlet / outlet
+ *  shifted     nonzero: store f - w_i rho0 (required for LBM_F16S)
+ *  f16_scale   LBM_F16S scale (e.g. 1024); ignored otherwise */
+typedef struct {
+  double omega_plus;
+  double magic;
+  double g[3];
+  double rho0;
+  double rho_in;
+  double rho_out;
+  int shifted;
+  double f16_scale;
+} lbm_params;
+
+/* Message describing the calling thread's most recent failed call ("" if none).
+ * The pointer stays valid until the next failing call on the same thread. */
+LBM_API const char* lbm_last_error(void);
+
+/* ---- lattice construction (host) -------------------------------------------- */
+
+/* Build the sparse lattice of a voxel geometry: enumerate the fluid voxels,
+ * fill the adjacency list and the RIA run table.
+ * Sect. 1 and Sect. 5.6 (enumeration by LS with blocking factor B or by the
+ * Hilbert curve), Sect. 4 "Loop Balance" (adjacency list, Fig. 2a), Sect. 4.1
+ * (RIA, Fig. 2b).
+ *  solid   host array [Z][Y][X] (x fastest), nonzero = solid; not retained.
+ *  X,Y,Z   box size, each >= 1, X*Y*Z < 2^40; at most 2^31-1 fluid nodes.
+ *  bc      boundary conditions (see lbm_bc).
+ *  enumeration  LBM_ENUM_LEX or LBM_ENUM_HILBERT.
+ *  block_B LS blocking factor (>= 1; 1 = plain lexicographic); ignored for
+ *          Hilbert.
+ *  out     receives the new handle; free it with lbm_free_lattice.
+ * Node order, adjacency entries and runs are defined exactly (bit-exact
+ * tables): LS sorts by (z/B, y/B, x/B, z, y, x); Hilbert by Skilling's index
+ * with bits interleaved x, y, z from the most significant level on a 2^k cube.
+ * Returns LBM_ERR_ARG for bad sizes/pointers, LBM_ERR_ALLOC on host OOM. */
+LBM_API int lbm_build_lattice(const uint8_t* solid, int X, int Y, int Z, const lbm_bc* bc,
+                      int enumeration, int block_B, lbm_lattice** out);
+
+/* Build a lattice from a caller-supplied adjacency list instead of voxels
+ * (Sect. 4, Fig. 2a: the list is the lattice).  adj is host [18][N], entries
+ * a node index in [0, N) or a marker -1/-2/-3; node_xyz (host [N][3], may be
+ * NULL) is kept for export.  The RIA table is derived from adj.  Call
+ * lbm_validate_tables to check the list before use. */
+LBM_API int lbm_lattice_from_adjacency(int64_t N, const int32_t* adj, const int32_t* node_xyz,
+                               lbm_lattice** out);
+
+/* Release a handle (NULL is ignored).  Device buffers are the caller's. */
+LBM_API void lbm_free_lattice(lbm_lattice* lat);
+
+/* Sizes of a lattice.  Any output pointer may be NULL.  run_hist[b], b = 0..32,
+ * counts RIA runs of length in [2^b, 2^(b+1)). */
+LBM_API int lbm_lattice_info(const lbm_lattice* lat, int64_t* N, int64_t* Npad, int64_t* R,
+                     int64_t* run_hist);
+
+/* Copy the host tables out (bit-exact comparison).  Any pointer may be NULL.
+ *  node_xyz [N][3] (x, y, z) of each node in enumeration order
+ *  adj      [18][N] pull source of f_{i}, i = 1..18, node index or marker
+ *  run_start [R+1]  first node of each run, run_start[R] = N
+ *  run_adj  [18][R] adjacency entries of each run's first node */
+LBM_API int lbm_export_tables(const lbm_lattice* lat, int32_t* node_xyz, int32_t* adj,
+                      int32_t* run_start, int32_t* run_adj);
+
+/* Check the host tables: entries in range, adjacency reciprocity
+ * (adj[i][n] = m >= 0  <=>  adj[inv i][m] = n), run table decoding back to the
+ * adjacency list exactly, runs sorted and covering [0, N).  Returns
+ * LBM_ERR_TABLE with a message naming the first violation. */
+LBM_API int lbm_validate_tables(const lbm_lattice* lat);
+
+/* ---- device tables -------------------------------------------------------------- */
+
+/* Bytes of the caller-owned device buffer that holds the tables selected by
+ * `which` (LBM_TABLES_ADJ | LBM_TABLES_RIA). */
+LBM_API int lbm_device_table_bytes(const lbm_lattice* lat, int which, size_t* bytes);
+
+/* Copy the selected tables into dev_tables (device, >= lbm_device_table_bytes,
+ * 256-byte aligned) on `stream` and remember the device addresses in the
+ * handle.  The buffer must outlive every later device call on the handle.
+ * The host source of the copy is the handle itself, so the handle must not be
+ * freed before the copy completes. */
+LBM_API int lbm_lattice_upload(lbm_lattice* lat, int which, void* dev_tables, size_t bytes, void* stream);
+
+/* Bytes of one PDF grid (19 * Npad elements) of a precision. */
+LBM_API int lbm_pdf_bytes(const lbm_lattice* lat, int prec, size_t* bytes);
+
+/* ---- state set-up and read-back ------------------------------------------------ */
+
+/* Fill a grid with the equilibrium state f^eq(rho0, u0) at every node, stored
+ * in `layout` (the state whose canonical form is f^eq).  pdf: device grid. */
+LBM_API int lbm_init_equilibrium(const lbm_lattice* lat, int prec, const lbm_params* params, void* pdf,
+                         int layout, double rho0, const double u0[3], void* stream);
+
+/* Store a canonical FP64 state F (device [19][N]) into a grid of `layout`
+ * (rounded to the storage precision). */
+LBM_API int lbm_load_canonical(const lbm_lattice* lat, int prec, const lbm_params* params, const double* F,
+                       void* pdf, int layout, void* stream);
+
+/* Gather the canonical FP64 state F (device [19][N]) of a grid. */
+LBM_API int lbm_canonical_pdfs(const lbm_lattice* lat, int prec, const lbm_params* params, const void* pdf,
+                       int layout, double* F, void* stream);
+
+/* ---- the stream-collide step --------------------------------------------------- */
+
+/* One OS-NT step (Sect. 4, "Loop Balance"): every node pulls its 19 PDFs from
+ * the neighbours in `src` (indirectly, through the adjacency list or the RIA
+ * runs), collides them with the TRT operator (Sect. 2) with body force g and
+ * optional Brinkman drag s, and stores the result at its own slots in `dst`
+ * with streaming (evict-first) stores.  src, dst: device grids in the
+ * LBM_LAYOUT_OSNT layout, distinct.  s: device float [N] in [0, 1] or NULL.
+ * ria = 0 uses the adjacency list (OS-NT, B_l = 38p + 72 B/FLUP), 1 the RIA
+ * table (OS-NT-R, Sect. 4.1); the matching table must have been uploaded. */
+LBM_API int lbm_step_osnt(const lbm_lattice* lat, int prec, const lbm_params* params, const void* src,
+                  void* dst, const float* s, int ria, void* stream);
+
+/* One AA-pattern step on the single grid `pdf` (Sect. 4, "Loop Balance",
+ * AA pattern).  parity 0 (even step): read the 19 local PDFs, collide, write
+ * them to the opposite local slots (direct addressing only).  parity 1 (odd
+ * step): read the neighbours' opposite slots, collide, write back to the same
+ * slots (indirect).  The grid must be in layout AA_EVEN before an even step
+ * and AA_ODD before an odd one.  ria selects the odd step's addressing as in
+ * lbm_step_osnt (AA-R, Sect. 4.1). */
+LBM_API int lbm_step_aa(const lbm_lattice* lat, int prec, const lbm_params* params, void* pdf, int parity,
+                const float* s, int ria, void* stream);
+
+/* `steps` consecutive AA steps starting with parity start_parity. */
+LBM_API int lbm_run_aa(const lbm_lattice* lat, int prec, const lbm_params* params, void* pdf,
+               int start_parity, int steps, const float* s, int ria, void* stream);
+
+/* ---- macroscopic quantities and reductions ------------------------------------- */
+
+/* Bytes of the device workspace the reductions below need (per-block FP64
+ * partial sums). */
+LBM_API int lbm_reduce_workspace_bytes(const lbm_lattice* lat, size_t* bytes);
+
+/* Density and velocity of every node and FP64 global sums.  The velocity is
+ * the force-corrected u = (j0/rho + g/2)/(1 + s/2).  rho (device double [N]),
+ * u (device double [3][N]) and sums (device double [4]: sum rho, sum rho u_x,
+ * sum rho u_y, sum rho u_z) may each be NULL.  workspace: device, at least
+ * lbm_reduce_workspace_bytes.  Sums are deterministic (fixed reduction order).
+ * No counterpart in the paper beyond the LBM moments of Sect. 2. */
+LBM_API int lbm_macroscopic(const lbm_lattice* lat, int prec, const lbm_params* params, const void* pdf,
+                    int layout, const float* s, double* rho, double* u, double* sums,
+                    void* workspace, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,341 @@
+"""GB300 sparse-lattice D3Q19 TRT stream-collide: Python binding of liblbm.
+
+A thin layer over the C ABI in ``include/lbm.h``: it marshals numpy arrays,
+torch CUDA tensors (device memory and streams only) and parameters into the
+library's calls.  Every step of the method runs in the library: the host
+lattice builder (C++) and the sm_103a CUDA kernels.  Importing this package
+fails if ``liblbm.so`` has not been built; there is no fallback.
+
+Functions named ``lbm_*`` mirror the C entry points one to one; ``Lattice``
+and ``Solver`` bundle them for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib
+from ._lib import (LBM_ENUM_HILBERT, LBM_ENUM_LEX, LBM_F16S, LBM_F32, LBM_F64, LBM_LAYOUT_AA_EVEN,
+                   LBM_LAYOUT_AA_ODD, LBM_LAYOUT_OSNT, LBM_TABLES_ADJ, LBM_TABLES_RIA, LbmError, check)
+
+_lib.load()
+
+PRECISIONS = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S}
+BYTES_PER_PDF = {LBM_F64: 8, LBM_F32: 4, LBM_F16S: 2}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype(prec):
+    torch = _torch()
+    return {LBM_F64: torch.float64, LBM_F32: torch.float32, LBM_F16S: torch.float16}[prec]
+
+
+def _prec(prec) -> int:
+    if isinstance(prec, str):
+        return PRECISIONS[prec]
+    return int(prec)
+
+
+@dataclass
+class Params:
+    """Step parameters (``lbm_params``): TRT rates, body force, densities, storage shift."""
+
+    omega_plus: float = 1.0
+    magic: float = 3.0 / 16.0
+    g: tuple = (0.0, 0.0, 0.0)
+    rho0: float = 1.0
+    rho_in: float = 1.0
+    rho_out: float = 1.0
+    shifted: bool = False
+    f16_scale: float = 1024.0
+
+    def c(self) -> _lib.lbm_params:
+        p = _lib.lbm_params()
+        p.omega_plus = self.omega_plus
+        p.magic = self.magic
+        for a in range(3):
+            p.g[a] = float(self.g[a])
+        p.rho0 = self.rho0
+        p.rho_in = self.rho_in
+        p.rho_out = self.rho_out
+        p.shifted = 1 if self.shifted else 0
+        p.f16_scale = self.f16_scale
+        return p
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _check_grid(lat, prec, t, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != _dtype(prec):
+        raise TypeError(f"{name} has dtype {t.dtype}, precision needs {_dtype(prec)}")
+    if not t.is_contiguous() or t.numel() < 19 * lat.Npad:
+        raise ValueError(f"{name} must be contiguous with at least 19 * Npad elements")
+
+
+def _check_s(lat, s):
+    torch = _torch()
+    if s is None:
+        return None
+    if not s.is_cuda or s.dtype != torch.float32 or not s.is_contiguous() or s.numel() < lat.N:
+        raise TypeError("s must be a contiguous CUDA float32 tensor with N elements")
+    return s
+
+
+class Lattice:
+    """A sparse lattice (``lbm_build_lattice``): enumeration, adjacency and RIA tables."""
+
+    def __init__(self, solid=None, periodic=(0, 0, 0), x_pressure=False, enum="lex", B=1, _handle=None):
+        self._h = ctypes.c_void_p()
+        self._dev = None
+        self.uploaded = 0
+        if _handle is not None:
+            self._h = _handle
+        else:
+            solid = np.ascontiguousarray(solid, dtype=np.uint8)
+            if solid.ndim != 3:
+                raise ValueError("solid must be [Z, Y, X]")
+            Z, Y, X = solid.shape
+            bc = _lib.lbm_bc()
+            for a in range(3):
+                bc.periodic[a] = 1 if periodic[a] else 0
+            bc.x_pressure = 1 if x_pressure else 0
+            e = {"lex": LBM_ENUM_LEX, "hilbert": LBM_ENUM_HILBERT}[enum]
+            check(_lib.load().lbm_build_lattice(solid.ctypes.data_as(ctypes.c_void_p), X, Y, Z,
+                                                ctypes.byref(bc), e, int(B), ctypes.byref(self._h)),
+                  "lbm_build_lattice")
+        self._info()
+
+    @classmethod
+    def from_adjacency(cls, adj, node_xyz=None):
+        adj = np.ascontiguousarray(adj, dtype=np.int32)
+        N = adj.shape[1]
+        h = ctypes.c_void_p()
+        xyz = None
+        if node_xyz is not None:
+            xyz = np.ascontiguousarray(node_xyz, dtype=np.int32)
+        check(_lib.load().lbm_lattice_from_adjacency(
+            N, adj.ctypes.data_as(ctypes.c_void_p),
+            None if xyz is None else xyz.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)),
+            "lbm_lattice_from_adjacency")
+        return cls(_handle=h)
+
+    def _info(self):
+        N, Np, R = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        hist = (ctypes.c_int64 * 33)()
+        check(_lib.load().lbm_lattice_info(self._h, ctypes.byref(N), ctypes.byref(Np), ctypes.byref(R), hist),
+              "lbm_lattice_info")
+        self.N, self.Npad, self.R = N.value, Np.value, R.value
+        self.run_hist = np.array(list(hist), dtype=np.int64)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def tables(self, node_xyz=True):
+        """Host tables as numpy arrays (node_xyz [N,3], adj [18,N], run_start [R+1], run_adj [18,R])."""
+        N, R = self.N, self.R
+        xyz = np.empty((N, 3), np.int32) if node_xyz else None
+        adj = np.empty((18, N), np.int32)
+        rs = np.empty(R + 1, np.int32)
+        ra = np.empty((18, R), np.int32)
+        p = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+        check(_lib.load().lbm_export_tables(self._h, p(xyz), p(adj), p(rs), p(ra)), "lbm_export_tables")
+        return {"node_xyz": xyz, "adj": adj, "run_start": rs, "run_adj": ra}
+
+    def validate(self):
+        check(_lib.load().lbm_validate_tables(self._h), "lbm_validate_tables")
+
+    def device_table_bytes(self, which=LBM_TABLES_ADJ | LBM_TABLES_RIA) -> int:
+        b = ctypes.c_size_t()
+        check(_lib.load().lbm_device_table_bytes(self._h, which, ctypes.byref(b)), "lbm_device_table_bytes")
+        return b.value
+
+    def upload(self, which=LBM_TABLES_ADJ | LBM_TABLES_RIA, device="cuda", stream=None):
+        """Copy the tables to a torch-allocated device buffer owned by this object."""
+        torch = _torch()
+        nbytes = self.device_table_bytes(which)
+        buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+        st = _stream(stream)
+        check(_lib.load().lbm_lattice_upload(self._h, which, _ptr(buf), nbytes, st), "lbm_lattice_upload")
+        torch.cuda.synchronize(buf.device)
+        self._dev = buf
+        self.uploaded = which
+        return self
+
+    def pdf_bytes(self, prec) -> int:
+        b = ctypes.c_size_t()
+        check(_lib.load().lbm_pdf_bytes(self._h, _prec(prec), ctypes.byref(b)), "lbm_pdf_bytes")
+        return b.value
+
+    def new_grid(self, prec, device="cuda"):
+        torch = _torch()
+        return torch.zeros((19, self.Npad), dtype=_dtype(_prec(prec)), device=device)
+
+    def reduce_workspace_bytes(self) -> int:
+        b = ctypes.c_size_t()
+        check(_lib.load().lbm_reduce_workspace_bytes(self._h, ctypes.byref(b)), "lbm_reduce_workspace_bytes")
+        return b.value
+
+    def close(self):
+        if self._h:
+            _lib.load().lbm_free_lattice(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- entry points with the C names ---------------------------------------------------------
+
+def lbm_init_equilibrium(lat, prec, params, pdf, layout, rho0=1.0, u0=(0.0, 0.0, 0.0), stream=None):
+    prec = _prec(prec)
+    _check_grid(lat, prec, pdf, "pdf")
+    u = (ctypes.c_double * 3)(*[float(v) for v in u0])
+    check(_lib.load().lbm_init_equilibrium(lat.handle, prec, ctypes.byref(params.c()), _ptr(pdf), layout,
+                                           float(rho0), u, _stream(stream)), "lbm_init_equilibrium")
+
+
+def lbm_load_canonical(lat, prec, params, F, pdf, layout, stream=None):
+    torch = _torch()
+    prec = _prec(prec)
+    _check_grid(lat, prec, pdf, "pdf")
+    if not F.is_cuda or F.dtype != torch.float64 or tuple(F.shape) != (19, lat.N) or not F.is_contiguous():
+        raise TypeError("F must be a contiguous CUDA float64 tensor [19, N]")
+    check(_lib.load().lbm_load_canonical(lat.handle, prec, ctypes.byref(params.c()), _ptr(F), _ptr(pdf), layout,
+                                         _stream(stream)), "lbm_load_canonical")
+
+
+def lbm_canonical_pdfs(lat, prec, params, pdf, layout, F=None, stream=None):
+    torch = _torch()
+    prec = _prec(prec)
+    _check_grid(lat, prec, pdf, "pdf")
+    if F is None:
+        F = torch.empty((19, lat.N), dtype=torch.float64, device=pdf.device)
+    check(_lib.load().lbm_canonical_pdfs(lat.handle, prec, ctypes.byref(params.c()), _ptr(pdf), layout, _ptr(F),
+                                         _stream(stream)), "lbm_canonical_pdfs")
+    return F
+
+
+def lbm_step_osnt(lat, prec, params, src, dst, s=None, ria=False, stream=None):
+    prec = _prec(prec)
+    _check_grid(lat, prec, src, "src")
+    _check_grid(lat, prec, dst, "dst")
+    check(_lib.load().lbm_step_osnt(lat.handle, prec, ctypes.byref(params.c()), _ptr(src), _ptr(dst),
+                                    _ptr(_check_s(lat, s)), 1 if ria else 0, _stream(stream)), "lbm_step_osnt")
+
+
+def lbm_step_aa(lat, prec, params, pdf, parity, s=None, ria=False, stream=None):
+    prec = _prec(prec)
+    _check_grid(lat, prec, pdf, "pdf")
+    check(_lib.load().lbm_step_aa(lat.handle, prec, ctypes.byref(params.c()), _ptr(pdf), int(parity),
+                                  _ptr(_check_s(lat, s)), 1 if ria else 0, _stream(stream)), "lbm_step_aa")
+
+
+def lbm_run_aa(lat, prec, params, pdf, start_parity, steps, s=None, ria=False, stream=None):
+    prec = _prec(prec)
+    _check_grid(lat, prec, pdf, "pdf")
+    check(_lib.load().lbm_run_aa(lat.handle, prec, ctypes.byref(params.c()), _ptr(pdf), int(start_parity),
+                                 int(steps), _ptr(_check_s(lat, s)), 1 if ria else 0, _stream(stream)),
+          "lbm_run_aa")
+
+
+def lbm_macroscopic(lat, prec, params, pdf, layout, s=None, fields=True, sums=True, workspace=None, stream=None):
+    """(rho [N], u [3, N], sums [4]) as FP64 CUDA tensors (None where not asked for)."""
+    torch = _torch()
+    prec = _prec(prec)
+    _check_grid(lat, prec, pdf, "pdf")
+    dev = pdf.device
+    rho = torch.empty(lat.N, dtype=torch.float64, device=dev) if fields else None
+    u = torch.empty((3, lat.N), dtype=torch.float64, device=dev) if fields else None
+    out = torch.empty(4, dtype=torch.float64, device=dev) if sums else None
+    ws_bytes = lat.reduce_workspace_bytes()
+    if sums and workspace is None:
+        workspace = torch.empty(ws_bytes // 8, dtype=torch.float64, device=dev)
+    check(_lib.load().lbm_macroscopic(lat.handle, prec, ctypes.byref(params.c()), _ptr(pdf), layout,
+                                      _ptr(_check_s(lat, s)), _ptr(rho), _ptr(u), _ptr(out), _ptr(workspace),
+                                      ws_bytes if sums else 0, _stream(stream)), "lbm_macroscopic")
+    return rho, u, out
+
+
+class Solver:
+    """A running simulation in one storage form ("osnt" or "aa") and precision."""
+
+    def __init__(self, lat: Lattice, prec="f64", params: Params | None = None, form="aa", ria=True, s=None,
+                 device="cuda"):
+        self.lat = lat
+        self.prec = _prec(prec)
+        self.params = params or Params()
+        self.form = form
+        self.ria = bool(ria)
+        self.s = s
+        self.t = 0
+        if form == "osnt":
+            self.grids = [lat.new_grid(self.prec, device), lat.new_grid(self.prec, device)]
+        elif form == "aa":
+            self.grids = [lat.new_grid(self.prec, device)]
+        else:
+            raise ValueError(form)
+
+    @property
+    def layout(self):
+        if self.form == "osnt":
+            return LBM_LAYOUT_OSNT
+        return LBM_LAYOUT_AA_EVEN if self.t % 2 == 0 else LBM_LAYOUT_AA_ODD
+
+    @property
+    def pdf(self):
+        return self.grids[0]
+
+    def init_equilibrium(self, rho0=1.0, u0=(0.0, 0.0, 0.0), stream=None):
+        self.t = 0
+        lbm_init_equilibrium(self.lat, self.prec, self.params, self.grids[0], self.layout, rho0, u0, stream)
+
+    def load(self, F, stream=None):
+        self.t = 0
+        lbm_load_canonical(self.lat, self.prec, self.params, F, self.grids[0], self.layout, stream)
+
+    def step(self, n=1, stream=None):
+        if self.form == "osnt":
+            for _ in range(n):
+                lbm_step_osnt(self.lat, self.prec, self.params, self.grids[0], self.grids[1], self.s, self.ria, stream)
+                self.grids.reverse()
+                self.t += 1
+        else:
+            lbm_run_aa(self.lat, self.prec, self.params, self.grids[0], self.t % 2, n, self.s, self.ria, stream)
+            self.t += n
+
+    def canonical(self, stream=None):
+        return lbm_canonical_pdfs(self.lat, self.prec, self.params, self.grids[0], self.layout, stream=stream)
+
+    def macroscopic(self, fields=True, sums=True, stream=None):
+        return lbm_macroscopic(self.lat, self.prec, self.params, self.grids[0], self.layout, self.s, fields, sums,
+                               stream=stream)
+
+
+__all__ = [
+    "Params", "Lattice", "Solver", "LbmError", "lbm_init_equilibrium", "lbm_load_canonical", "lbm_canonical_pdfs",
+    "lbm_step_osnt", "lbm_step_aa", "lbm_run_aa", "lbm_macroscopic", "LBM_F64", "LBM_F32", "LBM_F16S",
+    "LBM_LAYOUT_OSNT", "LBM_LAYOUT_AA_EVEN", "LBM_LAYOUT_AA_ODD", "LBM_TABLES_ADJ", "LBM_TABLES_RIA",
+]

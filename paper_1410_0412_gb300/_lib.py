@@ -1,0 +1,108 @@
+"""ctypes declarations of liblbm's C ABI (include/lbm.h).
+
+Loading fails loudly when the library has not been built: there is no
+fallback implementation of any entry point.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm.so")
+
+LBM_OK = 0
+LBM_ERR_ARG = 1
+LBM_ERR_ALLOC = 2
+LBM_ERR_CUDA = 3
+LBM_ERR_TABLE = 4
+LBM_ERR_UNSUPPORTED = 5
+LBM_ERR_NONFINITE = 6
+
+LBM_ENUM_LEX = 0
+LBM_ENUM_HILBERT = 1
+LBM_F64 = 0
+LBM_F32 = 1
+LBM_F16S = 2
+LBM_LAYOUT_OSNT = 0
+LBM_LAYOUT_AA_EVEN = 1
+LBM_LAYOUT_AA_ODD = 2
+LBM_TABLES_ADJ = 1
+LBM_TABLES_RIA = 2
+
+_ERRNAMES = {1: "LBM_ERR_ARG", 2: "LBM_ERR_ALLOC", 3: "LBM_ERR_CUDA", 4: "LBM_ERR_TABLE",
+             5: "LBM_ERR_UNSUPPORTED", 6: "LBM_ERR_NONFINITE"}
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code: int, fn: str, msg: str):
+        super().__init__(f"{fn} failed with {_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class lbm_bc(ctypes.Structure):
+    _fields_ = [("periodic", ctypes.c_int * 3), ("x_pressure", ctypes.c_int)]
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [("omega_plus", ctypes.c_double), ("magic", ctypes.c_double), ("g", ctypes.c_double * 3),
+                ("rho0", ctypes.c_double), ("rho_in", ctypes.c_double), ("rho_out", ctypes.c_double),
+                ("shifted", ctypes.c_int), ("f16_scale", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+_SZ = ctypes.c_size_t
+_PI64 = ctypes.POINTER(ctypes.c_int64)
+_PSZ = ctypes.POINTER(ctypes.c_size_t)
+_PD = ctypes.POINTER(ctypes.c_double)
+
+# name -> argument types (all return int unless listed in _RESTYPES)
+SIGNATURES = {
+    "lbm_last_error": [],
+    "lbm_build_lattice": [_P, _I, _I, _I, ctypes.POINTER(lbm_bc), _I, _I, ctypes.POINTER(_P)],
+    "lbm_lattice_from_adjacency": [_I64, _P, _P, ctypes.POINTER(_P)],
+    "lbm_free_lattice": [_P],
+    "lbm_lattice_info": [_P, _PI64, _PI64, _PI64, _PI64],
+    "lbm_export_tables": [_P, _P, _P, _P, _P],
+    "lbm_validate_tables": [_P],
+    "lbm_device_table_bytes": [_P, _I, _PSZ],
+    "lbm_lattice_upload": [_P, _I, _P, _SZ, _P],
+    "lbm_pdf_bytes": [_P, _I, _PSZ],
+    "lbm_init_equilibrium": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, ctypes.c_double, _PD, _P],
+    "lbm_load_canonical": [_P, _I, ctypes.POINTER(lbm_params), _P, _P, _I, _P],
+    "lbm_canonical_pdfs": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _P, _P],
+    "lbm_step_osnt": [_P, _I, ctypes.POINTER(lbm_params), _P, _P, _P, _I, _P],
+    "lbm_step_aa": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _P, _I, _P],
+    "lbm_run_aa": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _I, _P, _I, _P],
+    "lbm_reduce_workspace_bytes": [_P, _PSZ],
+    "lbm_macroscopic": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _P, _P, _P, _P, _P, _SZ, _P],
+}
+_RESTYPES = {"lbm_last_error": ctypes.c_char_p, "lbm_free_lattice": None}
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """The loaded library; raises if liblbm.so is missing (never falls back)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"liblbm.so not found at {LIB_PATH}: build it first "
+            "(python -c 'import __graft_entry__ as g; g.build()'). There is no non-CUDA fallback.")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, args in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = _RESTYPES.get(name, ctypes.c_int)
+    _lib = lib
+    return lib
+
+
+def check(rc: int, fn: str):
+    if rc != LBM_OK:
+        msg = load().lbm_last_error()
+        raise LbmError(rc, fn, msg.decode() if msg else "")

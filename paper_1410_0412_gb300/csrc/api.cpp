@@ -1,0 +1,377 @@
+// C ABI of liblbm: argument checking, the opaque lattice handle, device table
+// upload, and dispatch to the CUDA kernels.  See include/lbm.h for the
+// contract of every entry point.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "internal.h"
+
+namespace lbm {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+int set_error(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int make_kparams(const lbm_params* p, int prec, KParams* kp) {
+  if (!p) return set_error(LBM_ERR_ARG, "params is NULL");
+  if (!(p->omega_plus > 0.0 && p->omega_plus < 2.0))
+    return set_error(LBM_ERR_ARG, "omega_plus must lie in (0, 2)");
+  if (!(p->magic > 0.0) || !std::isfinite(p->magic)) return set_error(LBM_ERR_ARG, "magic must be > 0");
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(p->g[a])) return set_error(LBM_ERR_ARG, "g must be finite");
+  if (!std::isfinite(p->rho0) || !std::isfinite(p->rho_in) || !std::isfinite(p->rho_out))
+    return set_error(LBM_ERR_ARG, "densities must be finite");
+  if (prec < LBM_F64 || prec > LBM_F16S) return set_error(LBM_ERR_ARG, "unknown precision");
+  if (prec == LBM_F16S && !p->shifted)
+    return set_error(LBM_ERR_ARG, "LBM_F16S stores shifted values: set params.shifted");
+  if (prec == LBM_F16S && !(p->f16_scale > 0.0 && std::isfinite(p->f16_scale)))
+    return set_error(LBM_ERR_ARG, "f16_scale must be > 0");
+  // Lambda = (1/l+ - 1/2)(1/l- - 1/2)  =>  1/l- = Lambda / (1/l+ - 1/2) + 1/2
+  const double ep = 1.0 / p->omega_plus - 0.5;
+  kp->lp = p->omega_plus;
+  kp->lm = 1.0 / (p->magic / ep + 0.5);
+  for (int a = 0; a < 3; ++a) kp->g[a] = p->g[a];
+  kp->rho_s = p->shifted ? p->rho0 : 0.0;
+  kp->rho_in = p->rho_in;
+  kp->rho_out = p->rho_out;
+  kp->scale = prec == LBM_F16S ? float(p->f16_scale) : 1.0f;
+  kp->inv_scale = prec == LBM_F16S ? float(1.0 / p->f16_scale) : 1.0f;
+  return LBM_OK;
+}
+
+}  // namespace lbm
+
+using namespace lbm;
+
+namespace {
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct TableLayout {
+  size_t adj = 0, run_start = 0, run_adj = 0, tile_run0 = 0, total = 0;
+};
+
+TableLayout table_layout(const lbm_lattice* L, int which) {
+  TableLayout t;
+  size_t off = 0;
+  if (which & LBM_TABLES_ADJ) {
+    t.adj = off;
+    off = align256(off + size_t(18) * L->Npad * 4);
+  }
+  if (which & LBM_TABLES_RIA) {
+    t.run_start = off;
+    off = align256(off + size_t(L->R + 1) * 4);
+    t.run_adj = off;
+    off = align256(off + size_t(18) * L->Rpad * 4);
+    t.tile_run0 = off;
+    off = align256(off + size_t(L->ntiles + 1) * 4);
+  }
+  t.total = off;
+  return t;
+}
+
+int check_lat(const lbm_lattice* L) {
+  if (!L) return set_error(LBM_ERR_ARG, "lattice handle is NULL");
+  return LBM_OK;
+}
+
+int check_tables(const lbm_lattice* L, int ria) {
+  int need = ria ? LBM_TABLES_RIA : LBM_TABLES_ADJ;
+  if (!(L->uploaded & need))
+    return set_error(LBM_ERR_ARG, ria ? "RIA tables not uploaded to the device"
+                                      : "adjacency list not uploaded to the device");
+  return LBM_OK;
+}
+
+// Any uploaded addressing (adjacency preferred) for gathers that need one.
+int any_tables(const lbm_lattice* L, int* ria) {
+  if (L->uploaded & LBM_TABLES_ADJ) {
+    *ria = 0;
+    return LBM_OK;
+  }
+  if (L->uploaded & LBM_TABLES_RIA) {
+    *ria = 1;
+    return LBM_OK;
+  }
+  return set_error(LBM_ERR_ARG, "no device tables uploaded");
+}
+
+int check_layout(int layout) {
+  if (layout < LBM_LAYOUT_OSNT || layout > LBM_LAYOUT_AA_ODD) return set_error(LBM_ERR_ARG, "unknown layout");
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_last_error(void) { return g_last_error.c_str(); }
+
+int lbm_build_lattice(const uint8_t* solid, int X, int Y, int Z, const lbm_bc* bc, int enumeration,
+                      int block_B, lbm_lattice** out) {
+  if (!out) return set_error(LBM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!solid || !bc) return set_error(LBM_ERR_ARG, "solid or bc is NULL");
+  if (X < 1 || Y < 1 || Z < 1) return set_error(LBM_ERR_ARG, "box dimensions must be >= 1");
+  if (int64_t(X) * Y * Z >= (int64_t(1) << 40)) return set_error(LBM_ERR_ARG, "box too large");
+  if (enumeration != LBM_ENUM_LEX && enumeration != LBM_ENUM_HILBERT)
+    return set_error(LBM_ERR_ARG, "unknown enumeration");
+  if (enumeration == LBM_ENUM_LEX && block_B < 1) return set_error(LBM_ERR_ARG, "block_B must be >= 1");
+  if (bc->x_pressure && bc->periodic[0]) return set_error(LBM_ERR_ARG, "x cannot be periodic and a pressure axis");
+  lbm_lattice* L = new (std::nothrow) lbm_lattice();
+  if (!L) return set_error(LBM_ERR_ALLOC, "out of host memory");
+  L->X = X;
+  L->Y = Y;
+  L->Z = Z;
+  L->bc = *bc;
+  for (int a = 0; a < 3; ++a) L->bc.periodic[a] = bc->periodic[a] ? 1 : 0;
+  L->bc.x_pressure = bc->x_pressure ? 1 : 0;
+  L->enumeration = enumeration;
+  L->block_B = block_B;
+  int rc;
+  try {
+    rc = build_tables(L, solid);
+  } catch (const std::bad_alloc&) {
+    rc = set_error(LBM_ERR_ALLOC, "out of host memory while building tables");
+  }
+  if (rc) {
+    delete L;
+    return rc;
+  }
+  *out = L;
+  return LBM_OK;
+}
+
+int lbm_lattice_from_adjacency(int64_t N, const int32_t* adj, const int32_t* node_xyz, lbm_lattice** out) {
+  if (!out) return set_error(LBM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (N < 0 || N > INT32_MAX) return set_error(LBM_ERR_ARG, "N out of range");
+  if (N > 0 && !adj) return set_error(LBM_ERR_ARG, "adj is NULL");
+  lbm_lattice* L = new (std::nothrow) lbm_lattice();
+  if (!L) return set_error(LBM_ERR_ALLOC, "out of host memory");
+  int rc = LBM_OK;
+  try {
+    L->N = N;
+    L->Npad = round_up(std::max<int64_t>(N, 1), kPad);
+    L->adj.assign(18 * L->Npad, LBM_MARK_WALL);
+    for (int i = 0; i < 18; ++i) std::memcpy(&L->adj[i * L->Npad], adj + i * N, size_t(N) * 4);
+    if (node_xyz) L->node_xyz.assign(node_xyz, node_xyz + 3 * N);
+    rc = derive_ria(L);
+  } catch (const std::bad_alloc&) {
+    rc = set_error(LBM_ERR_ALLOC, "out of host memory");
+  }
+  if (rc) {
+    delete L;
+    return rc;
+  }
+  *out = L;
+  return LBM_OK;
+}
+
+void lbm_free_lattice(lbm_lattice* lat) { delete lat; }
+
+int lbm_lattice_info(const lbm_lattice* L, int64_t* N, int64_t* Npad, int64_t* R, int64_t* run_hist) {
+  if (int rc = check_lat(L)) return rc;
+  if (N) *N = L->N;
+  if (Npad) *Npad = L->Npad;
+  if (R) *R = L->R;
+  if (run_hist) std::memcpy(run_hist, L->hist, sizeof(L->hist));
+  return LBM_OK;
+}
+
+int lbm_export_tables(const lbm_lattice* L, int32_t* node_xyz, int32_t* adj, int32_t* run_start,
+                      int32_t* run_adj) {
+  if (int rc = check_lat(L)) return rc;
+  if (node_xyz) {
+    if (int64_t(L->node_xyz.size()) != 3 * L->N)
+      return set_error(LBM_ERR_ARG, "lattice has no node coordinates");
+    std::memcpy(node_xyz, L->node_xyz.data(), size_t(3 * L->N) * 4);
+  }
+  if (adj)
+    for (int i = 0; i < 18; ++i) std::memcpy(adj + i * L->N, &L->adj[i * L->Npad], size_t(L->N) * 4);
+  if (run_start) std::memcpy(run_start, L->run_start.data(), size_t(L->R + 1) * 4);
+  if (run_adj)
+    for (int i = 0; i < 18; ++i) std::memcpy(run_adj + i * L->R, &L->run_adj[i * L->Rpad], size_t(L->R) * 4);
+  return LBM_OK;
+}
+
+int lbm_validate_tables(const lbm_lattice* L) {
+  if (int rc = check_lat(L)) return rc;
+  return validate(L);
+}
+
+int lbm_device_table_bytes(const lbm_lattice* L, int which, size_t* bytes) {
+  if (int rc = check_lat(L)) return rc;
+  if (!bytes) return set_error(LBM_ERR_ARG, "bytes is NULL");
+  if (which <= 0 || which > (LBM_TABLES_ADJ | LBM_TABLES_RIA)) return set_error(LBM_ERR_ARG, "bad table selection");
+  *bytes = table_layout(L, which).total;
+  return LBM_OK;
+}
+
+int lbm_lattice_upload(lbm_lattice* L, int which, void* dev, size_t bytes, void* stream) {
+  if (int rc = check_lat(L)) return rc;
+  if (which <= 0 || which > (LBM_TABLES_ADJ | LBM_TABLES_RIA)) return set_error(LBM_ERR_ARG, "bad table selection");
+  TableLayout t = table_layout(L, which);
+  if (!dev) return set_error(LBM_ERR_ARG, "device table buffer is NULL");
+  if (reinterpret_cast<uintptr_t>(dev) % 256) return set_error(LBM_ERR_ARG, "device table buffer not 256-byte aligned");
+  if (bytes < t.total) return set_error(LBM_ERR_ARG, "device table buffer too small");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(dev);
+  cudaError_t e = cudaSuccess;
+  L->dev = DevTables{};
+  L->uploaded = 0;
+  if (which & LBM_TABLES_ADJ) {
+    e = cudaMemcpyAsync(base + t.adj, L->adj.data(), L->adj.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return set_error(LBM_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+    L->dev.adj = reinterpret_cast<const int32_t*>(base + t.adj);
+  }
+  if (which & LBM_TABLES_RIA) {
+    e = cudaMemcpyAsync(base + t.run_start, L->run_start.data(), L->run_start.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(base + t.run_adj, L->run_adj.data(), L->run_adj.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(base + t.tile_run0, L->tile_run0.data(), L->tile_run0.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return set_error(LBM_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+    L->dev.run_start = reinterpret_cast<const int32_t*>(base + t.run_start);
+    L->dev.run_adj = reinterpret_cast<const int32_t*>(base + t.run_adj);
+    L->dev.tile_run0 = reinterpret_cast<const int32_t*>(base + t.tile_run0);
+  }
+  L->dev.Npad = L->Npad;
+  L->dev.Rpad = L->Rpad;
+  L->dev.R = L->R;
+  L->dev.ntiles = L->ntiles;
+  L->uploaded = which;
+  return LBM_OK;
+}
+
+int lbm_pdf_bytes(const lbm_lattice* L, int prec, size_t* bytes) {
+  if (int rc = check_lat(L)) return rc;
+  if (!bytes) return set_error(LBM_ERR_ARG, "bytes is NULL");
+  size_t el = prec == LBM_F64 ? 8 : prec == LBM_F32 ? 4 : prec == LBM_F16S ? 2 : 0;
+  if (!el) return set_error(LBM_ERR_ARG, "unknown precision");
+  *bytes = size_t(19) * L->Npad * el;
+  return LBM_OK;
+}
+
+int lbm_init_equilibrium(const lbm_lattice* L, int prec, const lbm_params* params, void* pdf, int layout,
+                         double rho0, const double u0[3], void* stream) {
+  if (int rc = check_lat(L)) return rc;
+  KParams kp;
+  if (int rc = make_kparams(params, prec, &kp)) return rc;
+  if (int rc = check_layout(layout)) return rc;
+  if (!pdf || !u0) return set_error(LBM_ERR_ARG, "pdf or u0 is NULL");
+  if (!(rho0 > 0.0) || !std::isfinite(rho0)) return set_error(LBM_ERR_ARG, "rho0 must be > 0");
+  if (layout != LBM_LAYOUT_AA_EVEN && L->N > 0) {
+    int ria;
+    if (int rc = any_tables(L, &ria)) return rc;
+  }
+  return LBM_DISPATCH(prec, launch_init_eq_t, L, kp, pdf, layout, rho0, u0, stream);
+}
+
+int lbm_load_canonical(const lbm_lattice* L, int prec, const lbm_params* params, const double* F, void* pdf,
+                       int layout, void* stream) {
+  if (int rc = check_lat(L)) return rc;
+  KParams kp;
+  if (int rc = make_kparams(params, prec, &kp)) return rc;
+  if (int rc = check_layout(layout)) return rc;
+  if (!pdf || (!F && L->N > 0)) return set_error(LBM_ERR_ARG, "pdf or F is NULL");
+  if (layout != LBM_LAYOUT_AA_EVEN && L->N > 0) {
+    int ria;
+    if (int rc = any_tables(L, &ria)) return rc;
+  }
+  return LBM_DISPATCH(prec, launch_load_canonical_t, L, kp, F, pdf, layout, stream);
+}
+
+int lbm_canonical_pdfs(const lbm_lattice* L, int prec, const lbm_params* params, const void* pdf, int layout,
+                       double* F, void* stream) {
+  if (int rc = check_lat(L)) return rc;
+  KParams kp;
+  if (int rc = make_kparams(params, prec, &kp)) return rc;
+  if (int rc = check_layout(layout)) return rc;
+  if (!pdf || (!F && L->N > 0)) return set_error(LBM_ERR_ARG, "pdf or F is NULL");
+  if (layout != LBM_LAYOUT_AA_EVEN && L->N > 0) {
+    int ria;
+    if (int rc = any_tables(L, &ria)) return rc;
+  }
+  return LBM_DISPATCH(prec, launch_canonical_t, L, kp, pdf, layout, F, stream);
+}
+
+int lbm_step_osnt(const lbm_lattice* L, int prec, const lbm_params* params, const void* src, void* dst,
+                  const float* s, int ria, void* stream) {
+  if (int rc = check_lat(L)) return rc;
+  KParams kp;
+  if (int rc = make_kparams(params, prec, &kp)) return rc;
+  if (!src || !dst) return set_error(LBM_ERR_ARG, "src or dst is NULL");
+  if (src == dst) return set_error(LBM_ERR_ARG, "OS-NT needs two distinct grids");
+  if (L->N == 0) return LBM_OK;
+  if (int rc = check_tables(L, ria)) return rc;
+  return LBM_DISPATCH(prec, launch_osnt_t, L, kp, src, dst, s, ria ? 1 : 0, stream);
+}
+
+int lbm_step_aa(const lbm_lattice* L, int prec, const lbm_params* params, void* pdf, int parity, const float* s,
+                int ria, void* stream) {
+  if (int rc = check_lat(L)) return rc;
+  KParams kp;
+  if (int rc = make_kparams(params, prec, &kp)) return rc;
+  if (!pdf) return set_error(LBM_ERR_ARG, "pdf is NULL");
+  if (parity != 0 && parity != 1) return set_error(LBM_ERR_ARG, "parity must be 0 or 1");
+  if (L->N == 0) return LBM_OK;
+  if (parity == 1)
+    if (int rc = check_tables(L, ria)) return rc;
+  return LBM_DISPATCH(prec, launch_aa_t, L, kp, pdf, parity, s, ria ? 1 : 0, stream);
+}
+
+int lbm_run_aa(const lbm_lattice* L, int prec, const lbm_params* params, void* pdf, int start_parity, int steps,
+               const float* s, int ria, void* stream) {
+  if (int rc = check_lat(L)) return rc;
+  KParams kp;
+  if (int rc = make_kparams(params, prec, &kp)) return rc;
+  if (!pdf) return set_error(LBM_ERR_ARG, "pdf is NULL");
+  if (start_parity != 0 && start_parity != 1) return set_error(LBM_ERR_ARG, "parity must be 0 or 1");
+  if (steps < 0) return set_error(LBM_ERR_ARG, "steps must be >= 0");
+  if (L->N == 0 || steps == 0) return LBM_OK;
+  if (steps > 1 || start_parity == 1)
+    if (int rc = check_tables(L, ria)) return rc;
+  for (int t = 0; t < steps; ++t)
+    if (int rc = LBM_DISPATCH(prec, launch_aa_t, L, kp, pdf, (start_parity + t) & 1, s, ria ? 1 : 0, stream))
+      return rc;
+  return LBM_OK;
+}
+
+int lbm_reduce_workspace_bytes(const lbm_lattice* L, size_t* bytes) {
+  if (int rc = check_lat(L)) return rc;
+  if (!bytes) return set_error(LBM_ERR_ARG, "bytes is NULL");
+  *bytes = size_t(reduce_parts(L)) * 4 * sizeof(double);
+  return LBM_OK;
+}
+
+int lbm_macroscopic(const lbm_lattice* L, int prec, const lbm_params* params, const void* pdf, int layout,
+                    const float* s, double* rho, double* u, double* sums, void* workspace, size_t ws_bytes,
+                    void* stream) {
+  if (int rc = check_lat(L)) return rc;
+  KParams kp;
+  if (int rc = make_kparams(params, prec, &kp)) return rc;
+  if (int rc = check_layout(layout)) return rc;
+  if (!pdf) return set_error(LBM_ERR_ARG, "pdf is NULL");
+  const int64_t parts = reduce_parts(L);
+  if (sums && (!workspace || ws_bytes < size_t(parts) * 4 * sizeof(double)))
+    return set_error(LBM_ERR_ARG, "reduction workspace missing or too small");
+  if (reinterpret_cast<uintptr_t>(workspace) % 8) return set_error(LBM_ERR_ARG, "workspace not 8-byte aligned");
+  if (layout != LBM_LAYOUT_AA_EVEN && L->N > 0) {
+    int ria;
+    if (int rc = any_tables(L, &ria)) return rc;
+  }
+  return LBM_DISPATCH(prec, launch_macroscopic_t, L, kp, pdf, layout, s, rho, u, sums,
+                      static_cast<double*>(workspace), parts, stream);
+}
+
+}  // extern "C"

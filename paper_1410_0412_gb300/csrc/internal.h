@@ -1,0 +1,107 @@
+// Internal declarations shared by the host lattice builder, the C ABI layer
+// and the CUDA kernels of liblbm.  Not part of the public interface.
+#pragma once
+
+#include <algorithm>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+// D3Q19 velocity set in the library's direction order (see lbm.h).
+constexpr int kQ = 19;
+constexpr int kCX[kQ] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+constexpr int kCY[kQ] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+constexpr int kCZ[kQ] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+constexpr int kInv[kQ] = {0, 2, 1, 4, 3, 6, 5, 8, 7, 10, 9, 12, 11, 14, 13, 16, 15, 18, 17};
+
+// Node-count padding of every SoA direction array; 128 nodes keep each
+// direction of an FP16 grid 256-byte aligned.
+constexpr int64_t kPad = 128;
+// Node tile of the RIA run index: tile_run0[t] is the run holding node t*kTile.
+constexpr int kTile = 128;
+
+inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// Device addresses of the uploaded tables (all inside one caller buffer).
+struct DevTables {
+  const int32_t* adj = nullptr;        // [18][Npad]
+  const int32_t* run_start = nullptr;  // [R+1]
+  const int32_t* run_adj = nullptr;    // [18][Rpad]
+  const int32_t* tile_run0 = nullptr;  // [ntiles+1]
+  int64_t Npad = 0, Rpad = 0, R = 0, ntiles = 0;
+};
+
+}  // namespace lbm
+
+struct lbm_lattice {
+  int X = 0, Y = 0, Z = 0;
+  lbm_bc bc{};
+  int enumeration = 0, block_B = 1;
+  int64_t N = 0, Npad = 0, R = 0, Rpad = 0, ntiles = 0;
+  std::vector<int32_t> node_xyz;   // [N][3]
+  std::vector<int32_t> adj;        // [18][Npad], padding = -1
+  std::vector<int32_t> run_start;  // [R+1]
+  std::vector<int32_t> run_adj;    // [18][Rpad], padding = -1
+  std::vector<int32_t> tile_run0;  // [ntiles+1]
+  int64_t hist[33] = {0};
+  int uploaded = 0;                // LBM_TABLES_* bits present on the device
+  lbm::DevTables dev;
+};
+
+namespace lbm {
+
+// Error reporting (thread-local message, see lbm_last_error).
+int set_error(int code, const std::string& msg);
+
+// Host table construction (lattice.cpp).
+int build_tables(lbm_lattice* L, const uint8_t* solid);
+int derive_ria(lbm_lattice* L);
+int validate(const lbm_lattice* L);
+
+// Kernel-side parameter block, computed on the host from lbm_params.
+struct KParams {
+  double lp, lm;        // TRT rates lambda+, lambda-
+  double g[3];          // body force per unit mass
+  double rho_s;         // density of the storage shift (0 when unshifted)
+  double rho_in, rho_out;
+  float scale, inv_scale;  // FP16 storage scale and its inverse
+};
+
+int make_kparams(const lbm_params* p, int prec, KParams* kp);
+
+// Kernel launchers, one explicit instantiation per storage precision in
+// kernels_<prec>.cu.  All return a LBM_* status.
+template <int PREC>
+int launch_osnt_t(const lbm_lattice* L, const KParams& kp, const void* src, void* dst, const float* s, int ria,
+                  void* stream);
+template <int PREC>
+int launch_aa_t(const lbm_lattice* L, const KParams& kp, void* pdf, int parity, const float* s, int ria,
+                void* stream);
+template <int PREC>
+int launch_init_eq_t(const lbm_lattice* L, const KParams& kp, void* pdf, int layout, double rho0, const double* u0,
+                     void* stream);
+template <int PREC>
+int launch_load_canonical_t(const lbm_lattice* L, const KParams& kp, const double* F, void* pdf, int layout,
+                            void* stream);
+template <int PREC>
+int launch_canonical_t(const lbm_lattice* L, const KParams& kp, const void* pdf, int layout, double* F,
+                       void* stream);
+template <int PREC>
+int launch_macroscopic_t(const lbm_lattice* L, const KParams& kp, const void* pdf, int layout, const float* s,
+                         double* rho, double* u, double* sums, double* partials, int64_t nparts, void* stream);
+
+// Precision dispatch: call F<LBM_F64 | LBM_F32 | LBM_F16S>.
+#define LBM_DISPATCH(prec, fn, ...)                                   \
+  ((prec) == LBM_F64 ? fn<LBM_F64>(__VA_ARGS__)                       \
+   : (prec) == LBM_F32 ? fn<LBM_F32>(__VA_ARGS__)                     \
+                       : fn<LBM_F16S>(__VA_ARGS__))
+
+// Number of per-CTA partial sums of the reductions (one per 128-node CTA).
+inline int64_t reduce_parts(const lbm_lattice* L) { return std::max<int64_t>(1, (L->N + 127) / 128); }
+
+}  // namespace lbm

@@ -1,0 +1,746 @@
+// Device code of liblbm: storage traits, neighbour addressing (adjacency
+// list or RIA runs), the TRT collision, and the stream-collide kernels of the
+// OS-NT and AA forms.  Each kernels_<prec>.cu instantiates these templates for
+// one storage precision; nothing here is shared with the CPU oracle.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace lbm {
+namespace dev {
+
+// ---- D3Q19 (device copies; the direction order of lbm.h) ---------------------------
+__host__ __device__ constexpr int cx(int i) {
+  return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1 : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int cy(int i) {
+  return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1 : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int cz(int i) {
+  return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1 : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int inv(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+constexpr bool same_as_host_table(int i) {
+  return i == kQ || (cx(i) == kCX[i] && cy(i) == kCY[i] && cz(i) == kCZ[i] && inv(i) == kInv[i] && same_as_host_table(i + 1));
+}
+static_assert(same_as_host_table(0), "device and host direction tables differ");
+// weight class: 0 rest, 1 axis (1/18), 2 face diagonal (1/36)
+__host__ __device__ constexpr int wclass(int i) { return i == 0 ? 0 : (i <= 6 ? 1 : 2); }
+__host__ __device__ constexpr double wgt(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+
+constexpr int kBlock = 128;  // nodes per CTA of the step kernels (one node per thread)
+static_assert(kBlock % kTile == 0, "CTA must cover whole RIA tiles");
+
+// ---- storage traits -----------------------------------------------------------------
+// Value stored for PDF i: f_i - w_i rho_s (rho_s = 0 when unshifted), in the
+// storage type; LBM_F16S additionally multiplies by the scale.
+template <int PREC> struct St;
+
+template <> struct St<LBM_F64> {
+  using T = double;
+  using R = double;
+  static __device__ __forceinline__ R ld(const T* p, float) { return __ldg(p); }
+  static __device__ __forceinline__ void st(T* p, R v, float) { *p = v; }
+  static __device__ __forceinline__ void st_stream(T* p, R v, float) { __stcs(p, v); }
+};
+
+template <> struct St<LBM_F32> {
+  using T = float;
+  using R = float;
+  static __device__ __forceinline__ R ld(const T* p, float) { return __ldg(p); }
+  static __device__ __forceinline__ void st(T* p, R v, float) { *p = v; }
+  static __device__ __forceinline__ void st_stream(T* p, R v, float) { __stcs(p, v); }
+};
+
+template <> struct St<LBM_F16S> {
+  using T = __half;
+  using R = float;
+  static __device__ __forceinline__ R ld(const T* p, float inv_scale) {
+    return __half2float(__ldg(p)) * inv_scale;
+  }
+  static __device__ __forceinline__ void st(T* p, R v, float scale) { *p = __float2half_rn(v * scale); }
+  static __device__ __forceinline__ void st_stream(T* p, R v, float scale) {
+    __stcs(p, __float2half_rn(v * scale));
+  }
+};
+
+// ---- neighbour addressing --------------------------------------------------------------
+// m[i-1] for i = 1..18: the adjacency entry of node n (node index or marker).
+// Plain form: one coalesced int32 load per direction (D_idx = 72 B/node).
+__device__ __forceinline__ void nbr_adj(const DevTables& t, int n, int (&m)[18]) {
+#pragma unroll
+  for (int i = 0; i < 18; ++i) m[i] = __ldg(t.adj + size_t(i) * t.Npad + n);
+}
+
+// RIA form (Sect. 4.1): the CTA loads the starts of the runs overlapping its
+// node range into shared memory; each thread finds its run by binary search
+// and rebuilds its entries from the run head's (a + offset for fluid sources,
+// the marker itself otherwise).  Threads of one run read the same head entry,
+// so only runs cost index bytes.  Must be called by all threads of the CTA.
+struct RiaCursor {
+  int r;     // run of this thread's node
+  int off;   // node - first node of the run
+};
+
+__device__ __forceinline__ RiaCursor ria_locate(const DevTables& t, int n0, int n, int N, int* s_rs) {
+  const int t0 = n0 / kTile;
+  const int t1 = min(int64_t((n0 + kBlock) / kTile), t.ntiles);
+  const int r0 = __ldg(t.tile_run0 + t0);
+  const int r1 = __ldg(t.tile_run0 + t1);
+  const int cnt = r1 - r0 + 1;  // <= kBlock + 1 runs overlap [n0, n0 + kBlock]
+  for (int j = threadIdx.x; j < cnt; j += kBlock) s_rs[j] = __ldg(t.run_start + r0 + j);
+  __syncthreads();
+  RiaCursor c{r0, 0};
+  if (n < N) {
+    int lo = 0, hi = cnt - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_rs[mid] <= n) lo = mid; else hi = mid - 1;
+    }
+    c.r = r0 + lo;
+    c.off = n - s_rs[lo];
+  }
+  return c;
+}
+
+__device__ __forceinline__ void nbr_ria(const DevTables& t, RiaCursor c, int (&m)[18]) {
+#pragma unroll
+  for (int i = 0; i < 18; ++i) {
+    const int a = __ldg(t.run_adj + size_t(i) * t.Rpad + c.r);
+    m[i] = a >= 0 ? a + c.off : a;
+  }
+}
+
+// ---- TRT collision (Sect. 2) in pair form ------------------------------------------------
+// Operates on deviations d_i = f_i - w_i rho_s and returns post-collision
+// deviations.  With l+ / l- the TRT rates, a+- = 1 - l+-/2, the even and odd
+// parts of each opposite pair (a, b = inv a) relax separately:
+//   p_a = (1-l+)/2 (d_a+d_b) + (1-l-)/2 (d_a-d_b) + e + o
+//   p_b = (1-l+)/2 (d_a+d_b) - (1-l-)/2 (d_a-d_b) + e - o
+// e = l+ (feq+ - w rho_s) + a+ S+,  o = l- feq- + a- S-  (Guo forcing),
+// which is f* = f - l+(f+ - feq+) - l-(f- - feq-) + a+ S+ + a- S- rewritten.
+template <class R> struct CollConst {
+  R lp;       // lambda+
+  R qp, qm;   // (1 - l+)/2, (1 - l-)/2
+  R hg[3];    // g / 2
+  R g[3];
+  R k0a, k0b; // l+/18, 3 a+/18 (K0 of the axis class: k0a*base - k0b*uF)
+  R k1;       // 4.5 l+ / 18 = l+/4 (K1 of the axis class, times rho)
+  R k2;       // 3 l- / 18 = l-/6   (K2 of the axis class, times rho)
+  R fs;       // 9 a+ / 18 = a+/2   (axis-class scale of F in S+)
+  R fo;       // 3 a- / 18 = a-/6   (axis-class scale of F in S-)
+  R rho_s;
+  R abb_in[2], abb_out[2];  // 2 w (rho_bc - rho_s) for w = 1/18 and 1/36
+};
+
+template <class R> __host__ __device__ inline CollConst<R> make_coll(const KParams& kp) {
+  CollConst<R> c;
+  const double ap = 1.0 - kp.lp / 2, am = 1.0 - kp.lm / 2;
+  c.lp = R(kp.lp);
+  c.qp = R((1.0 - kp.lp) / 2);
+  c.qm = R((1.0 - kp.lm) / 2);
+  for (int a = 0; a < 3; ++a) {
+    c.g[a] = R(kp.g[a]);
+    c.hg[a] = R(kp.g[a] / 2);
+  }
+  c.k0a = R(kp.lp / 18.0);
+  c.k0b = R(3.0 * ap / 18.0);
+  c.k1 = R(kp.lp / 4.0);
+  c.k2 = R(kp.lm / 6.0);
+  c.fs = R(ap / 2.0);
+  c.fo = R(am / 6.0);
+  c.rho_s = R(kp.rho_s);
+  for (int k = 0; k < 2; ++k) {
+    const double w = k == 0 ? 1.0 / 18.0 : 1.0 / 36.0;
+    c.abb_in[k] = R(2.0 * w * (kp.rho_in - kp.rho_s));
+    c.abb_out[k] = R(2.0 * w * (kp.rho_out - kp.rho_s));
+  }
+  return c;
+}
+
+// c . v for a lattice direction with components in {-1, 0, 1}; folds at compile time.
+template <class R, int X, int Y, int Z> __device__ __forceinline__ R cdot(R vx, R vy, R vz) {
+  R acc = R(0);
+  bool first = true;
+  if (X != 0) { acc = X > 0 ? vx : -vx; first = false; }
+  if (Y != 0) { acc = first ? (Y > 0 ? vy : -vy) : (Y > 0 ? acc + vy : acc - vy); first = false; }
+  if (Z != 0) { acc = first ? (Z > 0 ? vz : -vz) : (Z > 0 ? acc + vz : acc - vz); }
+  return acc;
+}
+
+template <class R, bool FORCE, int K>
+__device__ __forceinline__ void coll_pair(R (&d)[kQ], const R sa, const R da, const R ux, const R uy, const R uz,
+                                          const R K0, const R K1, const R K2, const R Fsx, const R Fsy,
+                                          const R Fsz, const R Fox, const R Foy, const R Foz, const R qp,
+                                          const R qm) {
+  constexpr int a = 2 * K - 1, b = 2 * K;
+  const R cu = cdot<R, cx(a), cy(a), cz(a)>(ux, uy, uz);
+  R t, o;
+  if (FORCE) {
+    const R cFs = cdot<R, cx(a), cy(a), cz(a)>(Fsx, Fsy, Fsz);
+    const R cFo = cdot<R, cx(a), cy(a), cz(a)>(Fox, Foy, Foz);
+    t = fma(K1, cu, cFs);
+    o = fma(K2, cu, cFo);
+  } else {
+    t = K1 * cu;
+    o = K2 * cu;
+  }
+  const R e = fma(cu, t, K0);
+  const R Ep = fma(qp, sa, e);
+  const R Op = fma(qm, da, o);
+  d[a] = Ep + Op;
+  d[b] = Ep - Op;
+}
+
+// s: Brinkman solid fraction of the node (DRAG only).
+template <class R, bool FORCE, bool DRAG>
+__device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const R s) {
+  R sa[10], da[10];
+#pragma unroll
+  for (int k = 1; k <= 9; ++k) {
+    sa[k] = d[2 * k - 1] + d[2 * k];
+    da[k] = d[2 * k - 1] - d[2 * k];
+  }
+  R drho = d[0];
+#pragma unroll
+  for (int k = 1; k <= 9; ++k) drho += sa[k];
+  // first moment: pairs k = 1..9 have directions (1,0,0) (0,1,0) (0,0,1) (1,1,0)
+  // (1,-1,0) (1,0,1) (1,0,-1) (0,1,1) (0,1,-1)
+  const R jx = da[1] + da[4] + da[5] + da[6] + da[7];
+  const R jy = da[2] + da[4] - da[5] + da[8] + da[9];
+  const R jz = da[3] + da[6] - da[7] + da[8] - da[9];
+  const R rho = c.rho_s + drho;
+  const R irho = R(1) / rho;
+  R ux = fma(jx, irho, c.hg[0]);
+  R uy = fma(jy, irho, c.hg[1]);
+  R uz = fma(jz, irho, c.hg[2]);
+  R Fx = R(0), Fy = R(0), Fz = R(0);
+  if (DRAG) {
+    const R kd = R(1) / (R(1) + R(0.5) * s);
+    ux *= kd;
+    uy *= kd;
+    uz *= kd;
+    const R rs = rho * s;
+    Fx = fma(-rs, ux, rho * c.g[0]);
+    Fy = fma(-rs, uy, rho * c.g[1]);
+    Fz = fma(-rs, uz, rho * c.g[2]);
+  } else if (FORCE) {
+    Fx = rho * c.g[0];
+    Fy = rho * c.g[1];
+    Fz = rho * c.g[2];
+  }
+  const R uu = fma(ux, ux, fma(uy, uy, uz * uz));
+  const R base = fma(R(-1.5) * rho, uu, drho);  // drho - 3/2 rho u.u
+  R K0a;                                      // axis-class K0 = w (l+ base - 3 a+ u.F)
+  R Fsx = R(0), Fsy = R(0), Fsz = R(0), Fox = R(0), Foy = R(0), Foz = R(0);
+  if (FORCE || DRAG) {
+    const R uF = fma(ux, Fx, fma(uy, Fy, uz * Fz));
+    K0a = fma(c.k0a, base, -c.k0b * uF);
+    Fsx = c.fs * Fx;
+    Fsy = c.fs * Fy;
+    Fsz = c.fs * Fz;
+    Fox = c.fo * Fx;
+    Foy = c.fo * Fy;
+    Foz = c.fo * Fz;
+  } else {
+    K0a = c.k0a * base;
+  }
+  const R K1a = c.k1 * rho, K2a = c.k2 * rho;
+  const R K0b = R(0.5) * K0a, K1b = R(0.5) * K1a, K2b = R(0.5) * K2a;
+  constexpr bool F = FORCE || DRAG;
+  // axis pairs (weight 1/18)
+  coll_pair<R, F, 1>(d, sa[1], da[1], ux, uy, uz, K0a, K1a, K2a, Fsx, Fsy, Fsz, Fox, Foy, Foz, c.qp, c.qm);
+  coll_pair<R, F, 2>(d, sa[2], da[2], ux, uy, uz, K0a, K1a, K2a, Fsx, Fsy, Fsz, Fox, Foy, Foz, c.qp, c.qm);
+  coll_pair<R, F, 3>(d, sa[3], da[3], ux, uy, uz, K0a, K1a, K2a, Fsx, Fsy, Fsz, Fox, Foy, Foz, c.qp, c.qm);
+  // diagonal pairs (weight 1/36): every class constant halves
+  const R hFsx = R(0.5) * Fsx, hFsy = R(0.5) * Fsy, hFsz = R(0.5) * Fsz;
+  const R hFox = R(0.5) * Fox, hFoy = R(0.5) * Foy, hFoz = R(0.5) * Foz;
+  coll_pair<R, F, 4>(d, sa[4], da[4], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
+  coll_pair<R, F, 5>(d, sa[5], da[5], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
+  coll_pair<R, F, 6>(d, sa[6], da[6], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
+  coll_pair<R, F, 7>(d, sa[7], da[7], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
+  coll_pair<R, F, 8>(d, sa[8], da[8], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
+  coll_pair<R, F, 9>(d, sa[9], da[9], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
+  // rest PDF: p0 = (1 - l+) d0 + w0 (l+ base - 3 a+ u.F), w0 = 6 w_axis
+  d[0] = fma(R(2) * c.qp, d[0], R(6) * K0a);
+}
+
+// ---- PDF gathers of the storage layouts ----------------------------------------------
+// Pull of f_i at node n with adjacency entry m:
+//   OS-NT grid (post-collision P):   P[i][m]      | marker: P[inv i][n]
+//   AA grid after an odd count:      A[inv i][m]  | marker: A[i][n]
+// a pressure marker (-2 / -3) turns the bounce-back value v into
+// 2 w_i (rho_bc - rho_s) - v (anti-bounce-back, in deviation form).
+template <int PREC, bool AA_ODD>
+__device__ __forceinline__ void gather(const typename St<PREC>::T* g, int64_t Npad, int n, const int (&m)[18],
+                                       typename St<PREC>::R (&d)[kQ], float inv_scale,
+                                       const CollConst<typename St<PREC>::R>& c) {
+  using R = typename St<PREC>::R;
+  d[0] = St<PREC>::ld(g + n, inv_scale);
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) {
+    const int mi = m[i - 1];
+    const int dir = (mi >= 0) == AA_ODD ? inv(i) : i;
+    const int node = mi >= 0 ? mi : n;
+    R v = St<PREC>::ld(g + size_t(dir) * Npad + node, inv_scale);
+    if (mi < -1) v = (mi == LBM_MARK_INLET ? c.abb_in[wclass(i) - 1] : c.abb_out[wclass(i) - 1]) - v;
+    d[i] = v;
+  }
+}
+
+// ---- kernels -----------------------------------------------------------------------------
+// OS-NT step: pull (indirect) from src, collide, store locally into dst with
+// evict-first stores so the write stream does not push src out of L2.
+template <int PREC, bool RIA, bool FORCE, bool DRAG>
+__global__ void __launch_bounds__(kBlock) k_osnt(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
+                                                 const typename St<PREC>::T* __restrict__ src,
+                                                 typename St<PREC>::T* __restrict__ dst, const float* __restrict__ s,
+                                                 int N) {
+  using R = typename St<PREC>::R;
+  __shared__ int s_rs[kBlock + 1];
+  const int n0 = blockIdx.x * kBlock;
+  const int n = n0 + threadIdx.x;
+  int m[18];
+  if (RIA) {
+    RiaCursor cur = ria_locate(t, n0, n, N, s_rs);
+    if (n >= N) return;
+    nbr_ria(t, cur, m);
+  } else {
+    if (n >= N) return;
+    nbr_adj(t, n, m);
+  }
+  R d[kQ];
+  gather<PREC, false>(src, t.Npad, n, m, d, kp.inv_scale, c);
+  const R sn = DRAG ? R(__ldg(s + n)) : R(0);
+  collide<R, FORCE, DRAG>(d, c, sn);
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) St<PREC>::st_stream(dst + size_t(i) * t.Npad + n, d[i], kp.scale);
+}
+
+// AA even step: direct read of the 19 local PDFs, collide, write to the
+// opposite local slots (no index loads at all).
+template <int PREC, bool FORCE, bool DRAG>
+__global__ void __launch_bounds__(kBlock) k_aa_even(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
+                                                    typename St<PREC>::T* __restrict__ A,
+                                                    const float* __restrict__ s, int N) {
+  using R = typename St<PREC>::R;
+  const int n = blockIdx.x * kBlock + threadIdx.x;
+  if (n >= N) return;
+  R d[kQ];
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) d[i] = St<PREC>::ld(A + size_t(i) * t.Npad + n, kp.inv_scale);
+  const R sn = DRAG ? R(__ldg(s + n)) : R(0);
+  collide<R, FORCE, DRAG>(d, c, sn);
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) St<PREC>::st(A + size_t(inv(i)) * t.Npad + n, d[i], kp.scale);
+}
+
+// AA odd step: read f_i from the neighbour's opposite slot A[inv i][m_i], collide,
+// write p_i to A[i][m_{inv i}] -- the same 19 slots, so in place and race-free.
+template <int PREC, bool RIA, bool FORCE, bool DRAG>
+__global__ void __launch_bounds__(kBlock) k_aa_odd(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
+                                                   typename St<PREC>::T* __restrict__ A,
+                                                   const float* __restrict__ s, int N) {
+  using R = typename St<PREC>::R;
+  __shared__ int s_rs[kBlock + 1];
+  const int n0 = blockIdx.x * kBlock;
+  const int n = n0 + threadIdx.x;
+  int m[18];
+  if (RIA) {
+    RiaCursor cur = ria_locate(t, n0, n, N, s_rs);
+    if (n >= N) return;
+    nbr_ria(t, cur, m);
+  } else {
+    if (n >= N) return;
+    nbr_adj(t, n, m);
+  }
+  R d[kQ];
+  gather<PREC, true>(A, t.Npad, n, m, d, kp.inv_scale, c);
+  const R sn = DRAG ? R(__ldg(s + n)) : R(0);
+  collide<R, FORCE, DRAG>(d, c, sn);
+  St<PREC>::st(A + n, d[0], kp.scale);
+#pragma unroll
+  for (int i = 1; i < kQ; ++i) {
+    const int mo = m[inv(i) - 1];  // who pulls p_i next: node mo, or this node through a marker
+    R v = d[i];
+    if (mo < -1) v = (mo == LBM_MARK_INLET ? c.abb_in[wclass(i) - 1] : c.abb_out[wclass(i) - 1]) - v;
+    const int dir = mo >= 0 ? i : inv(i);
+    const int node = mo >= 0 ? mo : n;
+    St<PREC>::st(A + size_t(dir) * t.Npad + node, v, kp.scale);
+  }
+}
+
+}  // namespace dev
+}  // namespace lbm
+
+namespace lbm {
+namespace dev {
+
+// ---- state set-up and read-back kernels ------------------------------------------------
+
+// Fill a grid so that its canonical state is the uniform f^eq given in feq[19]
+// (FP64, unshifted).  AA_EVEN layout stores f^eq directly; the OS-NT layout
+// stores the slot (j, n) as the value node adj(inv j, n) pulls from it:
+// f^eq_j for a fluid puller, f^eq_{inv j} for bounce-back, and
+// 2 w_j rho_bc - f^eq_{inv j} for anti-bounce-back; the AA_ODD layout holds
+// that same value in slot (inv j, n).
+struct Feq19 {
+  double v[kQ];
+};
+
+template <int PREC, bool RIA>
+__global__ void __launch_bounds__(kBlock) k_init_eq(DevTables t, KParams kp, Feq19 feq, typename St<PREC>::T* pdf,
+                                                    int layout, int N) {
+  using R = typename St<PREC>::R;
+  __shared__ int s_rs[kBlock + 1];
+  const int n0 = blockIdx.x * kBlock;
+  const int n = n0 + threadIdx.x;
+  int m[18];
+  if (layout != LBM_LAYOUT_AA_EVEN) {
+    if (RIA) {
+      RiaCursor cur = ria_locate(t, n0, n, N, s_rs);
+      if (n >= N) return;
+      nbr_ria(t, cur, m);
+    } else {
+      if (n >= N) return;
+      nbr_adj(t, n, m);
+    }
+  } else if (n >= N) {
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < kQ; ++j) {
+    double v = feq.v[j];
+    int slot = j;
+    if (layout != LBM_LAYOUT_AA_EVEN && j > 0) {
+      const int mp = m[inv(j) - 1];
+      if (mp < 0) v = feq.v[inv(j)];
+      if (mp < -1) v = wgt(j) * 2.0 * (mp == LBM_MARK_INLET ? kp.rho_in : kp.rho_out) - v;
+      if (layout == LBM_LAYOUT_AA_ODD) slot = inv(j);
+    }
+    St<PREC>::st(pdf + size_t(slot) * t.Npad + n, R(v - wgt(j) * kp.rho_s), kp.scale);
+  }
+}
+
+// Store a canonical FP64 state F[19][N] into a grid of the given layout (the
+// general form of k_init_eq: the fluid puller's value is read from F at that
+// node).
+template <int PREC, bool RIA>
+__global__ void __launch_bounds__(kBlock) k_load_canonical(DevTables t, KParams kp, const double* __restrict__ F,
+                                                           typename St<PREC>::T* pdf, int layout, int N) {
+  using R = typename St<PREC>::R;
+  __shared__ int s_rs[kBlock + 1];
+  const int n0 = blockIdx.x * kBlock;
+  const int n = n0 + threadIdx.x;
+  int m[18];
+  if (layout != LBM_LAYOUT_AA_EVEN) {
+    if (RIA) {
+      RiaCursor cur = ria_locate(t, n0, n, N, s_rs);
+      if (n >= N) return;
+      nbr_ria(t, cur, m);
+    } else {
+      if (n >= N) return;
+      nbr_adj(t, n, m);
+    }
+  } else if (n >= N) {
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < kQ; ++j) {
+    double v;
+    int slot = j;
+    if (layout == LBM_LAYOUT_AA_EVEN || j == 0) {
+      v = F[size_t(j) * N + n];
+    } else {
+      const int mp = m[inv(j) - 1];
+      if (mp >= 0) {
+        v = F[size_t(j) * N + mp];
+      } else {
+        v = F[size_t(inv(j)) * N + n];
+        if (mp < -1) v = wgt(j) * 2.0 * (mp == LBM_MARK_INLET ? kp.rho_in : kp.rho_out) - v;
+      }
+      if (layout == LBM_LAYOUT_AA_ODD) slot = inv(j);
+    }
+    St<PREC>::st(pdf + size_t(slot) * t.Npad + n, R(v - wgt(j) * kp.rho_s), kp.scale);
+  }
+}
+
+// Canonical pre-collision state of one node, FP64, unshifted.
+template <int PREC, bool RIA>
+__device__ __forceinline__ bool node_canonical(const DevTables& t, const KParams& kp,
+                                               const typename St<PREC>::T* pdf, int layout, int n0, int n, int N,
+                                               int* s_rs, double (&F)[kQ]) {
+  using R = typename St<PREC>::R;
+  int m[18];
+  if (layout != LBM_LAYOUT_AA_EVEN) {
+    if (RIA) {
+      RiaCursor cur = ria_locate(t, n0, n, N, s_rs);
+      if (n >= N) return false;
+      nbr_ria(t, cur, m);
+    } else {
+      if (n >= N) return false;
+      nbr_adj(t, n, m);
+    }
+  } else if (n >= N) {
+    return false;
+  }
+  R d[kQ];
+  if (layout == LBM_LAYOUT_AA_EVEN) {
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) d[i] = St<PREC>::ld(pdf + size_t(i) * t.Npad + n, kp.inv_scale);
+  } else if (layout == LBM_LAYOUT_OSNT) {
+    gather<PREC, false>(pdf, t.Npad, n, m, d, kp.inv_scale, make_coll<R>(kp));
+  } else {
+    gather<PREC, true>(pdf, t.Npad, n, m, d, kp.inv_scale, make_coll<R>(kp));
+  }
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) F[i] = double(d[i]) + wgt(i) * kp.rho_s;
+  return true;
+}
+
+template <int PREC, bool RIA>
+__global__ void __launch_bounds__(kBlock) k_canonical(DevTables t, KParams kp, const typename St<PREC>::T* pdf,
+                                                      int layout, double* __restrict__ F, int N) {
+  __shared__ int s_rs[kBlock + 1];
+  const int n0 = blockIdx.x * kBlock;
+  const int n = n0 + threadIdx.x;
+  double f[kQ];
+  if (!node_canonical<PREC, RIA>(t, kp, pdf, layout, n0, n, N, s_rs, f)) return;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) F[size_t(i) * N + n] = f[i];
+}
+
+// Block-wide sum of 4 doubles; result valid in thread 0.  Fixed order.
+__device__ __forceinline__ void block_sum4(double (&v)[4], double (*s_red)[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s_red[w][k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) {
+      double acc = s_red[0][k];
+      for (int j = 1; j < int(blockDim.x >> 5); ++j) acc += s_red[j][k];
+      v[k] = acc;
+    }
+  }
+}
+
+// rho, u = (j0/rho + g/2)/(1 + s/2) per node and per-CTA partial sums of
+// [rho, rho u_x, rho u_y, rho u_z] (FP64).
+template <int PREC, bool RIA>
+__global__ void __launch_bounds__(kBlock) k_macro(DevTables t, KParams kp, const typename St<PREC>::T* pdf,
+                                                  int layout, const float* __restrict__ s, double* __restrict__ rho,
+                                                  double* __restrict__ u, double* __restrict__ partials, int N) {
+  __shared__ int s_rs[kBlock + 1];
+  __shared__ double s_red[kBlock / 32][4];
+  const int n0 = blockIdx.x * kBlock;
+  const int n = n0 + threadIdx.x;
+  double f[kQ];
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  if (node_canonical<PREC, RIA>(t, kp, pdf, layout, n0, n, N, s_rs, f)) {
+    double r = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      r += f[i];
+      if (cx(i)) jx += cx(i) > 0 ? f[i] : -f[i];
+      if (cy(i)) jy += cy(i) > 0 ? f[i] : -f[i];
+      if (cz(i)) jz += cz(i) > 0 ? f[i] : -f[i];
+    }
+    const double kd = s ? 1.0 / (1.0 + 0.5 * double(s[n])) : 1.0;
+    const double ux = (jx / r + 0.5 * kp.g[0]) * kd;
+    const double uy = (jy / r + 0.5 * kp.g[1]) * kd;
+    const double uz = (jz / r + 0.5 * kp.g[2]) * kd;
+    if (rho) rho[n] = r;
+    if (u) {
+      u[n] = ux;
+      u[size_t(N) + n] = uy;
+      u[2 * size_t(N) + n] = uz;
+    }
+    acc[0] = r;
+    acc[1] = r * ux;
+    acc[2] = r * uy;
+    acc[3] = r * uz;
+  }
+  if (!partials) return;
+  __syncthreads();
+  block_sum4(acc, s_red);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) partials[size_t(blockIdx.x) * 4 + k] = acc[k];
+}
+
+// Sum nparts x 4 partials into out[4] with one CTA in a fixed order.
+template <int PREC>
+__global__ void __launch_bounds__(512) k_finish4(const double* __restrict__ partials, int64_t nparts,
+                                                 double* __restrict__ out) {
+  __shared__ double s_red[16][4];
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t p = threadIdx.x; p < nparts; p += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] += partials[p * 4 + k];
+  block_sum4(acc, s_red);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[k] = acc[k];
+}
+
+}  // namespace dev
+
+// ---- launchers, one set per storage precision ----------------------------------------------
+
+inline int cuda_check(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+inline unsigned grid_of(int64_t N) { return unsigned((N + dev::kBlock - 1) / dev::kBlock); }
+
+inline bool has_force(const KParams& kp) { return kp.g[0] != 0.0 || kp.g[1] != 0.0 || kp.g[2] != 0.0; }
+
+template <int PREC>
+int launch_osnt_t(const lbm_lattice* L, const KParams& kp, const void* src, void* dst, const float* s, int ria,
+                  void* stream) {
+  using T = typename dev::St<PREC>::T;
+  auto st = static_cast<cudaStream_t>(stream);
+  const unsigned g = grid_of(L->N);
+  const T* a = static_cast<const T*>(src);
+  T* b = static_cast<T*>(dst);
+  const int N = int(L->N);
+  const bool f = has_force(kp);
+  const auto c = dev::make_coll<typename dev::St<PREC>::R>(kp);
+#define LBM_OSNT(R_, F_, D_) dev::k_osnt<PREC, R_, F_, D_><<<g, dev::kBlock, 0, st>>>(L->dev, kp, c, a, b, s, N)
+  if (s) {
+    if (ria) LBM_OSNT(true, true, true); else LBM_OSNT(false, true, true);
+  } else if (f) {
+    if (ria) LBM_OSNT(true, true, false); else LBM_OSNT(false, true, false);
+  } else {
+    if (ria) LBM_OSNT(true, false, false); else LBM_OSNT(false, false, false);
+  }
+#undef LBM_OSNT
+  return cuda_check("OS-NT step launch");
+}
+
+template <int PREC>
+int launch_aa_t(const lbm_lattice* L, const KParams& kp, void* pdf, int parity, const float* s, int ria,
+                void* stream) {
+  using T = typename dev::St<PREC>::T;
+  auto st = static_cast<cudaStream_t>(stream);
+  const unsigned g = grid_of(L->N);
+  T* A = static_cast<T*>(pdf);
+  const int N = int(L->N);
+  const bool f = has_force(kp);
+  const auto c = dev::make_coll<typename dev::St<PREC>::R>(kp);
+  if (parity == 0) {
+    if (s) dev::k_aa_even<PREC, true, true><<<g, dev::kBlock, 0, st>>>(L->dev, kp, c, A, s, N);
+    else if (f) dev::k_aa_even<PREC, true, false><<<g, dev::kBlock, 0, st>>>(L->dev, kp, c, A, s, N);
+    else dev::k_aa_even<PREC, false, false><<<g, dev::kBlock, 0, st>>>(L->dev, kp, c, A, s, N);
+    return cuda_check("AA even step launch");
+  }
+#define LBM_AAODD(R_, F_, D_) dev::k_aa_odd<PREC, R_, F_, D_><<<g, dev::kBlock, 0, st>>>(L->dev, kp, c, A, s, N)
+  if (s) {
+    if (ria) LBM_AAODD(true, true, true); else LBM_AAODD(false, true, true);
+  } else if (f) {
+    if (ria) LBM_AAODD(true, true, false); else LBM_AAODD(false, true, false);
+  } else {
+    if (ria) LBM_AAODD(true, false, false); else LBM_AAODD(false, false, false);
+  }
+#undef LBM_AAODD
+  return cuda_check("AA odd step launch");
+}
+
+template <int PREC>
+int launch_init_eq_t(const lbm_lattice* L, const KParams& kp, void* pdf, int layout, double rho0, const double u0[3],
+                     void* stream) {
+  using T = typename dev::St<PREC>::T;
+  if (L->N == 0) return LBM_OK;
+  dev::Feq19 feq;
+  const double uu = u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2];
+  for (int i = 0; i < kQ; ++i) {
+    const double cu = kCX[i] * u0[0] + kCY[i] * u0[1] + kCZ[i] * u0[2];
+    feq.v[i] = dev::wgt(i) * rho0 * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+  }
+  auto st = static_cast<cudaStream_t>(stream);
+  const bool ria = !(L->uploaded & LBM_TABLES_ADJ);
+  if (ria)
+    dev::k_init_eq<PREC, true><<<grid_of(L->N), dev::kBlock, 0, st>>>(L->dev, kp, feq, static_cast<T*>(pdf), layout,
+                                                                     int(L->N));
+  else
+    dev::k_init_eq<PREC, false><<<grid_of(L->N), dev::kBlock, 0, st>>>(L->dev, kp, feq, static_cast<T*>(pdf), layout,
+                                                                      int(L->N));
+  return cuda_check("init launch");
+}
+
+template <int PREC>
+int launch_load_canonical_t(const lbm_lattice* L, const KParams& kp, const double* F, void* pdf, int layout,
+                            void* stream) {
+  using T = typename dev::St<PREC>::T;
+  if (L->N == 0) return LBM_OK;
+  auto st = static_cast<cudaStream_t>(stream);
+  const bool ria = !(L->uploaded & LBM_TABLES_ADJ);
+  if (ria)
+    dev::k_load_canonical<PREC, true><<<grid_of(L->N), dev::kBlock, 0, st>>>(L->dev, kp, F, static_cast<T*>(pdf),
+                                                                            layout, int(L->N));
+  else
+    dev::k_load_canonical<PREC, false><<<grid_of(L->N), dev::kBlock, 0, st>>>(L->dev, kp, F, static_cast<T*>(pdf),
+                                                                             layout, int(L->N));
+  return cuda_check("load launch");
+}
+
+template <int PREC>
+int launch_canonical_t(const lbm_lattice* L, const KParams& kp, const void* pdf, int layout, double* F,
+                       void* stream) {
+  using T = typename dev::St<PREC>::T;
+  if (L->N == 0) return LBM_OK;
+  auto st = static_cast<cudaStream_t>(stream);
+  const bool ria = !(L->uploaded & LBM_TABLES_ADJ);
+  if (ria)
+    dev::k_canonical<PREC, true><<<grid_of(L->N), dev::kBlock, 0, st>>>(L->dev, kp, static_cast<const T*>(pdf),
+                                                                       layout, F, int(L->N));
+  else
+    dev::k_canonical<PREC, false><<<grid_of(L->N), dev::kBlock, 0, st>>>(L->dev, kp, static_cast<const T*>(pdf),
+                                                                        layout, F, int(L->N));
+  return cuda_check("canonical launch");
+}
+
+template <int PREC>
+int launch_macroscopic_t(const lbm_lattice* L, const KParams& kp, const void* pdf, int layout, const float* s,
+                         double* rho, double* u, double* sums, double* partials, int64_t nparts, void* stream) {
+  using T = typename dev::St<PREC>::T;
+  auto st = static_cast<cudaStream_t>(stream);
+  double* part = sums ? partials : nullptr;
+  if (L->N > 0) {
+    const bool ria = !(L->uploaded & LBM_TABLES_ADJ);
+    if (ria)
+      dev::k_macro<PREC, true><<<grid_of(L->N), dev::kBlock, 0, st>>>(L->dev, kp, static_cast<const T*>(pdf), layout,
+                                                                     s, rho, u, part, int(L->N));
+    else
+      dev::k_macro<PREC, false><<<grid_of(L->N), dev::kBlock, 0, st>>>(L->dev, kp, static_cast<const T*>(pdf), layout,
+                                                                      s, rho, u, part, int(L->N));
+    if (int rc = cuda_check("macroscopic launch")) return rc;
+  }
+  if (sums) {
+    dev::k_finish4<PREC><<<1, 512, 0, st>>>(partials, L->N > 0 ? nparts : 0, sums);
+    return cuda_check("reduction launch");
+  }
+  return LBM_OK;
+}
+
+#define LBM_INSTANTIATE_LAUNCHERS(P)                                                                               \
+  template int launch_osnt_t<P>(const lbm_lattice*, const KParams&, const void*, void*, const float*, int, void*); \
+  template int launch_aa_t<P>(const lbm_lattice*, const KParams&, void*, int, const float*, int, void*);           \
+  template int launch_init_eq_t<P>(const lbm_lattice*, const KParams&, void*, int, double, const double*, void*);  \
+  template int launch_load_canonical_t<P>(const lbm_lattice*, const KParams&, const double*, void*, int, void*);   \
+  template int launch_canonical_t<P>(const lbm_lattice*, const KParams&, const void*, int, double*, void*);        \
+  template int launch_macroscopic_t<P>(const lbm_lattice*, const KParams&, const void*, int, const float*,          \
+                                       double*, double*, double*, double*, int64_t, void*);
+
+}  // namespace lbm

@@ -1,0 +1,6 @@
+// Instantiates the device kernels and launchers for LBM_F32 storage.
+#include "kernels.cuh"
+
+namespace lbm {
+LBM_INSTANTIATE_LAUNCHERS(LBM_F32)
+}  // namespace lbm

@@ -1,0 +1,421 @@
+// Host-side construction of the sparse lattice: fluid-node enumeration,
+// adjacency list and RIA run table, plus their validation.
+//
+// Sect. 1 and Sect. 5.6: fluid nodes are stored in one 1-D vector whose order
+// is set by an enumeration function, lexicographic sorting (LS) with a
+// blocking factor B or a space-filling (Hilbert) curve.  Sect. 4 "Loop
+// Balance" and Fig. 2a: an adjacency list holds, per node, where each of the
+// 18 moving PDFs is pulled from.  Sect. 4.1 and Fig. 2b: reduced indirect
+// addressing keeps only the runs of nodes whose access pattern is the
+// previous node's shifted by one, run-length coded.
+//
+// Everything here is O(voxels) or O(N) and multithreaded with std::thread;
+// none of it is on the timed path.
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <functional>
+#include <thread>
+
+#include "internal.h"
+
+namespace lbm {
+namespace {
+
+int n_threads() {
+  unsigned h = std::thread::hardware_concurrency();
+  return h == 0 ? 4 : static_cast<int>(std::min(h, 64u));
+}
+
+// Run body(begin, end) over [0, n) split into contiguous chunks, one per thread.
+void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& body) {
+  int T = n_threads();
+  if (n < 4096 || T == 1) {
+    if (n > 0) body(0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  int64_t chunk = (n + T - 1) / T;
+  for (int t = 0; t < T; ++t) {
+    int64_t b = t * chunk, e = std::min(n, b + chunk);
+    if (b >= e) break;
+    th.emplace_back(body, b, e);
+  }
+  for (auto& x : th) x.join();
+}
+
+// Exclusive prefix sum in place; returns the total.
+int64_t exclusive_scan(std::vector<int64_t>& v) {
+  int64_t acc = 0;
+  for (auto& x : v) {
+    int64_t c = x;
+    x = acc;
+    acc += c;
+  }
+  return acc;
+}
+
+// ---- LS with blocking factor B -------------------------------------------------
+// Work unit u = (block z, block y, block x, z offset in the block); units are
+// numbered in the enumeration's own order, so counting fluid voxels per unit,
+// scanning, and refilling gives the node order without a sort.
+int enumerate_lex(lbm_lattice* L, const uint8_t* solid, int B) {
+  const int64_t X = L->X, Y = L->Y, Z = L->Z;
+  const int64_t Bm = std::max<int64_t>({X, Y, Z});
+  const int64_t b = (B <= 1 || B >= Bm) ? Bm : B;  // B = 1 orders like one big block
+  const int64_t nbx = (X + b - 1) / b, nby = (Y + b - 1) / b, nbz = (Z + b - 1) / b;
+  const int64_t units = nbz * nby * nbx * b;
+  auto unit_box = [&](int64_t u, int64_t& z, int64_t& y0, int64_t& y1, int64_t& x0, int64_t& x1) {
+    int64_t dz = u % b;
+    int64_t blk = u / b;
+    int64_t bx = blk % nbx;
+    int64_t by = (blk / nbx) % nby;
+    int64_t bz = blk / (nbx * nby);
+    z = bz * b + dz;
+    y0 = by * b;
+    y1 = std::min(Y, y0 + b);
+    x0 = bx * b;
+    x1 = std::min(X, x0 + b);
+    return z < Z;
+  };
+  std::vector<int64_t> cnt(units, 0);
+  parallel_for(units, [&](int64_t ub, int64_t ue) {
+    for (int64_t u = ub; u < ue; ++u) {
+      int64_t z, y0, y1, x0, x1;
+      if (!unit_box(u, z, y0, y1, x0, x1)) continue;
+      int64_t c = 0;
+      for (int64_t y = y0; y < y1; ++y) {
+        const uint8_t* row = solid + (z * Y + y) * X;
+        for (int64_t x = x0; x < x1; ++x) c += row[x] == 0;
+      }
+      cnt[u] = c;
+    }
+  });
+  int64_t N = exclusive_scan(cnt);
+  if (N > INT32_MAX) return set_error(LBM_ERR_ARG, "more than 2^31-1 fluid nodes");
+  L->N = N;
+  L->node_xyz.assign(3 * N, 0);
+  parallel_for(units, [&](int64_t ub, int64_t ue) {
+    for (int64_t u = ub; u < ue; ++u) {
+      int64_t z, y0, y1, x0, x1;
+      if (!unit_box(u, z, y0, y1, x0, x1)) continue;
+      int64_t n = cnt[u];
+      for (int64_t y = y0; y < y1; ++y) {
+        const uint8_t* row = solid + (z * Y + y) * X;
+        for (int64_t x = x0; x < x1; ++x)
+          if (row[x] == 0) {
+            L->node_xyz[3 * n + 0] = static_cast<int32_t>(x);
+            L->node_xyz[3 * n + 1] = static_cast<int32_t>(y);
+            L->node_xyz[3 * n + 2] = static_cast<int32_t>(z);
+            ++n;
+          }
+      }
+    }
+  });
+  return LBM_OK;
+}
+
+// ---- Hilbert curve ----------------------------------------------------------------
+// Index of (x, y, z) on the Hilbert curve of the 2^bits cube, after J. Skilling,
+// "Programming the Hilbert curve" (AIP Conf. Proc. 707, 2004): undo the
+// per-level rotations/reflections from the top bit down, Gray-code across the
+// three axes, then read the transposed bits out level by level (x first).
+uint64_t hilbert_index(uint32_t x, uint32_t y, uint32_t z, int bits) {
+  if (bits == 0) return 0;
+  uint32_t a[3] = {x, y, z};
+  const uint32_t top = 1u << (bits - 1);
+  for (uint32_t q = top; q > 1; q >>= 1) {
+    const uint32_t low = q - 1;
+    for (int k = 0; k < 3; ++k) {
+      if (a[k] & q) {
+        a[0] ^= low;
+      } else {
+        uint32_t t = (a[0] ^ a[k]) & low;
+        a[0] ^= t;
+        a[k] ^= t;
+      }
+    }
+  }
+  a[1] ^= a[0];
+  a[2] ^= a[1];
+  uint32_t fix = 0;
+  for (uint32_t q = top; q > 1; q >>= 1)
+    if (a[2] & q) fix ^= q - 1;
+  for (int k = 0; k < 3; ++k) a[k] ^= fix;
+  uint64_t key = 0;
+  for (int lvl = bits - 1; lvl >= 0; --lvl)
+    for (int k = 0; k < 3; ++k) key = (key << 1) | ((a[k] >> lvl) & 1u);
+  return key;
+}
+
+int enumerate_hilbert(lbm_lattice* L, const uint8_t* solid) {
+  const int64_t X = L->X, Y = L->Y, Z = L->Z;
+  int bits = 0;
+  while ((int64_t(1) << bits) < std::max<int64_t>({X, Y, Z})) ++bits;
+  if (3 * bits > 33)
+    return set_error(LBM_ERR_UNSUPPORTED, "Hilbert enumeration limited to boxes up to 2048 per axis");
+  // Raster list of fluid voxels (count per z-slab, scan, fill).
+  std::vector<int64_t> cnt(Z, 0);
+  parallel_for(Z, [&](int64_t zb, int64_t ze) {
+    for (int64_t z = zb; z < ze; ++z) {
+      int64_t c = 0;
+      const uint8_t* sl = solid + z * X * Y;
+      for (int64_t k = 0; k < X * Y; ++k) c += sl[k] == 0;
+      cnt[z] = c;
+    }
+  });
+  const int64_t N = exclusive_scan(cnt);
+  if (N > INT32_MAX) return set_error(LBM_ERR_ARG, "more than 2^31-1 fluid nodes");
+  // Keys are unique in [0, 8^bits): place every fluid voxel in its key slot,
+  // then scan the slots in order.
+  const int64_t slots = int64_t(1) << (3 * bits);
+  std::vector<int32_t> slot;
+  try {
+    slot.assign(slots, -1);
+  } catch (...) {
+    return set_error(LBM_ERR_ALLOC, "out of host memory for the Hilbert slot table");
+  }
+  std::vector<int32_t> raster(3 * N);
+  parallel_for(Z, [&](int64_t zb, int64_t ze) {
+    for (int64_t z = zb; z < ze; ++z) {
+      int64_t n = cnt[z];
+      for (int64_t y = 0; y < Y; ++y)
+        for (int64_t x = 0; x < X; ++x)
+          if (solid[(z * Y + y) * X + x] == 0) {
+            raster[3 * n] = int32_t(x);
+            raster[3 * n + 1] = int32_t(y);
+            raster[3 * n + 2] = int32_t(z);
+            slot[hilbert_index(uint32_t(x), uint32_t(y), uint32_t(z), bits)] = int32_t(n);
+            ++n;
+          }
+    }
+  });
+  // Compact the occupied slots in key order.
+  const int T = n_threads();
+  const int64_t chunk = (slots + T - 1) / T;
+  std::vector<int64_t> part(T, 0);
+  parallel_for(T, [&](int64_t tb, int64_t te) {
+    for (int64_t t = tb; t < te; ++t) {
+      int64_t c = 0;
+      for (int64_t k = t * chunk; k < std::min(slots, (t + 1) * chunk); ++k) c += slot[k] >= 0;
+      part[t] = c;
+    }
+  });
+  exclusive_scan(part);
+  L->N = N;
+  L->node_xyz.assign(3 * N, 0);
+  parallel_for(T, [&](int64_t tb, int64_t te) {
+    for (int64_t t = tb; t < te; ++t) {
+      int64_t n = part[t];
+      for (int64_t k = t * chunk; k < std::min(slots, (t + 1) * chunk); ++k)
+        if (slot[k] >= 0) {
+          std::memcpy(&L->node_xyz[3 * n], &raster[3 * int64_t(slot[k])], 3 * sizeof(int32_t));
+          ++n;
+        }
+    }
+  });
+  return LBM_OK;
+}
+
+// ---- adjacency list -------------------------------------------------------------------
+int fill_adjacency(lbm_lattice* L) {
+  const int64_t X = L->X, Y = L->Y, Z = L->Z, N = L->N, Np = L->Npad;
+  std::vector<int32_t> v2n;
+  try {
+    v2n.assign(X * Y * Z, -1);
+    L->adj.assign(18 * Np, LBM_MARK_WALL);
+  } catch (...) {
+    return set_error(LBM_ERR_ALLOC, "out of host memory for the adjacency list");
+  }
+  parallel_for(N, [&](int64_t b, int64_t e) {
+    for (int64_t n = b; n < e; ++n) {
+      const int32_t* p = &L->node_xyz[3 * n];
+      v2n[(int64_t(p[2]) * Y + p[1]) * X + p[0]] = int32_t(n);
+    }
+  });
+  const int64_t dim[3] = {X, Y, Z};
+  const int* per = L->bc.periodic;
+  const int xp = L->bc.x_pressure;
+  parallel_for(N, [&](int64_t b, int64_t e) {
+    for (int64_t n = b; n < e; ++n) {
+      const int32_t* p = &L->node_xyz[3 * n];
+      for (int i = 1; i < kQ; ++i) {
+        int64_t s[3] = {p[0] - kCX[i], p[1] - kCY[i], p[2] - kCZ[i]};
+        bool wall = false;
+        int press = 0;
+        for (int a = 0; a < 3; ++a) {
+          if (s[a] >= 0 && s[a] < dim[a]) continue;
+          if (per[a]) {
+            s[a] = (s[a] + dim[a]) % dim[a];
+          } else if (a == 0 && xp) {
+            press = s[a] < 0 ? LBM_MARK_INLET : LBM_MARK_OUTLET;
+          } else {
+            wall = true;
+          }
+        }
+        int32_t v;
+        if (wall)
+          v = LBM_MARK_WALL;
+        else if (press)
+          v = press;
+        else
+          v = v2n[(s[2] * Y + s[1]) * X + s[0]];  // -1 when solid
+        L->adj[(i - 1) * Np + n] = v;
+      }
+    }
+  });
+  return LBM_OK;
+}
+
+// Node n (>= 1) continues the run of node n-1 (Sect. 4.1): for every direction
+// both pull from fluid nodes with source index advanced by exactly one, or both
+// carry the same marker (their own-node source also advances by one).
+inline bool continues(const int32_t* adj, int64_t Np, int64_t n) {
+  for (int i = 0; i < 18; ++i) {
+    int32_t a = adj[i * Np + n - 1], c = adj[i * Np + n];
+    bool ok = (a >= 0 && c >= 0) ? (int64_t(c) == int64_t(a) + 1) : (a < 0 && c < 0 && a == c);
+    if (!ok) return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+int derive_ria(lbm_lattice* L) {
+  const int64_t N = L->N, Np = L->Npad;
+  const int T = n_threads();
+  const int64_t chunk = std::max<int64_t>(1, (N + T - 1) / T);
+  const int64_t nchunks = N == 0 ? 0 : (N + chunk - 1) / chunk;
+  std::vector<int64_t> heads(nchunks, 0);
+  parallel_for(nchunks, [&](int64_t cb, int64_t ce) {
+    for (int64_t c = cb; c < ce; ++c) {
+      int64_t h = 0;
+      for (int64_t n = c * chunk; n < std::min(N, (c + 1) * chunk); ++n)
+        h += (n == 0 || !continues(L->adj.data(), Np, n));
+      heads[c] = h;
+    }
+  });
+  const int64_t R = exclusive_scan(heads);
+  L->R = R;
+  L->Rpad = round_up(std::max<int64_t>(R, 1), kPad);
+  try {
+    L->run_start.assign(R + 1, 0);
+    L->run_adj.assign(18 * L->Rpad, LBM_MARK_WALL);
+  } catch (...) {
+    return set_error(LBM_ERR_ALLOC, "out of host memory for the RIA table");
+  }
+  parallel_for(nchunks, [&](int64_t cb, int64_t ce) {
+    for (int64_t c = cb; c < ce; ++c) {
+      int64_t r = heads[c];
+      for (int64_t n = c * chunk; n < std::min(N, (c + 1) * chunk); ++n)
+        if (n == 0 || !continues(L->adj.data(), Np, n)) {
+          L->run_start[r] = int32_t(n);
+          for (int i = 0; i < 18; ++i) L->run_adj[i * L->Rpad + r] = L->adj[i * Np + n];
+          ++r;
+        }
+    }
+  });
+  L->run_start[R] = int32_t(N);
+  // Run holding the first node of every tile (the last run past the end).
+  L->ntiles = (N + kTile - 1) / kTile;
+  L->tile_run0.assign(L->ntiles + 1, 0);
+  parallel_for(L->ntiles + 1, [&](int64_t tb, int64_t te) {
+    for (int64_t t = tb; t < te; ++t) {
+      int64_t first = std::min<int64_t>(t * kTile, N - 1);
+      if (N == 0) {
+        L->tile_run0[t] = 0;
+        continue;
+      }
+      auto it = std::upper_bound(L->run_start.begin(), L->run_start.begin() + R, int32_t(first));
+      L->tile_run0[t] = int32_t((it - L->run_start.begin()) - 1);
+    }
+  });
+  std::memset(L->hist, 0, sizeof(L->hist));
+  for (int64_t r = 0; r < R; ++r) {
+    int64_t len = int64_t(L->run_start[r + 1]) - L->run_start[r];
+    int b = 0;
+    while ((int64_t(2) << b) <= len) ++b;
+    L->hist[b]++;
+  }
+  return LBM_OK;
+}
+
+int build_tables(lbm_lattice* L, const uint8_t* solid) {
+  int rc = (L->enumeration == LBM_ENUM_HILBERT) ? enumerate_hilbert(L, solid)
+                                                 : enumerate_lex(L, solid, L->block_B);
+  if (rc) return rc;
+  L->Npad = round_up(std::max<int64_t>(L->N, 1), kPad);
+  if ((rc = fill_adjacency(L))) return rc;
+  return derive_ria(L);
+}
+
+int validate(const lbm_lattice* L) {
+  const int64_t N = L->N, Np = L->Npad, R = L->R;
+  const int32_t* adj = L->adj.data();
+  std::atomic<int64_t> bad{-1};
+  std::atomic<int> kind{0};
+  auto flag = [&](int64_t n, int k) {
+    int64_t cur = -1;
+    if (bad.compare_exchange_strong(cur, n)) kind = k;
+  };
+  parallel_for(N, [&](int64_t b, int64_t e) {
+    for (int64_t n = b; n < e && bad < 0; ++n)
+      for (int i = 1; i < kQ; ++i) {
+        int32_t m = adj[(i - 1) * Np + n];
+        if (m >= 0) {
+          if (m >= N) {
+            flag(n, 1);
+            break;
+          }
+          if (adj[(kInv[i] - 1) * Np + m] != n) {
+            flag(n, 2);
+            break;
+          }
+        } else if (m < LBM_MARK_OUTLET) {
+          flag(n, 1);
+          break;
+        }
+      }
+  });
+  if (bad >= 0)
+    return set_error(LBM_ERR_TABLE, std::string(kind == 1 ? "adjacency entry out of range"
+                                                          : "adjacency not reciprocal") +
+                                        " at node " + std::to_string(int64_t(bad)));
+  if (int64_t(L->run_start.size()) != R + 1 || L->run_start[0] != 0 || L->run_start[R] != N)
+    return set_error(LBM_ERR_TABLE, "run table does not cover [0, N)");
+  for (int64_t r = 0; r < R; ++r)
+    if (L->run_start[r + 1] <= L->run_start[r])
+      return set_error(LBM_ERR_TABLE, "run starts not strictly increasing at run " + std::to_string(r));
+  parallel_for(R, [&](int64_t b, int64_t e) {
+    for (int64_t r = b; r < e && bad < 0; ++r) {
+      const int64_t h = L->run_start[r];
+      if (h > 0 && continues(adj, Np, h)) {
+        flag(r, 3);
+        break;
+      }
+      for (int64_t n = h; n < L->run_start[r + 1]; ++n)
+        for (int i = 0; i < 18; ++i) {
+          int32_t a = L->run_adj[i * L->Rpad + r];
+          int64_t want = a >= 0 ? int64_t(a) + (n - h) : a;
+          if (want != adj[i * Np + n]) {
+            flag(r, 4);
+            n = L->run_start[r + 1];
+            break;
+          }
+        }
+    }
+  });
+  if (bad >= 0)
+    return set_error(LBM_ERR_TABLE, std::string(kind == 3 ? "run is not maximal"
+                                                          : "run table does not decode to the adjacency list") +
+                                        " at run " + std::to_string(int64_t(bad)));
+  for (int64_t t = 0; t <= L->ntiles && N > 0; ++t) {
+    int64_t first = std::min<int64_t>(t * kTile, N - 1);
+    int32_t r = L->tile_run0[t];
+    if (r < 0 || r >= R || L->run_start[r] > first || L->run_start[r + 1] <= first)
+      return set_error(LBM_ERR_TABLE, "tile run index inconsistent at tile " + std::to_string(t));
+  }
+  return LBM_OK;
+}
+
+}  // namespace lbm
