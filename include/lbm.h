@@ -242,6 +242,51 @@ LBM_API int lbm_macroscopic(const lbm_lattice* lat, int prec, const lbm_params* 
                     int layout, const float* s, double* rho, double* u, double* sums,
                     void* workspace, size_t ws_bytes, void* stream);
 
+/* ---- objective, discrete adjoint and checkpointed gradient ------------------------ */
+/* None of these has a counterpart in the paper: they differentiate the step of
+ * Eq. 1 (TRT collision, Sect. 2; pull streaming, Sect. 4) with respect to the
+ * per-node Brinkman solid fraction s.  The adjoint arrays ("lambda") have the
+ * grid layout [19][Npad] and element type double for LBM_F64, float for
+ * LBM_F32 and LBM_F16S. */
+
+/* Mean x-momentum objective J = (1/N) sum_n rho_n u_x,n of the canonical state
+ * of `pdf` (compensated FP64 sum) written to J (device double[1]).  Optional
+ * outputs: lambda_T = dJ/dF (adjoint layout) and grad_s (device double [N],
+ * overwritten) = the direct term dJ/ds.  workspace as for lbm_macroscopic. */
+LBM_API int lbm_objective_flux(const lbm_lattice* lat, int prec, const lbm_params* params, const void* pdf,
+                               int layout, const float* s, double* J, void* lambda_T, double* grad_s,
+                               void* workspace, size_t ws_bytes, void* stream);
+
+/* One discrete-adjoint step: given the OS-NT grid G_n of step n (its pull
+ * gather is the canonical state F_n) and lambda_next = dJ/dF_{n+1}, write
+ * lambda_n = dJ/dF_n and add (dF_{n+1}/ds)^T lambda_next to grad_s (device
+ * double [N], accumulated; may be NULL).  s may be NULL (s = 0).  lambda_next
+ * and lambda_n must not overlap.  ria selects the addressing as for the step. */
+LBM_API int lbm_adjoint_step(const lbm_lattice* lat, int prec, const lbm_params* params, const void* G_n,
+                             const void* lambda_next, void* lambda_n, const float* s, double* grad_s, int ria,
+                             void* stream);
+
+/* Device workspace of the checkpointed gradient: ceil(T/K) checkpoint grids,
+ * the final grid, max(2, K-1) recompute grids, two adjoint grids and the
+ * reduction partials. */
+LBM_API int lbm_ckpt_workspace_bytes(const lbm_lattice* lat, int prec, int T, int K, size_t* bytes);
+
+/* Forward pass of J(s) after T OS-NT steps from the OS-NT grid G0 (not
+ * modified), storing a checkpoint every K steps in the workspace; J written to
+ * device double[1].  K ~ sqrt(T) balances memory and recomputation. */
+LBM_API int lbm_flux_forward(const lbm_lattice* lat, int prec, const lbm_params* params, const void* G0,
+                             const float* s, int T, int K, int ria, void* workspace, size_t ws_bytes, double* J,
+                             void* stream);
+
+/* Backward pass after lbm_flux_forward with the same arguments and
+ * workspace: segment by segment in reverse, recompute the K states from the
+ * checkpoint, then run the adjoint steps back through them.  grad_s (device
+ * double [N]) is overwritten with dJ/ds; lambda_0 (adjoint layout, may be
+ * NULL) receives dJ/dF_0. */
+LBM_API int lbm_flux_backward(const lbm_lattice* lat, int prec, const lbm_params* params, const float* s, int T,
+                              int K, int ria, void* workspace, size_t ws_bytes, double* grad_s, void* lambda_0,
+                              void* stream);
+
 #ifdef __cplusplus
 }
 #endif

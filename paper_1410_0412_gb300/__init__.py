@@ -279,6 +279,112 @@ def lbm_macroscopic(lat, prec, params, pdf, layout, s=None, fields=True, sums=Tr
     return rho, u, out
 
 
+def _adjoint_dtype(prec):
+    torch = _torch()
+    return torch.float64 if prec == LBM_F64 else torch.float32
+
+
+def new_adjoint(lat, prec, device="cuda"):
+    """A zeroed adjoint array [19, Npad] (double for f64, float otherwise)."""
+    return _torch().zeros((19, lat.Npad), dtype=_adjoint_dtype(_prec(prec)), device=device)
+
+
+def _check_adj(lat, prec, t, name):
+    if t is None:
+        return
+    if not t.is_cuda or t.dtype != _adjoint_dtype(prec) or not t.is_contiguous() or t.numel() < 19 * lat.Npad:
+        raise TypeError(f"{name} must be a contiguous CUDA {_adjoint_dtype(prec)} tensor [19, Npad]")
+
+
+def lbm_objective_flux(lat, prec, params, pdf, layout, s=None, lambda_T=None, grad_s=None, stream=None):
+    """J (CUDA float64 [1]); optionally fills lambda_T = dJ/dF and grad_s = direct dJ/ds."""
+    torch = _torch()
+    prec = _prec(prec)
+    _check_grid(lat, prec, pdf, "pdf")
+    _check_adj(lat, prec, lambda_T, "lambda_T")
+    J = torch.empty(1, dtype=torch.float64, device=pdf.device)
+    ws_bytes = lat.reduce_workspace_bytes()
+    ws = torch.empty(ws_bytes // 8, dtype=torch.float64, device=pdf.device)
+    check(_lib.load().lbm_objective_flux(lat.handle, prec, ctypes.byref(params.c()), _ptr(pdf), layout,
+                                         _ptr(_check_s(lat, s)), _ptr(J), _ptr(lambda_T), _ptr(grad_s), _ptr(ws),
+                                         ws_bytes, _stream(stream)), "lbm_objective_flux")
+    return J
+
+
+def lbm_adjoint_step(lat, prec, params, G_n, lambda_next, lambda_n, s=None, grad_s=None, ria=False, stream=None):
+    prec = _prec(prec)
+    _check_grid(lat, prec, G_n, "G_n")
+    _check_adj(lat, prec, lambda_next, "lambda_next")
+    _check_adj(lat, prec, lambda_n, "lambda_n")
+    check(_lib.load().lbm_adjoint_step(lat.handle, prec, ctypes.byref(params.c()), _ptr(G_n), _ptr(lambda_next),
+                                       _ptr(lambda_n), _ptr(_check_s(lat, s)), _ptr(grad_s), 1 if ria else 0,
+                                       _stream(stream)), "lbm_adjoint_step")
+
+
+def lbm_ckpt_workspace_bytes(lat, prec, T, K) -> int:
+    b = ctypes.c_size_t()
+    check(_lib.load().lbm_ckpt_workspace_bytes(lat.handle, _prec(prec), int(T), int(K), ctypes.byref(b)),
+          "lbm_ckpt_workspace_bytes")
+    return b.value
+
+
+def lbm_flux_forward(lat, prec, params, G0, s, T, K, ws, ria=False, stream=None):
+    torch = _torch()
+    prec = _prec(prec)
+    _check_grid(lat, prec, G0, "G0")
+    J = torch.empty(1, dtype=torch.float64, device=G0.device)
+    check(_lib.load().lbm_flux_forward(lat.handle, prec, ctypes.byref(params.c()), _ptr(G0), _ptr(_check_s(lat, s)),
+                                       int(T), int(K), 1 if ria else 0, _ptr(ws), ws.numel() * ws.element_size(),
+                                       _ptr(J), _stream(stream)), "lbm_flux_forward")
+    return J
+
+
+def lbm_flux_backward(lat, prec, params, s, T, K, ws, ria=False, lambda_0=None, stream=None):
+    torch = _torch()
+    prec = _prec(prec)
+    _check_adj(lat, prec, lambda_0, "lambda_0")
+    grad = torch.empty(lat.N, dtype=torch.float64, device=ws.device)
+    check(_lib.load().lbm_flux_backward(lat.handle, prec, ctypes.byref(params.c()), _ptr(_check_s(lat, s)), int(T),
+                                        int(K), 1 if ria else 0, _ptr(ws), ws.numel() * ws.element_size(),
+                                        _ptr(grad), _ptr(lambda_0), _stream(stream)), "lbm_flux_backward")
+    return grad
+
+
+def _flux_function():
+    torch = _torch()
+
+    class FluxObjective(torch.autograd.Function):
+        """J(s) = mean x-momentum after T OS-NT steps from the OS-NT grid G0.
+
+        forward: T steps with a checkpoint every K steps (lbm_flux_forward);
+        backward: recompute each K-step segment from its checkpoint and run the
+        discrete adjoint back through it (lbm_flux_backward), gradient in FP64.
+        """
+
+        @staticmethod
+        def forward(ctx, s, lat, prec, params, G0, T, K, ria):
+            sf = s.detach().to(torch.float32).contiguous()
+            ws = torch.empty((lbm_ckpt_workspace_bytes(lat, prec, T, K) + 7) // 8, dtype=torch.float64,
+                             device=G0.device)
+            J = lbm_flux_forward(lat, prec, params, G0, sf, T, K, ws, ria)
+            ctx.state = (lat, prec, params, sf, T, K, ws, ria)
+            ctx.s_dtype = s.dtype
+            return J[0]
+
+        @staticmethod
+        def backward(ctx, gJ):
+            lat, prec, params, sf, T, K, ws, ria = ctx.state
+            grad = lbm_flux_backward(lat, prec, params, sf, T, K, ws, ria)
+            return (grad * gJ).to(ctx.s_dtype), None, None, None, None, None, None, None
+
+    return FluxObjective
+
+
+def flux_objective(s, lat, prec, params, G0, T, K, ria=False):
+    """Differentiable J(s) (torch autograd through the checkpointed adjoint)."""
+    return _flux_function().apply(s, lat, _prec(prec), params, G0, int(T), int(K), bool(ria))
+
+
 class Solver:
     """A running simulation in one storage form ("osnt" or "aa") and precision."""
 
@@ -338,4 +444,6 @@ __all__ = [
     "Params", "Lattice", "Solver", "LbmError", "lbm_init_equilibrium", "lbm_load_canonical", "lbm_canonical_pdfs",
     "lbm_step_osnt", "lbm_step_aa", "lbm_run_aa", "lbm_macroscopic", "LBM_F64", "LBM_F32", "LBM_F16S",
     "LBM_LAYOUT_OSNT", "LBM_LAYOUT_AA_EVEN", "LBM_LAYOUT_AA_ODD", "LBM_TABLES_ADJ", "LBM_TABLES_RIA",
+    "lbm_objective_flux", "lbm_adjoint_step", "lbm_ckpt_workspace_bytes", "lbm_flux_forward", "lbm_flux_backward",
+    "flux_objective", "new_adjoint",
 ]

@@ -78,6 +78,11 @@ SIGNATURES = {
     "lbm_run_aa": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _I, _P, _I, _P],
     "lbm_reduce_workspace_bytes": [_P, _PSZ],
     "lbm_macroscopic": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _P, _P, _P, _P, _P, _SZ, _P],
+    "lbm_objective_flux": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _P, _P, _P, _P, _P, _SZ, _P],
+    "lbm_adjoint_step": [_P, _I, ctypes.POINTER(lbm_params), _P, _P, _P, _P, _P, _I, _P],
+    "lbm_ckpt_workspace_bytes": [_P, _I, _I, _I, _PSZ],
+    "lbm_flux_forward": [_P, _I, ctypes.POINTER(lbm_params), _P, _P, _I, _I, _I, _P, _SZ, _P, _P],
+    "lbm_flux_backward": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _I, _I, _P, _SZ, _P, _P, _P],
 }
 _RESTYPES = {"lbm_last_error": ctypes.c_char_p, "lbm_free_lattice": None}
 

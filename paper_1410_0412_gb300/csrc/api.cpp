@@ -374,4 +374,172 @@ int lbm_macroscopic(const lbm_lattice* L, int prec, const lbm_params* params, co
                       static_cast<double*>(workspace), parts, stream);
 }
 
+
+int lbm_objective_flux(const lbm_lattice* L, int prec, const lbm_params* params, const void* pdf, int layout,
+                       const float* s, double* J, void* lambda_T, double* grad_s, void* workspace, size_t ws_bytes,
+                       void* stream) {
+  if (int rc = check_lat(L)) return rc;
+  KParams kp;
+  if (int rc = make_kparams(params, prec, &kp)) return rc;
+  if (int rc = check_layout(layout)) return rc;
+  if (!pdf || !J) return set_error(LBM_ERR_ARG, "pdf or J is NULL");
+  const int64_t parts = reduce_parts(L);
+  if (!workspace || ws_bytes < size_t(parts) * 4 * sizeof(double))
+    return set_error(LBM_ERR_ARG, "reduction workspace missing or too small");
+  if (layout != LBM_LAYOUT_AA_EVEN && L->N > 0) {
+    int ria;
+    if (int rc = any_tables(L, &ria)) return rc;
+  }
+  return LBM_DISPATCH(prec, launch_objective_t, L, kp, pdf, layout, s, J, lambda_T, grad_s,
+                      static_cast<double*>(workspace), stream);
+}
+
+int lbm_adjoint_step(const lbm_lattice* L, int prec, const lbm_params* params, const void* G_n,
+                     const void* lambda_next, void* lambda_n, const float* s, double* grad_s, int ria,
+                     void* stream) {
+  if (int rc = check_lat(L)) return rc;
+  KParams kp;
+  if (int rc = make_kparams(params, prec, &kp)) return rc;
+  if (!G_n || !lambda_next || !lambda_n) return set_error(LBM_ERR_ARG, "G_n, lambda_next or lambda_n is NULL");
+  if (lambda_next == lambda_n) return set_error(LBM_ERR_ARG, "lambda_next and lambda_n must differ");
+  if (L->N == 0) return LBM_OK;
+  if (int rc = check_tables(L, ria)) return rc;
+  return LBM_DISPATCH(prec, launch_adjoint_t, L, kp, G_n, lambda_next, lambda_n, s, grad_s, ria ? 1 : 0, stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+struct CkptLayout {
+  size_t grid = 0, lam = 0;
+  int nck = 0, nseg = 0;
+  size_t ck = 0, gT = 0, seg = 0, lamA = 0, lamB = 0, red = 0, total = 0;
+};
+
+CkptLayout ckpt_layout(const lbm_lattice* L, int prec, int T, int K) {
+  CkptLayout c;
+  const size_t el = prec == LBM_F64 ? 8 : prec == LBM_F32 ? 4 : 2;
+  const size_t lel = prec == LBM_F64 ? 8 : 4;
+  c.grid = align256(size_t(19) * L->Npad * el);
+  c.lam = align256(size_t(19) * L->Npad * lel);
+  c.nck = T > 0 ? (T + K - 1) / K : 1;
+  c.nseg = std::max(2, K - 1);
+  size_t off = 0;
+  c.ck = off;
+  off += c.grid * c.nck;
+  c.gT = off;
+  off += c.grid;
+  c.seg = off;
+  off += c.grid * c.nseg;
+  c.lamA = off;
+  off += c.lam;
+  c.lamB = off;
+  off += c.lam;
+  c.red = off;
+  off += align256(size_t(reduce_parts(L)) * 4 * sizeof(double));
+  c.total = off;
+  return c;
+}
+
+int check_ckpt_args(const lbm_lattice* L, int prec, int T, int K, void* ws, size_t ws_bytes, CkptLayout* out) {
+  if (T < 0) return set_error(LBM_ERR_ARG, "T must be >= 0");
+  if (K < 1) return set_error(LBM_ERR_ARG, "K must be >= 1");
+  if (prec < LBM_F64 || prec > LBM_F16S) return set_error(LBM_ERR_ARG, "unknown precision");
+  *out = ckpt_layout(L, prec, T, K);
+  if (!ws || ws_bytes < out->total) return set_error(LBM_ERR_ARG, "checkpoint workspace missing or too small");
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return set_error(LBM_ERR_ARG, "workspace not 256-byte aligned");
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_ckpt_workspace_bytes(const lbm_lattice* L, int prec, int T, int K, size_t* bytes) {
+  if (int rc = check_lat(L)) return rc;
+  if (!bytes) return set_error(LBM_ERR_ARG, "bytes is NULL");
+  if (T < 0 || K < 1) return set_error(LBM_ERR_ARG, "T must be >= 0 and K >= 1");
+  if (prec < LBM_F64 || prec > LBM_F16S) return set_error(LBM_ERR_ARG, "unknown precision");
+  *bytes = ckpt_layout(L, prec, T, K).total;
+  return LBM_OK;
+}
+
+int lbm_flux_forward(const lbm_lattice* L, int prec, const lbm_params* params, const void* G0, const float* s,
+                     int T, int K, int ria, void* ws, size_t ws_bytes, double* J, void* stream) {
+  if (int rc = check_lat(L)) return rc;
+  KParams kp;
+  if (int rc = make_kparams(params, prec, &kp)) return rc;
+  CkptLayout c;
+  if (int rc = check_ckpt_args(L, prec, T, K, ws, ws_bytes, &c)) return rc;
+  if (!G0 || !J) return set_error(LBM_ERR_ARG, "G0 or J is NULL");
+  if (L->N > 0)
+    if (int rc = check_tables(L, ria)) return rc;
+  char* base = static_cast<char*>(ws);
+  auto st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(base + c.ck, G0, c.grid, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return set_error(LBM_ERR_CUDA, std::string("checkpoint copy: ") + cudaGetErrorString(e));
+  const void* cur = base + c.ck;
+  for (int t = 0; t < T && L->N > 0; ++t) {
+    void* dst;
+    if (t + 1 == T)
+      dst = base + c.gT;
+    else if ((t + 1) % K == 0)
+      dst = base + c.ck + c.grid * ((t + 1) / K);
+    else
+      dst = base + c.seg + c.grid * ((t + 1) % 2);
+    if (int rc = LBM_DISPATCH(prec, launch_osnt_t, L, kp, cur, dst, s, ria ? 1 : 0, stream)) return rc;
+    cur = dst;
+  }
+  if (T == 0) {
+    e = cudaMemcpyAsync(base + c.gT, G0, c.grid, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return set_error(LBM_ERR_CUDA, std::string("copy: ") + cudaGetErrorString(e));
+  }
+  return LBM_DISPATCH(prec, launch_objective_t, L, kp, base + c.gT, LBM_LAYOUT_OSNT, s, J, nullptr, nullptr,
+                      reinterpret_cast<double*>(base + c.red), stream);
+}
+
+int lbm_flux_backward(const lbm_lattice* L, int prec, const lbm_params* params, const float* s, int T, int K,
+                      int ria, void* ws, size_t ws_bytes, double* grad_s, void* lambda_0, void* stream) {
+  if (int rc = check_lat(L)) return rc;
+  KParams kp;
+  if (int rc = make_kparams(params, prec, &kp)) return rc;
+  CkptLayout c;
+  if (int rc = check_ckpt_args(L, prec, T, K, ws, ws_bytes, &c)) return rc;
+  if (!grad_s && L->N > 0) return set_error(LBM_ERR_ARG, "grad_s is NULL");
+  if (L->N == 0) return LBM_OK;
+  if (int rc = check_tables(L, ria)) return rc;
+  char* base = static_cast<char*>(ws);
+  auto st = static_cast<cudaStream_t>(stream);
+  void* lamA = base + c.lamA;
+  void* lamB = base + c.lamB;
+  double* J = reinterpret_cast<double*>(base + c.red);  // scratch: the objective's J lands in the partials area
+  // lambda_T = dJ/dF_T and the direct dJ/ds term (overwrites grad_s)
+  if (int rc = LBM_DISPATCH(prec, launch_objective_t, L, kp, base + c.gT, LBM_LAYOUT_OSNT, s,
+                            J + 4 * reduce_parts(L) - 1, lamA, grad_s, J, stream))
+    return rc;
+  for (int ck = c.nck - 1; ck >= 0 && T > 0; --ck) {
+    const int t0 = ck * K, t1 = std::min(T, t0 + K);
+    auto state = [&](int t) -> const void* {
+      return t == t0 ? static_cast<const void*>(base + c.ck + c.grid * ck)
+                     : static_cast<const void*>(base + c.seg + c.grid * (t - t0 - 1));
+    };
+    for (int t = t0; t + 1 < t1; ++t)
+      if (int rc = LBM_DISPATCH(prec, launch_osnt_t, L, kp, state(t), const_cast<void*>(state(t + 1)), s,
+                                ria ? 1 : 0, stream))
+        return rc;
+    for (int t = t1 - 1; t >= t0; --t) {
+      if (int rc = LBM_DISPATCH(prec, launch_adjoint_t, L, kp, state(t), lamA, lamB, s, grad_s, ria ? 1 : 0, stream))
+        return rc;
+      std::swap(lamA, lamB);
+    }
+  }
+  if (lambda_0) {
+    cudaError_t e = cudaMemcpyAsync(lambda_0, lamA, size_t(19) * L->Npad * (prec == LBM_F64 ? 8 : 4),
+                                    cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return set_error(LBM_ERR_CUDA, std::string("copy: ") + cudaGetErrorString(e));
+  }
+  return LBM_OK;
+}
+
 }  // extern "C"

@@ -95,6 +95,13 @@ template <int PREC>
 int launch_macroscopic_t(const lbm_lattice* L, const KParams& kp, const void* pdf, int layout, const float* s,
                          double* rho, double* u, double* sums, double* partials, int64_t nparts, void* stream);
 
+template <int PREC>
+int launch_adjoint_t(const lbm_lattice* L, const KParams& kp, const void* G, const void* lam_next, void* lam,
+                     const float* s, double* grad_s, int ria, void* stream);
+template <int PREC>
+int launch_objective_t(const lbm_lattice* L, const KParams& kp, const void* pdf, int layout, const float* s,
+                       double* J, void* lamT, double* grad_s, double* partials, void* stream);
+
 // Precision dispatch: call F<LBM_F64 | LBM_F32 | LBM_F16S>.
 #define LBM_DISPATCH(prec, fn, ...)                                   \
   ((prec) == LBM_F64 ? fn<LBM_F64>(__VA_ARGS__)                       \

@@ -9,8 +9,8 @@ if ROOT not in sys.path:
 def _ensure_library():
     # The tests call the library through its C ABI; (re)build it when the
     # sources changed (a no-op when liblbm.so is up to date).
-    from paper_1410_0412_gb300 import _build
-    _build.build()
+    import __graft_entry__
+    __graft_entry__._builder().build()
 
 
 _ensure_library()
