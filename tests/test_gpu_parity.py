@@ -106,7 +106,9 @@ def test_layout_roundtrip_and_init(layout, ria):
     pdf = lat.new_grid("f64")
     lbm.lbm_load_canonical(lat, "f64", lp, F.cuda(), pdf, layout)
     ref_grid = olbm.from_canonical(F, layout, T.adj, op)
-    assert torch.equal(pdf[:, :T.N].cpu(), ref_grid)
+    # pure data movement, except anti-bounce-back slots 2 w rho_bc - F, which the
+    # device may evaluate as one fused multiply-add (one rounding less)
+    assert float((pdf[:, :T.N].cpu() - ref_grid).abs().max()) <= 2e-16
     back = lbm.lbm_canonical_pdfs(lat, "f64", lp, pdf, layout).cpu()
     assert float((back - F).abs().max()) <= 1e-16    # a - (a - b) may differ from b by one ulp
     lbm.lbm_init_equilibrium(lat, "f64", lp, pdf, layout, 1.0, (0.02, 0.0, -0.01))
