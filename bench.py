@@ -37,9 +37,11 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 # FP64 pipe of GB300: 152 SMs x 2 DP lanes/clk x 2.07 GHz (measured 0.60 T DFMA/s burst)
 FP64_PEAK_GINSTR = 152 * 2 * 2.07e9 / 1e9
-# FP64-pipe instructions of one TRT collision with body force in the library's
-# pair form (adds, multiplies and FMAs each take one FP64 issue slot).
-COLL_DP_INSTR = 169
+# FP64-pipe instructions per node of the AA odd step with RIA and body force
+# (adds, multiplies, FMAs, the reciprocal's iterations and selects each take one
+# FP64 slot): 198, from ncu's FP64-pipe utilisation (86.6 % of a 476.7 us launch
+# over 1,310,203 nodes at 2.07 GHz, 152 SMs x 2 lanes).
+COLL_DP_INSTR = 198
 
 WORKLOAD = dict(name="packed_bed_256_rsa_r12", X=256, Y=256, Z=256, radius=12.0, seed=1, rejections=20000,
                 periodic=(1, 0, 0), g=(1e-6, 0.0, 0.0), omega_plus=1.0, magic=3.0 / 16.0)
@@ -189,7 +191,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-variants", action="store_true")
