@@ -242,6 +242,22 @@ LBM_API int lbm_macroscopic(const lbm_lattice* lat, int prec, const lbm_params* 
                     int layout, const float* s, double* rho, double* u, double* sums,
                     void* workspace, size_t ws_bytes, void* stream);
 
+/* lbm_macroscopic for callers that cannot allocate device memory.  No
+ * counterpart in the paper: it exists because lbm_macroscopic needs a
+ * caller-provided workspace, and some callers cannot get one (a host
+ * application whose pool allocator owns all device memory, or a loop in which
+ * a possibly synchronising cudaMalloc is not allowed).  Same arguments and
+ * results as lbm_macroscopic without the workspace: the per-block partial
+ * sums live in a fixed 4 MiB array inside the library (present on every GPU
+ * that loads it, until unload), so at most 16,777,216 fluid nodes are
+ * accepted (LBM_ERR_ARG otherwise).  The first call on a device looks up that
+ * array's address with the device current; make it before any stream capture.
+ * All calls share the array: calls whose kernels overlap on the GPU race and
+ * may return wrong sums.  Allocates nothing. */
+LBM_API int lbm_macroscopic_noalloc(const lbm_lattice* lat, int prec, const lbm_params* params, const void* pdf,
+                                    int layout, const float* s, double* rho, double* u, double* sums,
+                                    void* stream);
+
 /* ---- objective, discrete adjoint and checkpointed gradient ------------------------ */
 /* None of these has a counterpart in the paper: they differentiate the step of
  * Eq. 1 (TRT collision, Sect. 2; pull streaming, Sect. 4) with respect to the

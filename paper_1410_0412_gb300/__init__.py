@@ -279,6 +279,22 @@ def lbm_macroscopic(lat, prec, params, pdf, layout, s=None, fields=True, sums=Tr
     return rho, u, out
 
 
+def lbm_macroscopic_noalloc(lat, prec, params, pdf, layout, s=None, rho=None, u=None, sums=None, stream=None):
+    """lbm_macroscopic for callers that cannot allocate device memory.
+
+    The library keeps the reduction's partial sums in its own fixed device
+    array, so no workspace is passed; rho [N], u [3, N] and sums [4] are
+    caller-provided float64 CUDA tensors (any may be None) and nothing is
+    allocated here.  At most 16,777,216 fluid nodes; concurrent calls that
+    overlap on the GPU share the array and race.
+    """
+    prec = _prec(prec)
+    _check_grid(lat, prec, pdf, "pdf")
+    check(_lib.load().lbm_macroscopic_noalloc(lat.handle, prec, ctypes.byref(params.c()), _ptr(pdf), layout,
+                                              _ptr(_check_s(lat, s)), _ptr(rho), _ptr(u), _ptr(sums),
+                                              _stream(stream)), "lbm_macroscopic_noalloc")
+
+
 def _adjoint_dtype(prec):
     torch = _torch()
     return torch.float64 if prec == LBM_F64 else torch.float32
@@ -445,5 +461,5 @@ __all__ = [
     "lbm_step_osnt", "lbm_step_aa", "lbm_run_aa", "lbm_macroscopic", "LBM_F64", "LBM_F32", "LBM_F16S",
     "LBM_LAYOUT_OSNT", "LBM_LAYOUT_AA_EVEN", "LBM_LAYOUT_AA_ODD", "LBM_TABLES_ADJ", "LBM_TABLES_RIA",
     "lbm_objective_flux", "lbm_adjoint_step", "lbm_ckpt_workspace_bytes", "lbm_flux_forward", "lbm_flux_backward",
-    "flux_objective", "new_adjoint",
+    "flux_objective", "new_adjoint", "lbm_macroscopic_noalloc",
 ]
