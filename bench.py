@@ -197,6 +197,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--box", type=int, default=None, help="smaller cubic bed (profiling only)")
+    ap.add_argument("--prec", default="f64", choices=["f64", "f64df", "f32", "f16s"],
+                    help="storage/arithmetic of the timed AA-R pair (the headline is f64)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -223,7 +225,8 @@ def main():
     setup_s = time.time() - t0
     N, R = lat.N, lat.R
     r = R / N
-    params = lbm.Params(omega_plus=w["omega_plus"], magic=w["magic"], g=w["g"])
+    hp = args.prec
+    params = lbm.Params(omega_plus=w["omega_plus"], magic=w["magic"], g=w["g"], shifted=hp in ("f32", "f16s"))
     stream = torch.cuda.current_stream(dev)
 
     def barrier():
@@ -232,7 +235,7 @@ def main():
         torch.cuda.synchronize(dev)
 
     # ---- headline: AA-R FP64, one even+odd pair per step ---------------------------------------------
-    solver = lbm.Solver(lat, "f64", params, form="aa", ria=True)
+    solver = lbm.Solver(lat, hp, params, form="aa", ria=True)
     solver.init_equilibrium(1.0)
     for _ in range(args.warmup):
         solver.step(2)
@@ -245,9 +248,9 @@ def main():
         start.record(stream)
         for k in range(K):
             ev[k][0].record(stream)
-            lbm.lbm_step_aa(lat, "f64", params, solver.pdf, 0, None, True)
+            lbm.lbm_step_aa(lat, hp, params, solver.pdf, 0, None, True)
             ev[k][1].record(stream)
-            lbm.lbm_step_aa(lat, "f64", params, solver.pdf, 1, None, True)
+            lbm.lbm_step_aa(lat, hp, params, solver.pdf, 1, None, True)
             ev[k][2].record(stream)
         stop.record(stream)
         barrier()
@@ -265,23 +268,28 @@ def main():
     mass = float(sums[0])
 
     hbm, hbm_kind = peaks()
-    p = 8
-    dom_ms, dom_name, dom_bl = (odd_ms, "aa_odd_ria_f64", loop_balance("aa_odd_r", p, r)) if odd_ms >= even_ms \
-        else (even_ms, "aa_even_f64", loop_balance("aa_even", p, r))
+    p = {"f64": 8, "f64df": 8, "f32": 4, "f16s": 2}[hp]
+    odd_dom = odd_ms >= even_ms
+    dom_ms = odd_ms if odd_dom else even_ms
+    dom_name = f"aa_{'odd_ria' if odd_dom else 'even'}_{hp}"
+    dom_bl = loop_balance("aa_odd_r" if odd_dom else "aa_even", p, r)
     achieved_gbs = dom_bl * N / (dom_ms / 1e3) / 1e9
-    dp_rate = COLL_DP_INSTR * N / (dom_ms / 1e3) / 1e9
-    roofline = {"kernel": dom_name, "bound": "alu", "achieved": dp_rate, "peak": FP64_PEAK_GINSTR,
-                "unit": "G FP64-instr/s", "frac": dp_rate / FP64_PEAK_GINSTR, "traffic": None,
-                "peak_kind": "FP64 pipe from unit counts: 152 SM x 2 DP lanes/clk x 2.07 GHz",
-                "dp_instr_per_node": COLL_DP_INSTR}
     roofline_hbm = {"kernel": dom_name, "bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved_gbs / hbm, "peak_kind": hbm_kind, "bytes_per_node": dom_bl,
+                    "frac": achieved_gbs / hbm, "traffic": None, "peak_kind": hbm_kind, "bytes_per_node": dom_bl,
                     "kernel_ms": {"even": even_ms, "odd": odd_ms}}
+    if hp == "f64":
+        dp_rate = COLL_DP_INSTR * N / (dom_ms / 1e3) / 1e9
+        roofline = {"kernel": dom_name, "bound": "alu", "achieved": dp_rate, "peak": FP64_PEAK_GINSTR,
+                    "unit": "G FP64-instr/s", "frac": dp_rate / FP64_PEAK_GINSTR, "traffic": None,
+                    "peak_kind": "FP64 pipe from unit counts: 152 SM x 2 DP lanes/clk x 2.07 GHz",
+                    "dp_instr_per_node": COLL_DP_INSTR}
+    else:
+        roofline = roofline_hbm
 
     # ---- end to end through host buffers: H2D state, one pair, D2H state -------------------------------
     e2e = None
     if rank == 0 or world > 1:
-        host = torch.empty((19, lat.Npad), dtype=torch.float64, pin_memory=True)
+        host = torch.empty((19, lat.Npad), dtype=solver.pdf.dtype, pin_memory=True)
         host.copy_(solver.pdf)
         Ke = max(3, K // 2)
         barrier()
@@ -289,13 +297,13 @@ def main():
         s0.record(stream)
         for _ in range(Ke):
             solver.pdf.copy_(host, non_blocking=True)
-            lbm.lbm_step_aa(lat, "f64", params, solver.pdf, 0, None, True)
-            lbm.lbm_step_aa(lat, "f64", params, solver.pdf, 1, None, True)
+            lbm.lbm_step_aa(lat, hp, params, solver.pdf, 0, None, True)
+            lbm.lbm_step_aa(lat, hp, params, solver.pdf, 1, None, True)
             host.copy_(solver.pdf, non_blocking=True)
         s1.record(stream)
         barrier()
         ems = s0.elapsed_time(s1)
-        nb = 19 * lat.Npad * 8
+        nb = 19 * lat.Npad * p
         e2e = {"value": world * 2 * N * Ke / (ems / 1e3) / 1e9, "unit": "GFLUP/s", "h2d_bytes_per_step": nb,
                "d2h_bytes_per_step": nb, "what": "per step: pinned-host -> device copy of the FP64 state, "
                                                  "AA even+odd, device -> pinned-host copy of the state"}
@@ -307,8 +315,9 @@ def main():
         del solver
         torch.cuda.empty_cache()
         Kv = max(4, K // 2)
-        for prec, pb in (("f64", 8), ("f32", 4), ("f16s", 2)):
-            vp = lbm.Params(omega_plus=w["omega_plus"], magic=w["magic"], g=w["g"], shifted=(prec != "f64"))
+        for prec, pb in (("f64", 8), ("f64df", 8), ("f32", 4), ("f16s", 2)):
+            vp = lbm.Params(omega_plus=w["omega_plus"], magic=w["magic"], g=w["g"],
+                            shifted=(prec in ("f32", "f16s")))
             for form, ria in (("osnt", False), ("osnt", True), ("aa", False), ("aa", True)):
                 name = f"{form}{'_r' if ria else ''}"
                 sv = lbm.Solver(lat, prec, vp, form=form, ria=ria)
@@ -339,10 +348,12 @@ def main():
             cpu = {"error": str(e)}
 
     line = {
-        "metric": "sparse D3Q19 TRT AA-R FP64 lattice updates per second",
+        "metric": "sparse D3Q19 TRT AA-R FP64 lattice updates per second" if hp == "f64"
+                  else f"sparse D3Q19 TRT AA-R lattice updates per second ({hp} storage)",
         "value": value, "unit": "GFLUP/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
+        "dtype": {"f64": "f64", "f64df": "f64 storage, f32-pair arithmetic", "f32": "f32",
+                  "f16s": "f16 storage, f32 arithmetic"}[hp], "data": "synthetic",
         "config": {"workload": WORKLOAD["name"] if not args.box else f"packed_bed_{args.box}_rsa_r12",
                    "box": [solid.shape[2], solid.shape[1], solid.shape[0]], "fluid_nodes": N, "runs": R,
                    "r": r, "porosity": geometry.porosity(solid), "enumeration": "lex B=1",

@@ -28,8 +28,8 @@
  *    17 (0,1,-1) 18 (0,-1,1).  The opposite of 2k-1 is 2k.
  *  - PDF arrays are structure-of-arrays: element (i, n) of a grid lives at
  *    pdf[i * Npad + n], Npad = N rounded up to a multiple of 128.  The element
- *    type is double (LBM_F64), float (LBM_F32) or a 16-bit IEEE half
- *    (LBM_F16S).  With params->shifted the stored value is f_i - w_i * rho0
+ *    type is double (LBM_F64 and LBM_F64_DF), float (LBM_F32) or a 16-bit
+ *    IEEE half (LBM_F16S).  With params->shifted the stored value is f_i - w_i * rho0
  *    (LBM_F16S always stores half((f_i - w_i rho0) * f16_scale)).
  *  - "Canonical" state F[i][n]: the pre-collision PDFs after the last step,
  *    FP64, unshifted, dense [19][N].
@@ -70,6 +70,11 @@ extern "C" {
 #define LBM_F64 0            /* double storage, double collision                     */
 #define LBM_F32 1            /* float storage, float collision                       */
 #define LBM_F16S 2           /* half storage of (f - w rho0) * f16_scale, float math */
+#define LBM_F64_DF 3         /* double storage (same grids as LBM_F64); the step's
+                                collision runs in double-float arithmetic (pairs of
+                                floats, ~48 bits) on the FP32 pipe.  Only the step
+                                kernels differ; every other call treats the grid as
+                                LBM_F64. */
 
 #define LBM_LAYOUT_OSNT 0
 #define LBM_LAYOUT_AA_EVEN 1
@@ -262,8 +267,9 @@ LBM_API int lbm_macroscopic_noalloc(const lbm_lattice* lat, int prec, const lbm_
 /* None of these has a counterpart in the paper: they differentiate the step of
  * Eq. 1 (TRT collision, Sect. 2; pull streaming, Sect. 4) with respect to the
  * per-node Brinkman solid fraction s.  The adjoint arrays ("lambda") have the
- * grid layout [19][Npad] and element type double for LBM_F64, float for
- * LBM_F32 and LBM_F16S. */
+ * grid layout [19][Npad] and element type double for LBM_F64 / LBM_F64_DF,
+ * float for LBM_F32 and LBM_F16S (the adjoint step itself always runs in the
+ * element type's native arithmetic). */
 
 /* Mean x-momentum objective J = (1/N) sum_n rho_n u_x,n of the canonical state
  * of `pdf` (compensated FP64 sum) written to J (device double[1]).  Optional

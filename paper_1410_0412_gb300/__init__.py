@@ -17,13 +17,13 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _lib
-from ._lib import (LBM_ENUM_HILBERT, LBM_ENUM_LEX, LBM_F16S, LBM_F32, LBM_F64, LBM_LAYOUT_AA_EVEN,
+from ._lib import (LBM_ENUM_HILBERT, LBM_ENUM_LEX, LBM_F16S, LBM_F32, LBM_F64, LBM_F64_DF, LBM_LAYOUT_AA_EVEN,
                    LBM_LAYOUT_AA_ODD, LBM_LAYOUT_OSNT, LBM_TABLES_ADJ, LBM_TABLES_RIA, LbmError, check)
 
 _lib.load()
 
-PRECISIONS = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S}
-BYTES_PER_PDF = {LBM_F64: 8, LBM_F32: 4, LBM_F16S: 2}
+PRECISIONS = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S, "f64df": LBM_F64_DF}
+BYTES_PER_PDF = {LBM_F64: 8, LBM_F32: 4, LBM_F16S: 2, LBM_F64_DF: 8}
 
 
 def _torch():
@@ -33,7 +33,7 @@ def _torch():
 
 def _dtype(prec):
     torch = _torch()
-    return {LBM_F64: torch.float64, LBM_F32: torch.float32, LBM_F16S: torch.float16}[prec]
+    return {LBM_F64: torch.float64, LBM_F32: torch.float32, LBM_F16S: torch.float16, LBM_F64_DF: torch.float64}[prec]
 
 
 def _prec(prec) -> int:
@@ -297,7 +297,7 @@ def lbm_macroscopic_noalloc(lat, prec, params, pdf, layout, s=None, rho=None, u=
 
 def _adjoint_dtype(prec):
     torch = _torch()
-    return torch.float64 if prec == LBM_F64 else torch.float32
+    return torch.float64 if prec in (LBM_F64, LBM_F64_DF) else torch.float32
 
 
 def new_adjoint(lat, prec, device="cuda"):
@@ -458,7 +458,7 @@ class Solver:
 
 __all__ = [
     "Params", "Lattice", "Solver", "LbmError", "lbm_init_equilibrium", "lbm_load_canonical", "lbm_canonical_pdfs",
-    "lbm_step_osnt", "lbm_step_aa", "lbm_run_aa", "lbm_macroscopic", "LBM_F64", "LBM_F32", "LBM_F16S",
+    "lbm_step_osnt", "lbm_step_aa", "lbm_run_aa", "lbm_macroscopic", "LBM_F64", "LBM_F32", "LBM_F16S", "LBM_F64_DF",
     "LBM_LAYOUT_OSNT", "LBM_LAYOUT_AA_EVEN", "LBM_LAYOUT_AA_ODD", "LBM_TABLES_ADJ", "LBM_TABLES_RIA",
     "lbm_objective_flux", "lbm_adjoint_step", "lbm_ckpt_workspace_bytes", "lbm_flux_forward", "lbm_flux_backward",
     "flux_objective", "new_adjoint", "lbm_macroscopic_noalloc",

@@ -24,6 +24,7 @@ LBM_ENUM_HILBERT = 1
 LBM_F64 = 0
 LBM_F32 = 1
 LBM_F16S = 2
+LBM_F64_DF = 3
 LBM_LAYOUT_OSNT = 0
 LBM_LAYOUT_AA_EVEN = 1
 LBM_LAYOUT_AA_ODD = 2

@@ -55,14 +55,13 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(DevTables t, KParams kp, Col
                                                     typename St<PREC>::R* __restrict__ lam,
                                                     const float* __restrict__ s, double* __restrict__ grad_s, int N) {
   using R = typename St<PREC>::R;
-  __shared__ int s_rs[kBlock + 1];
+  using ::fma;
   const int n0 = blockIdx.x * kBlock;
   const int n = n0 + threadIdx.x;
   int m[18];
   if (RIA) {
-    RiaCursor cur = ria_locate(t, n0, n, N, s_rs);
     if (n >= N) return;
-    nbr_ria(t, cur, m);
+    nbr_ria(t, ria_locate(t, n), m);
   } else {
     if (n >= N) return;
     nbr_adj(t, n, m);
@@ -202,19 +201,19 @@ __device__ __forceinline__ void block_sum_dd(double& hi, double& lo, double (*s_
 
 // J partial sums of rho u_x (compensated), optional dJ/dF_T and the direct dJ/ds.
 template <int PREC, bool RIA>
-__global__ void __launch_bounds__(kBlock) k_objective(DevTables t, KParams kp, const typename St<PREC>::T* pdf,
-                                                      int layout, const float* __restrict__ s, double invN,
+__global__ void __launch_bounds__(kBlock) k_objective(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
+                                                      const typename St<PREC>::T* pdf, int layout,
+                                                      const float* __restrict__ s, double invN,
                                                       double* __restrict__ partials,
                                                       typename St<PREC>::R* __restrict__ lamT,
                                                       double* __restrict__ grad_s, int N) {
   using R = typename St<PREC>::R;
-  __shared__ int s_rs[kBlock + 1];
   __shared__ double s_red[kBlock / 32][2];
   const int n0 = blockIdx.x * kBlock;
   const int n = n0 + threadIdx.x;
   double f[kQ];
   double hi = 0.0, lo = 0.0;
-  if (node_canonical<PREC, RIA>(t, kp, pdf, layout, n0, n, N, s_rs, f)) {
+  if (node_canonical<PREC, RIA>(t, kp, c, pdf, layout, n, N, f)) {
     double r = 0.0, jx = 0.0;
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
@@ -288,13 +287,14 @@ int launch_objective_t(const lbm_lattice* L, const KParams& kp, const void* pdf,
   const double invN = L->N > 0 ? 1.0 / double(L->N) : 0.0;
   if (L->N > 0) {
     const bool ria = !(L->uploaded & LBM_TABLES_ADJ);
+    const auto c = dev::make_coll<R>(kp);
     if (ria)
       dev::k_objective<PREC, true><<<grid_of(L->N), dev::kBlock, 0, st>>>(
-          L->dev, kp, static_cast<const T*>(pdf), layout, s, invN, partials, static_cast<R*>(lamT), grad_s,
+          L->dev, kp, c, static_cast<const T*>(pdf), layout, s, invN, partials, static_cast<R*>(lamT), grad_s,
           int(L->N));
     else
       dev::k_objective<PREC, false><<<grid_of(L->N), dev::kBlock, 0, st>>>(
-          L->dev, kp, static_cast<const T*>(pdf), layout, s, invN, partials, static_cast<R*>(lamT), grad_s,
+          L->dev, kp, c, static_cast<const T*>(pdf), layout, s, invN, partials, static_cast<R*>(lamT), grad_s,
           int(L->N));
     if (int rc = cuda_check("objective launch")) return rc;
   }

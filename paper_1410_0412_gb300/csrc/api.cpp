@@ -30,7 +30,7 @@ int make_kparams(const lbm_params* p, int prec, KParams* kp) {
     if (!std::isfinite(p->g[a])) return set_error(LBM_ERR_ARG, "g must be finite");
   if (!std::isfinite(p->rho0) || !std::isfinite(p->rho_in) || !std::isfinite(p->rho_out))
     return set_error(LBM_ERR_ARG, "densities must be finite");
-  if (prec < LBM_F64 || prec > LBM_F16S) return set_error(LBM_ERR_ARG, "unknown precision");
+  if (prec < LBM_F64 || prec > LBM_F64_DF) return set_error(LBM_ERR_ARG, "unknown precision");
   if (prec == LBM_F16S && !p->shifted)
     return set_error(LBM_ERR_ARG, "LBM_F16S stores shifted values: set params.shifted");
   if (prec == LBM_F16S && !(p->f16_scale > 0.0 && std::isfinite(p->f16_scale)))
@@ -57,7 +57,7 @@ namespace {
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct TableLayout {
-  size_t adj = 0, run_start = 0, run_adj = 0, tile_run0 = 0, total = 0;
+  size_t adj = 0, run_adj = 0, head_bits = 0, warp_run0 = 0, warp_head0 = 0, total = 0;
 };
 
 TableLayout table_layout(const lbm_lattice* L, int which) {
@@ -68,12 +68,14 @@ TableLayout table_layout(const lbm_lattice* L, int which) {
     off = align256(off + size_t(18) * L->Npad * 4);
   }
   if (which & LBM_TABLES_RIA) {
-    t.run_start = off;
-    off = align256(off + size_t(L->R + 1) * 4);
     t.run_adj = off;
     off = align256(off + size_t(18) * L->Rpad * 4);
-    t.tile_run0 = off;
-    off = align256(off + size_t(L->ntiles + 1) * 4);
+    t.head_bits = off;
+    off = align256(off + size_t(std::max<int64_t>(L->nwarps, 1)) * 4);
+    t.warp_run0 = off;
+    off = align256(off + size_t(std::max<int64_t>(L->nwarps, 1)) * 4);
+    t.warp_head0 = off;
+    off = align256(off + size_t(std::max<int64_t>(L->nwarps, 1)) * 4);
   }
   t.total = off;
   return t;
@@ -235,20 +237,24 @@ int lbm_lattice_upload(lbm_lattice* L, int which, void* dev, size_t bytes, void*
     L->dev.adj = reinterpret_cast<const int32_t*>(base + t.adj);
   }
   if (which & LBM_TABLES_RIA) {
-    e = cudaMemcpyAsync(base + t.run_start, L->run_start.data(), L->run_start.size() * 4, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(base + t.run_adj, L->run_adj.data(), L->run_adj.size() * 4, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(base + t.tile_run0, L->tile_run0.data(), L->tile_run0.size() * 4, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(base + t.run_adj, L->run_adj.data(), L->run_adj.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && L->nwarps > 0)
+      e = cudaMemcpyAsync(base + t.head_bits, L->head_bits.data(), L->head_bits.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && L->nwarps > 0)
+      e = cudaMemcpyAsync(base + t.warp_run0, L->warp_run0.data(), L->warp_run0.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && L->nwarps > 0)
+      e = cudaMemcpyAsync(base + t.warp_head0, L->warp_head0.data(), L->warp_head0.size() * 4, cudaMemcpyHostToDevice,
+                          st);
     if (e != cudaSuccess) return set_error(LBM_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
-    L->dev.run_start = reinterpret_cast<const int32_t*>(base + t.run_start);
     L->dev.run_adj = reinterpret_cast<const int32_t*>(base + t.run_adj);
-    L->dev.tile_run0 = reinterpret_cast<const int32_t*>(base + t.tile_run0);
+    L->dev.head_bits = reinterpret_cast<const uint32_t*>(base + t.head_bits);
+    L->dev.warp_run0 = reinterpret_cast<const int32_t*>(base + t.warp_run0);
+    L->dev.warp_head0 = reinterpret_cast<const int32_t*>(base + t.warp_head0);
   }
   L->dev.Npad = L->Npad;
   L->dev.Rpad = L->Rpad;
   L->dev.R = L->R;
-  L->dev.ntiles = L->ntiles;
+  L->dev.nwarps = L->nwarps;
   L->uploaded = which;
   return LBM_OK;
 }
@@ -256,7 +262,7 @@ int lbm_lattice_upload(lbm_lattice* L, int which, void* dev, size_t bytes, void*
 int lbm_pdf_bytes(const lbm_lattice* L, int prec, size_t* bytes) {
   if (int rc = check_lat(L)) return rc;
   if (!bytes) return set_error(LBM_ERR_ARG, "bytes is NULL");
-  size_t el = prec == LBM_F64 ? 8 : prec == LBM_F32 ? 4 : prec == LBM_F16S ? 2 : 0;
+  size_t el = (prec == LBM_F64 || prec == LBM_F64_DF) ? 8 : prec == LBM_F32 ? 4 : prec == LBM_F16S ? 2 : 0;
   if (!el) return set_error(LBM_ERR_ARG, "unknown precision");
   *bytes = size_t(19) * L->Npad * el;
   return LBM_OK;
@@ -314,7 +320,7 @@ int lbm_step_osnt(const lbm_lattice* L, int prec, const lbm_params* params, cons
   if (src == dst) return set_error(LBM_ERR_ARG, "OS-NT needs two distinct grids");
   if (L->N == 0) return LBM_OK;
   if (int rc = check_tables(L, ria)) return rc;
-  return LBM_DISPATCH(prec, launch_osnt_t, L, kp, src, dst, s, ria ? 1 : 0, stream);
+  return LBM_DISPATCH_STEP(prec, launch_osnt_t, L, kp, src, dst, s, ria ? 1 : 0, stream);
 }
 
 int lbm_step_aa(const lbm_lattice* L, int prec, const lbm_params* params, void* pdf, int parity, const float* s,
@@ -327,7 +333,7 @@ int lbm_step_aa(const lbm_lattice* L, int prec, const lbm_params* params, void* 
   if (L->N == 0) return LBM_OK;
   if (parity == 1)
     if (int rc = check_tables(L, ria)) return rc;
-  return LBM_DISPATCH(prec, launch_aa_t, L, kp, pdf, parity, s, ria ? 1 : 0, stream);
+  return LBM_DISPATCH_STEP(prec, launch_aa_t, L, kp, pdf, parity, s, ria ? 1 : 0, stream);
 }
 
 int lbm_run_aa(const lbm_lattice* L, int prec, const lbm_params* params, void* pdf, int start_parity, int steps,
@@ -342,7 +348,7 @@ int lbm_run_aa(const lbm_lattice* L, int prec, const lbm_params* params, void* p
   if (steps > 1 || start_parity == 1)
     if (int rc = check_tables(L, ria)) return rc;
   for (int t = 0; t < steps; ++t)
-    if (int rc = LBM_DISPATCH(prec, launch_aa_t, L, kp, pdf, (start_parity + t) & 1, s, ria ? 1 : 0, stream))
+    if (int rc = LBM_DISPATCH_STEP(prec, launch_aa_t, L, kp, pdf, (start_parity + t) & 1, s, ria ? 1 : 0, stream))
       return rc;
   return LBM_OK;
 }
@@ -419,8 +425,9 @@ struct CkptLayout {
 
 CkptLayout ckpt_layout(const lbm_lattice* L, int prec, int T, int K) {
   CkptLayout c;
-  const size_t el = prec == LBM_F64 ? 8 : prec == LBM_F32 ? 4 : 2;
-  const size_t lel = prec == LBM_F64 ? 8 : 4;
+  const bool f64 = prec == LBM_F64 || prec == LBM_F64_DF;
+  const size_t el = f64 ? 8 : prec == LBM_F32 ? 4 : 2;
+  const size_t lel = f64 ? 8 : 4;
   c.grid = align256(size_t(19) * L->Npad * el);
   c.lam = align256(size_t(19) * L->Npad * lel);
   c.nck = T > 0 ? (T + K - 1) / K : 1;
@@ -445,7 +452,7 @@ CkptLayout ckpt_layout(const lbm_lattice* L, int prec, int T, int K) {
 int check_ckpt_args(const lbm_lattice* L, int prec, int T, int K, void* ws, size_t ws_bytes, CkptLayout* out) {
   if (T < 0) return set_error(LBM_ERR_ARG, "T must be >= 0");
   if (K < 1) return set_error(LBM_ERR_ARG, "K must be >= 1");
-  if (prec < LBM_F64 || prec > LBM_F16S) return set_error(LBM_ERR_ARG, "unknown precision");
+  if (prec < LBM_F64 || prec > LBM_F64_DF) return set_error(LBM_ERR_ARG, "unknown precision");
   *out = ckpt_layout(L, prec, T, K);
   if (!ws || ws_bytes < out->total) return set_error(LBM_ERR_ARG, "checkpoint workspace missing or too small");
   if (reinterpret_cast<uintptr_t>(ws) % 256) return set_error(LBM_ERR_ARG, "workspace not 256-byte aligned");
@@ -460,7 +467,7 @@ int lbm_ckpt_workspace_bytes(const lbm_lattice* L, int prec, int T, int K, size_
   if (int rc = check_lat(L)) return rc;
   if (!bytes) return set_error(LBM_ERR_ARG, "bytes is NULL");
   if (T < 0 || K < 1) return set_error(LBM_ERR_ARG, "T must be >= 0 and K >= 1");
-  if (prec < LBM_F64 || prec > LBM_F16S) return set_error(LBM_ERR_ARG, "unknown precision");
+  if (prec < LBM_F64 || prec > LBM_F64_DF) return set_error(LBM_ERR_ARG, "unknown precision");
   *bytes = ckpt_layout(L, prec, T, K).total;
   return LBM_OK;
 }
@@ -488,7 +495,7 @@ int lbm_flux_forward(const lbm_lattice* L, int prec, const lbm_params* params, c
       dst = base + c.ck + c.grid * ((t + 1) / K);
     else
       dst = base + c.seg + c.grid * ((t + 1) % 2);
-    if (int rc = LBM_DISPATCH(prec, launch_osnt_t, L, kp, cur, dst, s, ria ? 1 : 0, stream)) return rc;
+    if (int rc = LBM_DISPATCH_STEP(prec, launch_osnt_t, L, kp, cur, dst, s, ria ? 1 : 0, stream)) return rc;
     cur = dst;
   }
   if (T == 0) {
@@ -525,8 +532,8 @@ int lbm_flux_backward(const lbm_lattice* L, int prec, const lbm_params* params, 
                      : static_cast<const void*>(base + c.seg + c.grid * (t - t0 - 1));
     };
     for (int t = t0; t + 1 < t1; ++t)
-      if (int rc = LBM_DISPATCH(prec, launch_osnt_t, L, kp, state(t), const_cast<void*>(state(t + 1)), s,
-                                ria ? 1 : 0, stream))
+      if (int rc = LBM_DISPATCH_STEP(prec, launch_osnt_t, L, kp, state(t), const_cast<void*>(state(t + 1)), s,
+                                     ria ? 1 : 0, stream))
         return rc;
     for (int t = t1 - 1; t >= t0; --t) {
       if (int rc = LBM_DISPATCH(prec, launch_adjoint_t, L, kp, state(t), lamA, lamB, s, grad_s, ria ? 1 : 0, stream))
@@ -535,7 +542,7 @@ int lbm_flux_backward(const lbm_lattice* L, int prec, const lbm_params* params, 
     }
   }
   if (lambda_0) {
-    cudaError_t e = cudaMemcpyAsync(lambda_0, lamA, size_t(19) * L->Npad * (prec == LBM_F64 ? 8 : 4),
+    cudaError_t e = cudaMemcpyAsync(lambda_0, lamA, size_t(19) * L->Npad * ((prec == LBM_F64 || prec == LBM_F64_DF) ? 8 : 4),
                                     cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return set_error(LBM_ERR_CUDA, std::string("copy: ") + cudaGetErrorString(e));
   }

@@ -22,18 +22,20 @@ constexpr int kInv[kQ] = {0, 2, 1, 4, 3, 6, 5, 8, 7, 10, 9, 12, 11, 14, 13, 16, 
 // Node-count padding of every SoA direction array; 128 nodes keep each
 // direction of an FP16 grid 256-byte aligned.
 constexpr int64_t kPad = 128;
-// Node tile of the RIA run index: tile_run0[t] is the run holding node t*kTile.
-constexpr int kTile = 128;
+// RIA lookup granularity: one 32-bit run-head mask and one run index per 32
+// consecutive nodes (a warp's worth).
+constexpr int kWarpNodes = 32;
 
 inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
 // Device addresses of the uploaded tables (all inside one caller buffer).
 struct DevTables {
-  const int32_t* adj = nullptr;        // [18][Npad]
-  const int32_t* run_start = nullptr;  // [R+1]
-  const int32_t* run_adj = nullptr;    // [18][Rpad]
-  const int32_t* tile_run0 = nullptr;  // [ntiles+1]
-  int64_t Npad = 0, Rpad = 0, R = 0, ntiles = 0;
+  const int32_t* adj = nullptr;         // [18][Npad]
+  const int32_t* run_adj = nullptr;     // [18][Rpad]   adjacency entries of each run's first node
+  const uint32_t* head_bits = nullptr;  // [nwarps]     bit j of word w: node 32w+j starts a run
+  const int32_t* warp_run0 = nullptr;   // [nwarps]     run holding node 32w
+  const int32_t* warp_head0 = nullptr;  // [nwarps]     first node of that run
+  int64_t Npad = 0, Rpad = 0, R = 0, nwarps = 0;
 };
 
 }  // namespace lbm
@@ -42,12 +44,14 @@ struct lbm_lattice {
   int X = 0, Y = 0, Z = 0;
   lbm_bc bc{};
   int enumeration = 0, block_B = 1;
-  int64_t N = 0, Npad = 0, R = 0, Rpad = 0, ntiles = 0;
+  int64_t N = 0, Npad = 0, R = 0, Rpad = 0, nwarps = 0;
   std::vector<int32_t> node_xyz;   // [N][3]
   std::vector<int32_t> adj;        // [18][Npad], padding = -1
   std::vector<int32_t> run_start;  // [R+1]
   std::vector<int32_t> run_adj;    // [18][Rpad], padding = -1
-  std::vector<int32_t> tile_run0;  // [ntiles+1]
+  std::vector<uint32_t> head_bits; // [nwarps]  run heads, one bit per node
+  std::vector<int32_t> warp_run0;  // [nwarps]  run holding node 32w
+  std::vector<int32_t> warp_head0; // [nwarps]  first node of that run
   int64_t hist[33] = {0};
   int uploaded = 0;                // LBM_TABLES_* bits present on the device
   lbm::DevTables dev;
@@ -102,11 +106,15 @@ template <int PREC>
 int launch_objective_t(const lbm_lattice* L, const KParams& kp, const void* pdf, int layout, const float* s,
                        double* J, void* lamT, double* grad_s, double* partials, void* stream);
 
-// Precision dispatch: call F<LBM_F64 | LBM_F32 | LBM_F16S>.
-#define LBM_DISPATCH(prec, fn, ...)                                   \
-  ((prec) == LBM_F64 ? fn<LBM_F64>(__VA_ARGS__)                       \
-   : (prec) == LBM_F32 ? fn<LBM_F32>(__VA_ARGS__)                     \
+// Precision dispatch: call F<LBM_F64 | LBM_F32 | LBM_F16S>.  LBM_F64_DF grids
+// are IEEE double grids: everything but the step kernels treats them as LBM_F64.
+#define LBM_DISPATCH(prec, fn, ...)                                        \
+  (((prec) == LBM_F64 || (prec) == LBM_F64_DF) ? fn<LBM_F64>(__VA_ARGS__)  \
+   : (prec) == LBM_F32 ? fn<LBM_F32>(__VA_ARGS__)                          \
                        : fn<LBM_F16S>(__VA_ARGS__))
+// Step kernels: the double-float arithmetic has its own instantiation.
+#define LBM_DISPATCH_STEP(prec, fn, ...)                                   \
+  ((prec) == LBM_F64_DF ? fn<LBM_F64_DF>(__VA_ARGS__) : LBM_DISPATCH(prec, fn, __VA_ARGS__))
 
 // Number of per-CTA partial sums of the reductions (one per 128-node CTA).
 inline int64_t reduce_parts(const lbm_lattice* L) { return std::max<int64_t>(1, (L->N + 127) / 128); }

@@ -7,6 +7,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "df32.cuh"
 #include "internal.h"
 
 namespace lbm {
@@ -32,7 +33,8 @@ __host__ __device__ constexpr int wclass(int i) { return i == 0 ? 0 : (i <= 6 ? 
 __host__ __device__ constexpr double wgt(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
 
 constexpr int kBlock = 128;  // nodes per CTA of the step kernels (one node per thread)
-static_assert(kBlock % kTile == 0, "CTA must cover whole RIA tiles");
+constexpr int kMinCtas = 5;  // step kernels: keep <= 102 registers so 5 CTAs (20 warps) fit per SM
+static_assert(kBlock % kWarpNodes == 0, "a warp must cover one run-index group");
 
 // ---- storage traits -----------------------------------------------------------------
 // Value stored for PDF i: f_i - w_i rho_s (rho_s = 0 when unshifted), in the
@@ -45,6 +47,15 @@ template <> struct St<LBM_F64> {
   static __device__ __forceinline__ R ld(const T* p, float) { return __ldg(p); }
   static __device__ __forceinline__ void st(T* p, R v, float) { *p = v; }
   static __device__ __forceinline__ void st_stream(T* p, R v, float) { __stcs(p, v); }
+};
+
+// IEEE double storage, double-float (FP32-pair) arithmetic.
+template <> struct St<LBM_F64_DF> {
+  using T = double;
+  using R = df;
+  static __device__ __forceinline__ R ld(const T* p, float) { return df_from_double(__ldg(p)); }
+  static __device__ __forceinline__ void st(T* p, R v, float) { *p = double_from_df(v); }
+  static __device__ __forceinline__ void st_stream(T* p, R v, float) { __stcs(p, double_from_df(v)); }
 };
 
 template <> struct St<LBM_F32> {
@@ -75,35 +86,46 @@ __device__ __forceinline__ void nbr_adj(const DevTables& t, int n, int (&m)[18])
   for (int i = 0; i < 18; ++i) m[i] = __ldg(t.adj + size_t(i) * t.Npad + n);
 }
 
-// RIA form (Sect. 4.1): the CTA loads the starts of the runs overlapping its
-// node range into shared memory; each thread finds its run by binary search
-// and rebuilds its entries from the run head's (a + offset for fluid sources,
-// the marker itself otherwise).  Threads of one run read the same head entry,
-// so only runs cost index bytes.  Must be called by all threads of the CTA.
+// RIA form (Sect. 4.1), warp-level: the run-length coding is held as one run
+// head bit per node plus, per 32 nodes, the run holding the first of them and
+// that run's first node.  A lane counts the heads at or below it in its warp's
+// mask (popc) to get its run, and the highest such head (clz) gives the run's
+// first node; every lane of a run then rebuilds its 18 entries from the head's
+// (a + offset for fluid sources, the marker itself otherwise).  Lanes of one
+// run read the same head entry, so only runs cost index bytes.
 struct RiaCursor {
   int r;     // run of this thread's node
   int off;   // node - first node of the run
 };
 
-__device__ __forceinline__ RiaCursor ria_locate(const DevTables& t, int n0, int n, int N, int* s_rs) {
-  const int t0 = n0 / kTile;
-  const int t1 = min(int64_t((n0 + kBlock) / kTile), t.ntiles);
-  const int r0 = __ldg(t.tile_run0 + t0);
-  const int r1 = __ldg(t.tile_run0 + t1);
-  const int cnt = r1 - r0 + 1;  // <= kBlock + 1 runs overlap [n0, n0 + kBlock]
-  for (int j = threadIdx.x; j < cnt; j += kBlock) s_rs[j] = __ldg(t.run_start + r0 + j);
-  __syncthreads();
-  RiaCursor c{r0, 0};
-  if (n < N) {
-    int lo = 0, hi = cnt - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (s_rs[mid] <= n) lo = mid; else hi = mid - 1;
-    }
-    c.r = r0 + lo;
-    c.off = n - s_rs[lo];
-  }
+__device__ __forceinline__ RiaCursor ria_locate(const DevTables& t, int n) {
+  const int w = n >> 5;
+  const unsigned lane = unsigned(n) & 31u;
+  const unsigned bits = __ldg(t.head_bits + w);
+  const unsigned le = bits & (0xffffffffu >> (31u - lane));  // heads at lanes 0..lane
+  RiaCursor c;
+  c.r = __ldg(t.warp_run0 + w) + __popc(le) - int(bits & 1u);
+  const int head = le ? (w << 5) + (31 - __clz(le)) : __ldg(t.warp_head0 + w);
+  c.off = n - head;
   return c;
+}
+
+// One adjacency entry re-read after the collision, so that the 18 entries need
+// not stay in registers across it (the volatile load is never merged with the
+// first read; it hits L1).
+__device__ __forceinline__ int ld_index_again(const int32_t* p) {
+  int v;
+  asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
+template <bool RIA>
+__device__ __forceinline__ int nbr_again(const DevTables& t, RiaCursor c, int n, int i) {
+  if (RIA) {
+    const int a = ld_index_again(t.run_adj + size_t(i) * t.Rpad + c.r);
+    return a >= 0 ? a + c.off : a;
+  }
+  return ld_index_again(t.adj + size_t(i) * t.Npad + n);
 }
 
 __device__ __forceinline__ void nbr_ria(const DevTables& t, RiaCursor c, int (&m)[18]) {
@@ -132,11 +154,12 @@ template <class R> struct CollConst {
   R k2;       // 3 l- / 18 = l-/6   (K2 of the axis class, times rho)
   R fs;       // 9 a+ / 18 = a+/2   (axis-class scale of F in S+)
   R fo;       // 3 a- / 18 = a-/6   (axis-class scale of F in S-)
+  R omlp;     // 1 - l+
   R rho_s;
   R abb_in[2], abb_out[2];  // 2 w (rho_bc - rho_s) for w = 1/18 and 1/36
 };
 
-template <class R> __host__ __device__ inline CollConst<R> make_coll(const KParams& kp) {
+template <class R> inline CollConst<R> make_coll(const KParams& kp) {
   CollConst<R> c;
   const double ap = 1.0 - kp.lp / 2, am = 1.0 - kp.lm / 2;
   c.lp = R(kp.lp);
@@ -152,6 +175,7 @@ template <class R> __host__ __device__ inline CollConst<R> make_coll(const KPara
   c.k2 = R(kp.lm / 6.0);
   c.fs = R(ap / 2.0);
   c.fo = R(am / 6.0);
+  c.omlp = R(1.0 - kp.lp);
   c.rho_s = R(kp.rho_s);
   for (int k = 0; k < 2; ++k) {
     const double w = k == 0 ? 1.0 / 18.0 : 1.0 / 36.0;
@@ -176,6 +200,7 @@ __device__ __forceinline__ void coll_pair(R (&d)[kQ], const R sa, const R da, co
                                           const R K0, const R K1, const R K2, const R Fsx, const R Fsy,
                                           const R Fsz, const R Fox, const R Foy, const R Foz, const R qp,
                                           const R qm) {
+  using ::fma;
   constexpr int a = 2 * K - 1, b = 2 * K;
   const R cu = cdot<R, cx(a), cy(a), cz(a)>(ux, uy, uz);
   R t, o;
@@ -198,6 +223,7 @@ __device__ __forceinline__ void coll_pair(R (&d)[kQ], const R sa, const R da, co
 // s: Brinkman solid fraction of the node (DRAG only).
 template <class R, bool FORCE, bool DRAG>
 __device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const R s) {
+  using ::fma;
   R sa[10], da[10];
 #pragma unroll
   for (int k = 1; k <= 9; ++k) {
@@ -213,13 +239,13 @@ __device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const
   const R jy = da[2] + da[4] - da[5] + da[8] + da[9];
   const R jz = da[3] + da[6] - da[7] + da[8] - da[9];
   const R rho = c.rho_s + drho;
-  const R irho = R(1) / rho;
+  const R irho = recip(rho);
   R ux = fma(jx, irho, c.hg[0]);
   R uy = fma(jy, irho, c.hg[1]);
   R uz = fma(jz, irho, c.hg[2]);
   R Fx = R(0), Fy = R(0), Fz = R(0);
   if (DRAG) {
-    const R kd = R(1) / (R(1) + R(0.5) * s);
+    const R kd = recip(R(1) + half(s));
     ux *= kd;
     uy *= kd;
     uz *= kd;
@@ -233,7 +259,7 @@ __device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const
     Fz = rho * c.g[2];
   }
   const R uu = fma(ux, ux, fma(uy, uy, uz * uz));
-  const R base = fma(R(-1.5) * rho, uu, drho);  // drho - 3/2 rho u.u
+  const R base = fma(-1.5f * rho, uu, drho);  // drho - 3/2 rho u.u
   R K0a;                                      // axis-class K0 = w (l+ base - 3 a+ u.F)
   R Fsx = R(0), Fsy = R(0), Fsz = R(0), Fox = R(0), Foy = R(0), Foz = R(0);
   if (FORCE || DRAG) {
@@ -249,15 +275,15 @@ __device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const
     K0a = c.k0a * base;
   }
   const R K1a = c.k1 * rho, K2a = c.k2 * rho;
-  const R K0b = R(0.5) * K0a, K1b = R(0.5) * K1a, K2b = R(0.5) * K2a;
+  const R K0b = half(K0a), K1b = half(K1a), K2b = half(K2a);
   constexpr bool F = FORCE || DRAG;
   // axis pairs (weight 1/18)
   coll_pair<R, F, 1>(d, sa[1], da[1], ux, uy, uz, K0a, K1a, K2a, Fsx, Fsy, Fsz, Fox, Foy, Foz, c.qp, c.qm);
   coll_pair<R, F, 2>(d, sa[2], da[2], ux, uy, uz, K0a, K1a, K2a, Fsx, Fsy, Fsz, Fox, Foy, Foz, c.qp, c.qm);
   coll_pair<R, F, 3>(d, sa[3], da[3], ux, uy, uz, K0a, K1a, K2a, Fsx, Fsy, Fsz, Fox, Foy, Foz, c.qp, c.qm);
   // diagonal pairs (weight 1/36): every class constant halves
-  const R hFsx = R(0.5) * Fsx, hFsy = R(0.5) * Fsy, hFsz = R(0.5) * Fsz;
-  const R hFox = R(0.5) * Fox, hFoy = R(0.5) * Foy, hFoz = R(0.5) * Foz;
+  const R hFsx = half(Fsx), hFsy = half(Fsy), hFsz = half(Fsz);
+  const R hFox = half(Fox), hFoy = half(Foy), hFoz = half(Foz);
   coll_pair<R, F, 4>(d, sa[4], da[4], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
   coll_pair<R, F, 5>(d, sa[5], da[5], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
   coll_pair<R, F, 6>(d, sa[6], da[6], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
@@ -265,7 +291,7 @@ __device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const
   coll_pair<R, F, 8>(d, sa[8], da[8], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
   coll_pair<R, F, 9>(d, sa[9], da[9], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
   // rest PDF: p0 = (1 - l+) d0 + w0 (l+ base - 3 a+ u.F), w0 = 6 w_axis
-  d[0] = fma(R(2) * c.qp, d[0], R(6) * K0a);
+  d[0] = fma(c.omlp, d[0], 6.0f * K0a);
 }
 
 // ---- PDF gathers of the storage layouts ----------------------------------------------
@@ -295,19 +321,17 @@ __device__ __forceinline__ void gather(const typename St<PREC>::T* g, int64_t Np
 // OS-NT step: pull (indirect) from src, collide, store locally into dst with
 // evict-first stores so the write stream does not push src out of L2.
 template <int PREC, bool RIA, bool FORCE, bool DRAG>
-__global__ void __launch_bounds__(kBlock) k_osnt(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
+__global__ void __launch_bounds__(kBlock, kMinCtas) k_osnt(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
                                                  const typename St<PREC>::T* __restrict__ src,
                                                  typename St<PREC>::T* __restrict__ dst, const float* __restrict__ s,
                                                  int N) {
   using R = typename St<PREC>::R;
-  __shared__ int s_rs[kBlock + 1];
   const int n0 = blockIdx.x * kBlock;
   const int n = n0 + threadIdx.x;
   int m[18];
   if (RIA) {
-    RiaCursor cur = ria_locate(t, n0, n, N, s_rs);
     if (n >= N) return;
-    nbr_ria(t, cur, m);
+    nbr_ria(t, ria_locate(t, n), m);
   } else {
     if (n >= N) return;
     nbr_adj(t, n, m);
@@ -323,7 +347,7 @@ __global__ void __launch_bounds__(kBlock) k_osnt(DevTables t, KParams kp, CollCo
 // AA even step: direct read of the 19 local PDFs, collide, write to the
 // opposite local slots (no index loads at all).
 template <int PREC, bool FORCE, bool DRAG>
-__global__ void __launch_bounds__(kBlock) k_aa_even(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
+__global__ void __launch_bounds__(kBlock, kMinCtas) k_aa_even(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
                                                     typename St<PREC>::T* __restrict__ A,
                                                     const float* __restrict__ s, int N) {
   using R = typename St<PREC>::R;
@@ -341,30 +365,30 @@ __global__ void __launch_bounds__(kBlock) k_aa_even(DevTables t, KParams kp, Col
 // AA odd step: read f_i from the neighbour's opposite slot A[inv i][m_i], collide,
 // write p_i to A[i][m_{inv i}] -- the same 19 slots, so in place and race-free.
 template <int PREC, bool RIA, bool FORCE, bool DRAG>
-__global__ void __launch_bounds__(kBlock) k_aa_odd(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
+__global__ void __launch_bounds__(kBlock, kMinCtas) k_aa_odd(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
                                                    typename St<PREC>::T* __restrict__ A,
                                                    const float* __restrict__ s, int N) {
   using R = typename St<PREC>::R;
-  __shared__ int s_rs[kBlock + 1];
-  const int n0 = blockIdx.x * kBlock;
-  const int n = n0 + threadIdx.x;
-  int m[18];
-  if (RIA) {
-    RiaCursor cur = ria_locate(t, n0, n, N, s_rs);
-    if (n >= N) return;
-    nbr_ria(t, cur, m);
-  } else {
-    if (n >= N) return;
-    nbr_adj(t, n, m);
-  }
+  const int n = blockIdx.x * kBlock + threadIdx.x;
+  if (n >= N) return;
+  RiaCursor cur{0, 0};
   R d[kQ];
-  gather<PREC, true>(A, t.Npad, n, m, d, kp.inv_scale, c);
+  {
+    int m[18];
+    if (RIA) {
+      cur = ria_locate(t, n);
+      nbr_ria(t, cur, m);
+    } else {
+      nbr_adj(t, n, m);
+    }
+    gather<PREC, true>(A, t.Npad, n, m, d, kp.inv_scale, c);
+  }
   const R sn = DRAG ? R(__ldg(s + n)) : R(0);
   collide<R, FORCE, DRAG>(d, c, sn);
   St<PREC>::st(A + n, d[0], kp.scale);
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
-    const int mo = m[inv(i) - 1];  // who pulls p_i next: node mo, or this node through a marker
+    const int mo = nbr_again<RIA>(t, cur, n, inv(i) - 1);  // who pulls p_i next: node mo, or this node
     R v = d[i];
     if (mo < -1) v = (mo == LBM_MARK_INLET ? c.abb_in[wclass(i) - 1] : c.abb_out[wclass(i) - 1]) - v;
     const int dir = mo >= 0 ? i : inv(i);
@@ -395,15 +419,13 @@ template <int PREC, bool RIA>
 __global__ void __launch_bounds__(kBlock) k_init_eq(DevTables t, KParams kp, Feq19 feq, typename St<PREC>::T* pdf,
                                                     int layout, int N) {
   using R = typename St<PREC>::R;
-  __shared__ int s_rs[kBlock + 1];
   const int n0 = blockIdx.x * kBlock;
   const int n = n0 + threadIdx.x;
   int m[18];
   if (layout != LBM_LAYOUT_AA_EVEN) {
     if (RIA) {
-      RiaCursor cur = ria_locate(t, n0, n, N, s_rs);
       if (n >= N) return;
-      nbr_ria(t, cur, m);
+      nbr_ria(t, ria_locate(t, n), m);
     } else {
       if (n >= N) return;
       nbr_adj(t, n, m);
@@ -432,15 +454,13 @@ template <int PREC, bool RIA>
 __global__ void __launch_bounds__(kBlock) k_load_canonical(DevTables t, KParams kp, const double* __restrict__ F,
                                                            typename St<PREC>::T* pdf, int layout, int N) {
   using R = typename St<PREC>::R;
-  __shared__ int s_rs[kBlock + 1];
   const int n0 = blockIdx.x * kBlock;
   const int n = n0 + threadIdx.x;
   int m[18];
   if (layout != LBM_LAYOUT_AA_EVEN) {
     if (RIA) {
-      RiaCursor cur = ria_locate(t, n0, n, N, s_rs);
       if (n >= N) return;
-      nbr_ria(t, cur, m);
+      nbr_ria(t, ria_locate(t, n), m);
     } else {
       if (n >= N) return;
       nbr_adj(t, n, m);
@@ -471,15 +491,15 @@ __global__ void __launch_bounds__(kBlock) k_load_canonical(DevTables t, KParams 
 // Canonical pre-collision state of one node, FP64, unshifted.
 template <int PREC, bool RIA>
 __device__ __forceinline__ bool node_canonical(const DevTables& t, const KParams& kp,
-                                               const typename St<PREC>::T* pdf, int layout, int n0, int n, int N,
-                                               int* s_rs, double (&F)[kQ]) {
+                                               const CollConst<typename St<PREC>::R>& c,
+                                               const typename St<PREC>::T* pdf, int layout, int n, int N,
+                                               double (&F)[kQ]) {
   using R = typename St<PREC>::R;
   int m[18];
   if (layout != LBM_LAYOUT_AA_EVEN) {
     if (RIA) {
-      RiaCursor cur = ria_locate(t, n0, n, N, s_rs);
       if (n >= N) return false;
-      nbr_ria(t, cur, m);
+      nbr_ria(t, ria_locate(t, n), m);
     } else {
       if (n >= N) return false;
       nbr_adj(t, n, m);
@@ -492,9 +512,9 @@ __device__ __forceinline__ bool node_canonical(const DevTables& t, const KParams
 #pragma unroll
     for (int i = 0; i < kQ; ++i) d[i] = St<PREC>::ld(pdf + size_t(i) * t.Npad + n, kp.inv_scale);
   } else if (layout == LBM_LAYOUT_OSNT) {
-    gather<PREC, false>(pdf, t.Npad, n, m, d, kp.inv_scale, make_coll<R>(kp));
+    gather<PREC, false>(pdf, t.Npad, n, m, d, kp.inv_scale, c);
   } else {
-    gather<PREC, true>(pdf, t.Npad, n, m, d, kp.inv_scale, make_coll<R>(kp));
+    gather<PREC, true>(pdf, t.Npad, n, m, d, kp.inv_scale, c);
   }
 #pragma unroll
   for (int i = 0; i < kQ; ++i) F[i] = double(d[i]) + wgt(i) * kp.rho_s;
@@ -502,13 +522,13 @@ __device__ __forceinline__ bool node_canonical(const DevTables& t, const KParams
 }
 
 template <int PREC, bool RIA>
-__global__ void __launch_bounds__(kBlock) k_canonical(DevTables t, KParams kp, const typename St<PREC>::T* pdf,
-                                                      int layout, double* __restrict__ F, int N) {
-  __shared__ int s_rs[kBlock + 1];
+__global__ void __launch_bounds__(kBlock) k_canonical(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
+                                                      const typename St<PREC>::T* pdf, int layout,
+                                                      double* __restrict__ F, int N) {
   const int n0 = blockIdx.x * kBlock;
   const int n = n0 + threadIdx.x;
   double f[kQ];
-  if (!node_canonical<PREC, RIA>(t, kp, pdf, layout, n0, n, N, s_rs, f)) return;
+  if (!node_canonical<PREC, RIA>(t, kp, c, pdf, layout, n, N, f)) return;
 #pragma unroll
   for (int i = 0; i < kQ; ++i) F[size_t(i) * N + n] = f[i];
 }
@@ -536,16 +556,16 @@ __device__ __forceinline__ void block_sum4(double (&v)[4], double (*s_red)[4]) {
 // rho, u = (j0/rho + g/2)/(1 + s/2) per node and per-CTA partial sums of
 // [rho, rho u_x, rho u_y, rho u_z] (FP64).
 template <int PREC, bool RIA>
-__global__ void __launch_bounds__(kBlock) k_macro(DevTables t, KParams kp, const typename St<PREC>::T* pdf,
-                                                  int layout, const float* __restrict__ s, double* __restrict__ rho,
+__global__ void __launch_bounds__(kBlock) k_macro(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
+                                                  const typename St<PREC>::T* pdf, int layout,
+                                                  const float* __restrict__ s, double* __restrict__ rho,
                                                   double* __restrict__ u, double* __restrict__ partials, int N) {
-  __shared__ int s_rs[kBlock + 1];
   __shared__ double s_red[kBlock / 32][4];
   const int n0 = blockIdx.x * kBlock;
   const int n = n0 + threadIdx.x;
   double f[kQ];
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  if (node_canonical<PREC, RIA>(t, kp, pdf, layout, n0, n, N, s_rs, f)) {
+  if (node_canonical<PREC, RIA>(t, kp, c, pdf, layout, n, N, f)) {
     double r = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
@@ -702,11 +722,12 @@ int launch_canonical_t(const lbm_lattice* L, const KParams& kp, const void* pdf,
   if (L->N == 0) return LBM_OK;
   auto st = static_cast<cudaStream_t>(stream);
   const bool ria = !(L->uploaded & LBM_TABLES_ADJ);
+  const auto c = dev::make_coll<typename dev::St<PREC>::R>(kp);
   if (ria)
-    dev::k_canonical<PREC, true><<<grid_of(L->N), dev::kBlock, 0, st>>>(L->dev, kp, static_cast<const T*>(pdf),
+    dev::k_canonical<PREC, true><<<grid_of(L->N), dev::kBlock, 0, st>>>(L->dev, kp, c, static_cast<const T*>(pdf),
                                                                        layout, F, int(L->N));
   else
-    dev::k_canonical<PREC, false><<<grid_of(L->N), dev::kBlock, 0, st>>>(L->dev, kp, static_cast<const T*>(pdf),
+    dev::k_canonical<PREC, false><<<grid_of(L->N), dev::kBlock, 0, st>>>(L->dev, kp, c, static_cast<const T*>(pdf),
                                                                         layout, F, int(L->N));
   return cuda_check("canonical launch");
 }
@@ -719,12 +740,13 @@ int launch_macroscopic_t(const lbm_lattice* L, const KParams& kp, const void* pd
   double* part = sums ? partials : nullptr;
   if (L->N > 0) {
     const bool ria = !(L->uploaded & LBM_TABLES_ADJ);
+    const auto c = dev::make_coll<typename dev::St<PREC>::R>(kp);
     if (ria)
-      dev::k_macro<PREC, true><<<grid_of(L->N), dev::kBlock, 0, st>>>(L->dev, kp, static_cast<const T*>(pdf), layout,
-                                                                     s, rho, u, part, int(L->N));
+      dev::k_macro<PREC, true><<<grid_of(L->N), dev::kBlock, 0, st>>>(L->dev, kp, c, static_cast<const T*>(pdf),
+                                                                     layout, s, rho, u, part, int(L->N));
     else
-      dev::k_macro<PREC, false><<<grid_of(L->N), dev::kBlock, 0, st>>>(L->dev, kp, static_cast<const T*>(pdf), layout,
-                                                                      s, rho, u, part, int(L->N));
+      dev::k_macro<PREC, false><<<grid_of(L->N), dev::kBlock, 0, st>>>(L->dev, kp, c, static_cast<const T*>(pdf),
+                                                                      layout, s, rho, u, part, int(L->N));
     if (int rc = cuda_check("macroscopic launch")) return rc;
   }
   if (sums) {
@@ -733,6 +755,10 @@ int launch_macroscopic_t(const lbm_lattice* L, const KParams& kp, const void* pd
   }
   return LBM_OK;
 }
+
+#define LBM_INSTANTIATE_STEP_LAUNCHERS(P)                                                                          \
+  template int launch_osnt_t<P>(const lbm_lattice*, const KParams&, const void*, void*, const float*, int, void*); \
+  template int launch_aa_t<P>(const lbm_lattice*, const KParams&, void*, int, const float*, int, void*);
 
 #define LBM_INSTANTIATE_LAUNCHERS(P)                                                                               \
   template int launch_osnt_t<P>(const lbm_lattice*, const KParams&, const void*, void*, const float*, int, void*); \

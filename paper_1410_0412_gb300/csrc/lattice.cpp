@@ -316,18 +316,23 @@ int derive_ria(lbm_lattice* L) {
     }
   });
   L->run_start[R] = int32_t(N);
-  // Run holding the first node of every tile (the last run past the end).
-  L->ntiles = (N + kTile - 1) / kTile;
-  L->tile_run0.assign(L->ntiles + 1, 0);
-  parallel_for(L->ntiles + 1, [&](int64_t tb, int64_t te) {
-    for (int64_t t = tb; t < te; ++t) {
-      int64_t first = std::min<int64_t>(t * kTile, N - 1);
-      if (N == 0) {
-        L->tile_run0[t] = 0;
-        continue;
-      }
-      auto it = std::upper_bound(L->run_start.begin(), L->run_start.begin() + R, int32_t(first));
-      L->tile_run0[t] = int32_t((it - L->run_start.begin()) - 1);
+  // Warp-level run index: a head bit per node, and for every 32-node group the
+  // run holding its first node and that run's first node.
+  L->nwarps = (N + kWarpNodes - 1) / kWarpNodes;
+  L->head_bits.assign(L->nwarps, 0u);
+  L->warp_run0.assign(L->nwarps, 0);
+  L->warp_head0.assign(L->nwarps, 0);
+  for (int64_t r = 0; r < R; ++r) {
+    const int64_t h = L->run_start[r];
+    L->head_bits[h / kWarpNodes] |= 1u << (h % kWarpNodes);
+  }
+  parallel_for(L->nwarps, [&](int64_t wb, int64_t we) {
+    for (int64_t w = wb; w < we; ++w) {
+      const int32_t first = int32_t(w * kWarpNodes);
+      auto it = std::upper_bound(L->run_start.begin(), L->run_start.begin() + R, first);
+      const int32_t r = int32_t((it - L->run_start.begin()) - 1);
+      L->warp_run0[w] = r;
+      L->warp_head0[w] = L->run_start[r];
     }
   });
   std::memset(L->hist, 0, sizeof(L->hist));
@@ -409,11 +414,17 @@ int validate(const lbm_lattice* L) {
     return set_error(LBM_ERR_TABLE, std::string(kind == 3 ? "run is not maximal"
                                                           : "run table does not decode to the adjacency list") +
                                         " at run " + std::to_string(int64_t(bad)));
-  for (int64_t t = 0; t <= L->ntiles && N > 0; ++t) {
-    int64_t first = std::min<int64_t>(t * kTile, N - 1);
-    int32_t r = L->tile_run0[t];
-    if (r < 0 || r >= R || L->run_start[r] > first || L->run_start[r + 1] <= first)
-      return set_error(LBM_ERR_TABLE, "tile run index inconsistent at tile " + std::to_string(t));
+  // warp-level run index: recompute it by walking the runs once and compare
+  if (int64_t(L->head_bits.size()) != L->nwarps || int64_t(L->warp_run0.size()) != L->nwarps ||
+      int64_t(L->warp_head0.size()) != L->nwarps || L->nwarps != (N + kWarpNodes - 1) / kWarpNodes)
+    return set_error(LBM_ERR_TABLE, "warp run index has the wrong size");
+  std::vector<uint32_t> bits(L->nwarps, 0u);
+  for (int64_t r = 0; r < R; ++r) bits[L->run_start[r] / kWarpNodes] |= 1u << (L->run_start[r] % kWarpNodes);
+  int64_t r = 0;
+  for (int64_t w = 0; w < L->nwarps; ++w) {
+    while (r + 1 < R && L->run_start[r + 1] <= w * kWarpNodes) ++r;
+    if (L->head_bits[w] != bits[w] || L->warp_run0[w] != r || L->warp_head0[w] != L->run_start[r])
+      return set_error(LBM_ERR_TABLE, "warp run index inconsistent at node group " + std::to_string(w));
   }
   return LBM_OK;
 }

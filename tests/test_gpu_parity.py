@@ -78,7 +78,9 @@ def _geometry(kind, seed):
 @pytest.mark.parametrize("case", range(len(CASES)))
 @pytest.mark.parametrize("form", ["osnt", "aa"])
 @pytest.mark.parametrize("ria", [False, True])
-def test_f64_parity(case, form, ria):
+@pytest.mark.parametrize("prec", ["f64", "f64df"])
+def test_f64_parity(case, form, ria, prec):
+    """FP64 storage, with native FP64 or double-float (f32 pair) collision arithmetic."""
     kind, per, xp, enum, B, drag = CASES[case]
     solid = _geometry(kind, 200 + case)
     T = otables.Tables(solid, periodic=per, x_pressure=xp, enum=enum, B=B)
@@ -90,7 +92,7 @@ def test_f64_parity(case, form, ria):
     F0 = _state(T.N, case)
     steps = 6
     ref = _run_oracle(T, F0, op, steps, s, form)
-    got = _run_gpu(lat, "f64", lp, F0, steps, s, form, ria)
+    got = _run_gpu(lat, prec, lp, F0, steps, s, form, ria)
     assert _relerr(got, ref) <= TOL64
 
 
@@ -159,11 +161,26 @@ def test_config1_200_steps_parity():
     G = olbm.from_canonical(olbm.uniform_state(T.N, op), 0, T.adj, op)
     G = olbm.run_osnt(G, T.adj, op, 200)
     ref = olbm.canonical(G, 0, T.adj, op)
-    for form, ria in [("osnt", False), ("osnt", True), ("aa", True)]:
-        solver = lbm.Solver(lat, "f64", lp, form=form, ria=ria)
-        solver.init_equilibrium(1.0)
-        solver.step(200)
-        assert _relerr(solver.canonical().cpu(), ref) <= TOL64
+    for prec in ("f64", "f64df"):
+        for form, ria in [("osnt", False), ("osnt", True), ("aa", True)]:
+            solver = lbm.Solver(lat, prec, lp, form=form, ria=ria)
+            solver.init_equilibrium(1.0)
+            solver.step(200)
+            assert _relerr(solver.canonical().cpu(), ref) <= TOL64
+
+
+@pytest.mark.parametrize("prec", ["f64", "f64df"])
+def test_fast_flow_200_steps_parity(prec):
+    """A fast, strongly perturbed flow (|u| ~ 0.05) for 200 steps: the double-float
+    collision's 48-bit arithmetic must stay within the FP64 bar too."""
+    solid = geometry.random_voxels(31, 17, 13, 0.2, 77)
+    T = otables.Tables(solid, periodic=(1, 1, 1))
+    lat = lbm.Lattice(solid, periodic=(1, 1, 1)).upload()
+    op, lp = _params(g=(2e-5, -1e-5, 1e-5), omega=1.6)
+    F0 = _state(T.N, 21, amp=2e-2, u0=(0.05, -0.03, 0.02))
+    ref = _run_oracle(T, F0, op, 200, None, "aa")
+    got = _run_gpu(lat, prec, lp, F0, 200, None, "aa", True)
+    assert _relerr(got, ref) <= TOL64
 
 
 @pytest.mark.parametrize("prec,tol", [("f32", 2e-6), ("f16s", 5e-4)])
