@@ -157,6 +157,220 @@ def cpu_oracle_sample(solid, steps_pairs=1, zslab=16):
                       f"256^3 bed ({T.N} fluid nodes)"}
 
 
+# ---------------------------------------------------------------------------------------------
+# Suites: the other measured configurations (one JSON line each).  They time the library only;
+# GPU-vs-oracle comparisons of the same configurations live in tests/.
+# ---------------------------------------------------------------------------------------------
+
+def _time_variant(lbm, torch, lat, prec, params, form, ria, pairs, warm=2, s=None, init=True):
+    sv = lbm.Solver(lat, prec, params, form=form, ria=ria, s=s)
+    if init:
+        sv.init_equilibrium(1.0)
+    sv.step(2 * warm)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    sv.step(2 * pairs)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    return sv, 2 * lat.N * pairs / (ms / 1e3) / 1e9
+
+
+def suite_channel(args, lbm, torch):
+    """The paper's channel (Sect. 5.1): 100 x 100 x 500, long axis z, 1-voxel walls, periodic z."""
+    solid = geometry.square_channel(100, 100, 500)
+    lat = lbm.Lattice(solid, periodic=(0, 0, 1), enum="lex", B=1).upload()
+    r = lat.R / lat.N
+    hbm, kind = peaks()
+    out = {"suite": "channel", "fluid_nodes": lat.N, "runs": lat.R, "r": r, "r_times_98": r * 98,
+           "paper_table2_channel_B_l": [376, 306, 340, 305], "variants": {}}
+    w = WORKLOAD
+    for prec, pb in (("f64", 8), ("f64df", 8), ("f32", 4), ("f16s", 2)):
+        params = lbm.Params(omega_plus=w["omega_plus"], magic=w["magic"], g=(0.0, 0.0, 1e-6),
+                            shifted=prec in ("f32", "f16s"))
+        for form, ria in (("osnt", False), ("osnt", True), ("aa", False), ("aa", True)):
+            name = f"{form}{'_r' if ria else ''}"
+            sv, g = _time_variant(lbm, torch, lat, prec, params, form, ria, args.steps)
+            bl = loop_balance(name, pb, r)
+            out["variants"][f"{name}_{prec}"] = {"GFLUPs": g, "B_l": bl, "frac_hbm": g * bl / hbm,
+                                                  "roof_GFLUPs": hbm / bl}
+            del sv
+            torch.cuda.empty_cache()
+    out["hbm_peak_GBs"] = hbm
+    return out
+
+
+def suite_sweep(args, lbm, torch):
+    """Enumeration sweep on the bed (Sect. 5.6): LS with B = 1, 8, 16, 32, 64 and the Hilbert curve."""
+    solid = make_geometry(args.box)
+    w = WORKLOAD
+    hbm, kind = peaks()
+    out = {"suite": "sweep", "workload": WORKLOAD["name"] if not args.box else f"packed_bed_{args.box}",
+           "enumerations": {}}
+    for enum, B in (("lex", 1), ("lex", 8), ("lex", 16), ("lex", 32), ("lex", 64), ("hilbert", 1)):
+        lat = lbm.Lattice(solid, periodic=w["periodic"], enum=enum, B=B).upload()
+        r = lat.R / lat.N
+        runs = np.diff(lat.tables(node_xyz=False, adj=False)["run_start"].astype(np.int64))
+        rec = {"runs": lat.R, "r": r, "nodes_in_runs_ge_4": float(runs[runs >= 4].sum() / lat.N),
+               "nodes_in_runs_ge_32": float(runs[runs >= 32].sum() / lat.N),
+               "run_hist_log2": [int(x) for x in lat.run_hist[:16]]}
+        for prec, pb in (("f64df", 8), ("f32", 4)):
+            params = lbm.Params(omega_plus=w["omega_plus"], magic=w["magic"], g=w["g"], shifted=(prec == "f32"))
+            for form, ria in (("osnt", True), ("aa", False), ("aa", True)):
+                name = f"{form}{'_r' if ria else ''}"
+                sv, g = _time_variant(lbm, torch, lat, prec, params, form, ria, args.steps)
+                bl = loop_balance(name, pb, r)
+                rec[f"{name}_{prec}"] = {"GFLUPs": g, "B_l": bl, "frac_hbm": g * bl / hbm}
+                del sv
+                torch.cuda.empty_cache()
+        out["enumerations"][f"{enum}{B if enum == 'lex' else ''}"] = rec
+        del lat
+        torch.cuda.empty_cache()
+    return out
+
+
+def suite_foam(args, lbm, torch):
+    """Precision study on an open-cell foam with pressure faces in x (AA-R, FP64 / FP32 / FP16S)."""
+    n = args.box or 512
+    seeds = max(3, round(400 * (n / 512) ** 3))
+    radius = args.radius or 2.5
+    t0 = time.time()
+    solid = geometry.voronoi_foam(n, n, n, seeds, radius, 3)
+    gen_s = time.time() - t0
+    lat = lbm.Lattice(solid, periodic=(0, 0, 0), x_pressure=True, enum="lex", B=1).upload(lbm.LBM_TABLES_RIA)
+    w = WORKLOAD
+    out = {"suite": "foam", "box": n, "seeds": seeds, "strut_radius": radius, "porosity": geometry.porosity(solid),
+           "fluid_nodes": lat.N, "r": lat.R / lat.N, "geometry_s": gen_s, "steps": args.foam_steps, "variants": {}}
+    x = torch.as_tensor(lat.tables(adj=False, runs=False)["node_xyz"][:, 0].astype(np.int64), device="cuda")
+    inlet, outlet = x < 4, x >= n - 4
+    ref = None
+    for prec in ("f64", "f64df", "f32", "f16s"):
+        params = lbm.Params(omega_plus=w["omega_plus"], magic=w["magic"], rho_in=1.0 + 5e-4, rho_out=1.0 - 5e-4,
+                            shifted=prec in ("f32", "f16s"))
+        sv = lbm.Solver(lat, prec, params, form="aa", ria=True)
+        sv.init_equilibrium(1.0)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        sv.step(args.foam_steps)
+        b.record()
+        torch.cuda.synchronize()
+        g = lat.N * args.foam_steps / (a.elapsed_time(b) / 1e3) / 1e9
+        rho, u, _ = sv.macroscopic(sums=False)
+        dp = float((rho[inlet].mean() - rho[outlet].mean()) / 3.0)
+        rec = {"GFLUPs": g, "dP": dp, "mean_ux": float(u[0].mean())}
+        if ref is None:
+            ref = (u.clone(), dp)
+        else:
+            du = (u - ref[0]).abs()
+            rec.update({"u_err_max_rel": float(du.max() / ref[0].abs().max()),
+                        "u_err_l2_rel": float(du.norm() / ref[0].norm()),
+                        "dP_err_rel": abs(dp - ref[1]) / abs(ref[1])})
+        out["variants"][prec] = rec
+        del sv, rho, u
+        torch.cuda.empty_cache()
+    return out
+
+
+def suite_adjoint(args, lbm, torch):
+    """Adjoint cost: 128^3 periodic box, Brinkman field, FP32 storage, T steps, checkpoint every K."""
+    n = args.box or 128
+    T, K = args.adj_T, args.adj_K
+    solid = geometry.empty_box(n, n, n)
+    lat = lbm.Lattice(solid, periodic=(1, 1, 1)).upload()
+    s = torch.as_tensor(geometry.smooth_noise(n, n, n, 3.0, 2).reshape(-1), device="cuda")
+    out = {"suite": "adjoint", "box": n, "fluid_nodes": lat.N, "T": T, "K": K, "variants": {}}
+    for prec in ("f32", "f64df", "f64"):
+        params = lbm.Params(omega_plus=1.0, magic=3 / 16, g=(1e-5, 0.0, 0.0), shifted=True)
+        G0 = lat.new_grid(prec)
+        lbm.lbm_init_equilibrium(lat, prec, params, G0, lbm.LBM_LAYOUT_OSNT, 1.0)
+        nb = lbm.lbm_ckpt_workspace_bytes(lat, prec, T, K)
+        ws = torch.empty((nb + 7) // 8, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        J = lbm.lbm_flux_forward(lat, prec, params, G0, s, T, K, ws, ria=False)
+        e[1].record()
+        grad = lbm.lbm_flux_backward(lat, prec, params, s, T, K, ws, ria=False)
+        e[2].record()
+        torch.cuda.synchronize()
+        fwd, bwd = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+        out["variants"][prec] = {"J": float(J), "forward_ms": fwd, "backward_ms": bwd,
+                                 "backward_over_forward": bwd / fwd, "workspace_GB": nb / 1e9,
+                                 "grad_norm": float(grad.norm()), "grad": grad.cpu()}
+        del ws, G0
+        torch.cuda.empty_cache()
+    ref = out["variants"]["f64"]["grad"]
+    for prec in ("f32", "f64df"):
+        gv = out["variants"][prec]["grad"]
+        out["variants"][prec]["grad_err_max_rel"] = float((gv - ref).abs().max() / ref.abs().max())
+    if args.fd:
+        # central differences of the FP64 forward (shifted storage) at 20 nodes
+        rng = np.random.default_rng(4)
+        params = lbm.Params(omega_plus=1.0, magic=3 / 16, g=(1e-5, 0.0, 0.0), shifted=True)
+        G0 = lat.new_grid("f64")
+        lbm.lbm_init_equilibrium(lat, "f64", params, G0, lbm.LBM_LAYOUT_OSNT, 1.0)
+        nb = lbm.lbm_ckpt_workspace_bytes(lat, "f64", T, K)
+        ws = torch.empty((nb + 7) // 8, dtype=torch.float64, device="cuda")
+        worst = 0.0
+        for node in rng.choice(lat.N, args.fd, replace=False):
+            vals = []
+            for sign in (1, -1):
+                sp = s.clone()
+                sp[node] = float(s[node]) + sign * 1e-4
+                hh = float(sp[node].double() - s[node].double())
+                vals.append((float(lbm.lbm_flux_forward(lat, "f64", params, G0, sp, T, K, ws)), hh))
+            fd = (vals[0][0] - vals[1][0]) / (vals[0][1] - vals[1][1])
+            worst = max(worst, abs(fd - float(ref[node])) / abs(float(ref[node])))
+        out["fd_nodes"] = args.fd
+        out["fd_max_rel_err"] = worst
+    for v in out["variants"].values():
+        v.pop("grad", None)
+    return out
+
+
+def suite_large(args, lbm, torch):
+    """Large production run: 768^3 Voronoi foam, Hilbert order, pressure faces in x, FP32 AA-R."""
+    n = args.box or 768
+    seeds = max(3, round(1500 * (n / 768) ** 3))
+    radius = args.radius or 3.0
+    t0 = time.time()
+    solid = geometry.voronoi_foam(n, n, n, seeds, radius, 5)
+    gen_s = time.time() - t0
+    t0 = time.time()
+    lat = lbm.Lattice(solid, periodic=(0, 0, 0), x_pressure=True, enum="hilbert")
+    build_s = time.time() - t0
+    del solid
+    lat.upload(lbm.LBM_TABLES_RIA)
+    hbm, kind = peaks()
+    w = WORKLOAD
+    params = lbm.Params(omega_plus=w["omega_plus"], magic=w["magic"], rho_in=1.0 + 5e-4, rho_out=1.0 - 5e-4,
+                        shifted=True)
+    sv = lbm.Solver(lat, "f32", params, form="aa", ria=True)
+    sv.init_equilibrium(1.0)
+    sv.step(4)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(torch.cuda.current_device()) as clk:
+        a.record()
+        sv.step(args.large_steps)
+        b.record()
+        torch.cuda.synchronize()
+    g = lat.N * args.large_steps / (a.elapsed_time(b) / 1e3) / 1e9
+    r = lat.R / lat.N
+    bl = loop_balance("aa_r", 4, r)
+    _, _, sums = sv.macroscopic(fields=False)
+    return {"suite": "large", "box": n, "seeds": seeds, "strut_radius": radius, "fluid_nodes": lat.N, "r": r,
+            "enumeration": "hilbert", "geometry_s": gen_s, "lattice_build_s": build_s, "steps": args.large_steps,
+            "GFLUPs": g, "B_l": bl, "GBs_model": g * bl, "frac_hbm": g * bl / hbm,
+            "state_GB": 19 * lat.Npad * 4 / 1e9, "mass": float(sums[0]), "clocks": clk.summary()}
+
+
+SUITES = {"channel": suite_channel, "sweep": suite_sweep, "foam": suite_foam, "adjoint": suite_adjoint,
+          "large": suite_large}
+
+
 def run_reference(args):
     """--impl reference: the oracle on a bounded sample, same metric and unit."""
     import torch
@@ -197,6 +411,14 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--box", type=int, default=None, help="smaller cubic bed (profiling only)")
+    ap.add_argument("--suite", default=None, choices=sorted(["channel", "sweep", "foam", "adjoint", "large"]),
+                    help="measure another configuration instead of the headline (one JSON line)")
+    ap.add_argument("--radius", type=float, default=None, help="foam strut radius (suites foam/large)")
+    ap.add_argument("--foam-steps", type=int, default=2000)
+    ap.add_argument("--large-steps", type=int, default=5000)
+    ap.add_argument("--adj-T", type=int, default=2000)
+    ap.add_argument("--adj-K", type=int, default=45)
+    ap.add_argument("--fd", type=int, default=0, help="adjoint suite: finite-difference nodes")
     ap.add_argument("--prec", default="f64", choices=["f64", "f64df", "f32", "f16s"],
                     help="storage/arithmetic of the timed AA-R pair (the headline is f64)")
     args = ap.parse_args()
@@ -208,6 +430,12 @@ def main():
     import torch
     import torch.distributed as dist
     import paper_1410_0412_gb300 as lbm
+
+    if args.suite:
+        torch.cuda.set_device(0)
+        out = SUITES[args.suite](args, lbm, torch)
+        print(json.dumps(out))
+        return 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

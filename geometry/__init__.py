@@ -197,7 +197,7 @@ def rsa_spheres(X, Y, Z, radius, seed, periodic=(1, 0, 0), max_consecutive_rejec
     return solid, centres
 
 
-def voronoi_foam(X, Y, Z, n_seeds, strut_radius, seed, chunk=1 << 21):
+def voronoi_foam(X, Y, Z, n_seeds, strut_radius, seed, chunk=1 << 20, threads=None):
     """Open-cell foam: solid = voxels within ``strut_radius`` of a Voronoi edge.
 
     Seeds are uniform in the periodic box.  For voxel centre p with nearest
@@ -205,32 +205,35 @@ def voronoi_foam(X, Y, Z, n_seeds, strut_radius, seed, chunk=1 << 21):
     where the bisector planes of (s1, s2) and (s1, s3) meet; p is solid when
     its distance to that line is <= strut_radius.  With unit normals n2, n3
     and signed plane distances e2, e3 the squared distance to the line is
-    e^T G^-1 e with G = [[1, n2.n3], [n2.n3, 1]].
+    e^T G^-1 e with G = [[1, n2.n3], [n2.n3, 1]].  Chunks of voxels are
+    processed by a thread pool (the KD-tree queries and numpy kernels release
+    the interpreter lock).
     """
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+
     from scipy.spatial import cKDTree
 
     rng = SplitMix64(seed)
     dims = np.array([X, Y, Z], dtype=np.float64)
     seeds = rng.uniform(3 * n_seeds).reshape(n_seeds, 3) * dims
     tree = cKDTree(seeds, boxsize=dims)
-    solid = np.zeros(X * Y * Z, dtype=np.uint8)
+    total = X * Y * Z
+    solid = np.zeros(total, dtype=np.uint8)
     r2 = strut_radius * strut_radius
-    for start in range(0, X * Y * Z, chunk):
-        idx = np.arange(start, min(start + chunk, X * Y * Z), dtype=np.int64)
+
+    def work(start):
+        idx = np.arange(start, min(start + chunk, total), dtype=np.int64)
         p = np.stack([idx % X, (idx // X) % Y, idx // (X * Y)], axis=1).astype(np.float64)
         _, nb = tree.query(p, k=3)
         s1 = seeds[nb[:, 0]]
-        rel = []
+        v1 = p - s1
+        v1 -= dims * np.round(v1 / dims)
+        e, nrm = [], []
         for k in (1, 2):
             d = seeds[nb[:, k]] - s1
             d -= dims * np.round(d / dims)
-            rel.append(d)
-        v1 = p - s1
-        v1 -= dims * np.round(v1 / dims)
-        e = []
-        nrm = []
-        for d in rel:
-            L = np.linalg.norm(d, axis=1)
+            L = np.sqrt((d * d).sum(1))
             n = d / L[:, None]
             # signed distance of p from the bisector plane (mid-point at d/2)
             e.append((v1 * n).sum(1) - 0.5 * L)
@@ -239,6 +242,10 @@ def voronoi_foam(X, Y, Z, n_seeds, strut_radius, seed, chunk=1 << 21):
         det = np.maximum(1.0 - c * c, 1e-12)
         q = (e[0] ** 2 - 2 * c * e[0] * e[1] + e[1] ** 2) / det
         solid[idx] = (q <= r2).astype(np.uint8)
+
+    n_threads = threads or len(os.sched_getaffinity(0))
+    with ThreadPoolExecutor(max_workers=n_threads) as ex:
+        list(ex.map(work, range(0, total, chunk)))
     return solid.reshape(Z, Y, X)
 
 

@@ -148,6 +148,28 @@ def stream(P, adj, p: Params):
     return Fn
 
 
+def stream_at(P_of, targets, adj, p: Params):
+    """The canonical pull of ``stream`` evaluated only at the nodes ``targets``.
+
+    ``P_of(i, nodes)`` returns the post-collision PDFs P[i][nodes] (global node
+    ids); it only has to know the targets and their pull sources.  Used to
+    check single nodes of a large lattice one by one.
+    """
+    adj = as_t(adj, torch.int64)
+    targets = as_t(targets, torch.int64)
+    Fn = torch.empty((Q, len(targets)), dtype=torch.float64)
+    Fn[0] = P_of(0, targets)
+    for i in range(1, Q):
+        m = adj[i - 1][targets]
+        ii = int(_INV[i])
+        fluid = m >= 0
+        from_nb = P_of(i, torch.where(fluid, m, targets))
+        own = P_of(ii, targets)
+        abb = -own + 2 * float(_W[i]) * _rho_bc(m, p, own.dtype)
+        Fn[i] = torch.where(fluid, from_nb, torch.where(m == -1, own, abb))
+    return Fn
+
+
 def unstream(F, adj, p: Params):
     """The grid G with stream(G) = F (streaming is a bijection of PDF slots)."""
     adj = as_t(adj, torch.int64)

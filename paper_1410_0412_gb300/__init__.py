@@ -150,13 +150,14 @@ class Lattice:
     def handle(self):
         return self._h
 
-    def tables(self, node_xyz=True):
-        """Host tables as numpy arrays (node_xyz [N,3], adj [18,N], run_start [R+1], run_adj [18,R])."""
+    def tables(self, node_xyz=True, adj=True, runs=True):
+        """Host tables as numpy arrays (node_xyz [N,3], adj [18,N], run_start [R+1], run_adj [18,R]);
+        tables not asked for are returned as None."""
         N, R = self.N, self.R
         xyz = np.empty((N, 3), np.int32) if node_xyz else None
-        adj = np.empty((18, N), np.int32)
-        rs = np.empty(R + 1, np.int32)
-        ra = np.empty((18, R), np.int32)
+        adj = np.empty((18, N), np.int32) if adj else None
+        rs = np.empty(R + 1, np.int32) if runs else None
+        ra = np.empty((18, R), np.int32) if runs else None
         p = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)
         check(_lib.load().lbm_export_tables(self._h, p(xyz), p(adj), p(rs), p(ra)), "lbm_export_tables")
         return {"node_xyz": xyz, "adj": adj, "run_start": rs, "run_adj": ra}

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(DevTables t, KParams kp, Col
   }
   // forward quantities of F_n
   R d[kQ];
-  gather<PREC, false>(G, t.Npad, n, m, d, kp.inv_scale, cc);
+  gather<PREC, false>(G, t.npad, n, m, d, kp.inv_scale, cc, t.pressure);
   R drho = R(0), jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(DevTables t, KParams kp, Col
     const int mp = m[inv(j) - 1];
     const int dir = mp >= 0 ? j : inv(j);
     const int node = mp >= 0 ? mp : n;
-    const R v = lam_next[size_t(dir) * t.Npad + node];
+    const R v = lam_next[at(dir, t.npad, node)];
     mu[j] = mp < -1 ? -v : v;
   }
   // weighted moments of mu (pairs: even part for M0/M2, odd part for M1)
@@ -159,8 +159,8 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(DevTables t, KParams kp, Col
     if (cz(a)) Bc += cz(a) > 0 ? Bz : -Bz;
     const R e = fma(c.qp, sp, A);
     const R o = fma(c.qm, sm, Bc);
-    lam[size_t(a) * t.Npad + n] = e + o;
-    lam[size_t(a + 1) * t.Npad + n] = e - o;
+    lam[at(a, t.npad, n)] = e + o;
+    lam[at(a + 1, t.npad, n)] = e - o;
   }
 }
 
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kBlock) k_objective(DevTables t, KParams kp, C
     hi = rux;
     if (lamT) {
 #pragma unroll
-      for (int i = 0; i < kQ; ++i) lamT[size_t(i) * t.Npad + n] = R((cx(i) + 0.5 * kp.g[0]) * kd * invN);
+      for (int i = 0; i < kQ; ++i) lamT[at(i, t.npad, n)] = R((cx(i) + 0.5 * kp.g[0]) * kd * invN);
     }
     if (grad_s) grad_s[n] = -0.5 * rux * kd * invN;
   }

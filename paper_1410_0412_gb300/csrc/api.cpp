@@ -255,6 +255,11 @@ int lbm_lattice_upload(lbm_lattice* L, int which, void* dev, size_t bytes, void*
   L->dev.Rpad = L->Rpad;
   L->dev.R = L->R;
   L->dev.nwarps = L->nwarps;
+  L->dev.npad = uint32_t(L->Npad);
+  L->dev.rpad = uint32_t(L->Rpad);
+  L->dev.pressure = L->bc.x_pressure ? 1 : 0;
+  if (!L->bc.x_pressure)  // lattices from a raw adjacency list: look for markers
+    for (size_t k = 0; k < L->adj.size() && !L->dev.pressure; ++k) L->dev.pressure = L->adj[k] < LBM_MARK_WALL;
   L->uploaded = which;
   return LBM_OK;
 }

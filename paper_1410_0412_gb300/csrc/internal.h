@@ -36,6 +36,8 @@ struct DevTables {
   const int32_t* warp_run0 = nullptr;   // [nwarps]     run holding node 32w
   const int32_t* warp_head0 = nullptr;  // [nwarps]     first node of that run
   int64_t Npad = 0, Rpad = 0, R = 0, nwarps = 0;
+  uint32_t npad = 0, rpad = 0;          // the same strides as 32-bit values (N < 2^31)
+  int pressure = 0;                     // the lattice has inlet/outlet markers
 };
 
 }  // namespace lbm

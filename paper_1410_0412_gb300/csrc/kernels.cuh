@@ -78,12 +78,17 @@ template <> struct St<LBM_F16S> {
   }
 };
 
+// Element (dir, node) of a [19][npad] array: 32x32 -> 64-bit multiply-add.
+__device__ __forceinline__ size_t at(int dir, uint32_t npad, int node) {
+  return static_cast<unsigned long long>(static_cast<unsigned>(dir)) * npad + static_cast<unsigned>(node);
+}
+
 // ---- neighbour addressing --------------------------------------------------------------
 // m[i-1] for i = 1..18: the adjacency entry of node n (node index or marker).
 // Plain form: one coalesced int32 load per direction (D_idx = 72 B/node).
 __device__ __forceinline__ void nbr_adj(const DevTables& t, int n, int (&m)[18]) {
 #pragma unroll
-  for (int i = 0; i < 18; ++i) m[i] = __ldg(t.adj + size_t(i) * t.Npad + n);
+  for (int i = 0; i < 18; ++i) m[i] = __ldg(t.adj + at(i, t.npad, n));
 }
 
 // RIA form (Sect. 4.1), warp-level: the run-length coding is held as one run
@@ -122,16 +127,16 @@ __device__ __forceinline__ int ld_index_again(const int32_t* p) {
 template <bool RIA>
 __device__ __forceinline__ int nbr_again(const DevTables& t, RiaCursor c, int n, int i) {
   if (RIA) {
-    const int a = ld_index_again(t.run_adj + size_t(i) * t.Rpad + c.r);
+    const int a = ld_index_again(t.run_adj + at(i, t.rpad, c.r));
     return a >= 0 ? a + c.off : a;
   }
-  return ld_index_again(t.adj + size_t(i) * t.Npad + n);
+  return ld_index_again(t.adj + at(i, t.npad, n));
 }
 
 __device__ __forceinline__ void nbr_ria(const DevTables& t, RiaCursor c, int (&m)[18]) {
 #pragma unroll
   for (int i = 0; i < 18; ++i) {
-    const int a = __ldg(t.run_adj + size_t(i) * t.Rpad + c.r);
+    const int a = __ldg(t.run_adj + at(i, t.rpad, c.r));
     m[i] = a >= 0 ? a + c.off : a;
   }
 }
@@ -301,19 +306,23 @@ __device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const
 // a pressure marker (-2 / -3) turns the bounce-back value v into
 // 2 w_i (rho_bc - rho_s) - v (anti-bounce-back, in deviation form).
 template <int PREC, bool AA_ODD>
-__device__ __forceinline__ void gather(const typename St<PREC>::T* g, int64_t Npad, int n, const int (&m)[18],
+__device__ __forceinline__ void gather(const typename St<PREC>::T* g, uint32_t npad, int n, const int (&m)[18],
                                        typename St<PREC>::R (&d)[kQ], float inv_scale,
-                                       const CollConst<typename St<PREC>::R>& c) {
-  using R = typename St<PREC>::R;
+                                       const CollConst<typename St<PREC>::R>& c, int pressure) {
   d[0] = St<PREC>::ld(g + n, inv_scale);
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
     const int mi = m[i - 1];
     const int dir = (mi >= 0) == AA_ODD ? inv(i) : i;
     const int node = mi >= 0 ? mi : n;
-    R v = St<PREC>::ld(g + size_t(dir) * Npad + node, inv_scale);
-    if (mi < -1) v = (mi == LBM_MARK_INLET ? c.abb_in[wclass(i) - 1] : c.abb_out[wclass(i) - 1]) - v;
-    d[i] = v;
+    d[i] = St<PREC>::ld(g + at(dir, npad, node), inv_scale);
+  }
+  if (pressure) {  // uniform: only lattices with pressure faces pay for the check
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
+      const int mi = m[i - 1];
+      if (mi < -1) d[i] = (mi == LBM_MARK_INLET ? c.abb_in[wclass(i) - 1] : c.abb_out[wclass(i) - 1]) - d[i];
+    }
   }
 }
 
@@ -337,11 +346,11 @@ __global__ void __launch_bounds__(kBlock, kMinCtas) k_osnt(DevTables t, KParams 
     nbr_adj(t, n, m);
   }
   R d[kQ];
-  gather<PREC, false>(src, t.Npad, n, m, d, kp.inv_scale, c);
+  gather<PREC, false>(src, t.npad, n, m, d, kp.inv_scale, c, t.pressure);
   const R sn = DRAG ? R(__ldg(s + n)) : R(0);
   collide<R, FORCE, DRAG>(d, c, sn);
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) St<PREC>::st_stream(dst + size_t(i) * t.Npad + n, d[i], kp.scale);
+  for (int i = 0; i < kQ; ++i) St<PREC>::st_stream(dst + at(i, t.npad, n), d[i], kp.scale);
 }
 
 // AA even step: direct read of the 19 local PDFs, collide, write to the
@@ -355,11 +364,11 @@ __global__ void __launch_bounds__(kBlock, kMinCtas) k_aa_even(DevTables t, KPara
   if (n >= N) return;
   R d[kQ];
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) d[i] = St<PREC>::ld(A + size_t(i) * t.Npad + n, kp.inv_scale);
+  for (int i = 0; i < kQ; ++i) d[i] = St<PREC>::ld(A + at(i, t.npad, n), kp.inv_scale);
   const R sn = DRAG ? R(__ldg(s + n)) : R(0);
   collide<R, FORCE, DRAG>(d, c, sn);
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) St<PREC>::st(A + size_t(inv(i)) * t.Npad + n, d[i], kp.scale);
+  for (int i = 0; i < kQ; ++i) St<PREC>::st(A + at(inv(i), t.npad, n), d[i], kp.scale);
 }
 
 // AA odd step: read f_i from the neighbour's opposite slot A[inv i][m_i], collide,
@@ -381,19 +390,29 @@ __global__ void __launch_bounds__(kBlock, kMinCtas) k_aa_odd(DevTables t, KParam
     } else {
       nbr_adj(t, n, m);
     }
-    gather<PREC, true>(A, t.Npad, n, m, d, kp.inv_scale, c);
+    gather<PREC, true>(A, t.npad, n, m, d, kp.inv_scale, c, t.pressure);
   }
   const R sn = DRAG ? R(__ldg(s + n)) : R(0);
   collide<R, FORCE, DRAG>(d, c, sn);
   St<PREC>::st(A + n, d[0], kp.scale);
+  if (t.pressure) {
 #pragma unroll
-  for (int i = 1; i < kQ; ++i) {
-    const int mo = nbr_again<RIA>(t, cur, n, inv(i) - 1);  // who pulls p_i next: node mo, or this node
-    R v = d[i];
-    if (mo < -1) v = (mo == LBM_MARK_INLET ? c.abb_in[wclass(i) - 1] : c.abb_out[wclass(i) - 1]) - v;
-    const int dir = mo >= 0 ? i : inv(i);
-    const int node = mo >= 0 ? mo : n;
-    St<PREC>::st(A + size_t(dir) * t.Npad + node, v, kp.scale);
+    for (int i = 1; i < kQ; ++i) {
+      const int mo = nbr_again<RIA>(t, cur, n, inv(i) - 1);  // who pulls p_i next: node mo, or this node
+      R v = d[i];
+      if (mo < -1) v = (mo == LBM_MARK_INLET ? c.abb_in[wclass(i) - 1] : c.abb_out[wclass(i) - 1]) - v;
+      const int dir = mo >= 0 ? i : inv(i);
+      const int node = mo >= 0 ? mo : n;
+      St<PREC>::st(A + at(dir, t.npad, node), v, kp.scale);
+    }
+  } else {
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
+      const int mo = nbr_again<RIA>(t, cur, n, inv(i) - 1);
+      const int dir = mo >= 0 ? i : inv(i);
+      const int node = mo >= 0 ? mo : n;
+      St<PREC>::st(A + at(dir, t.npad, node), d[i], kp.scale);
+    }
   }
 }
 
@@ -443,7 +462,7 @@ __global__ void __launch_bounds__(kBlock) k_init_eq(DevTables t, KParams kp, Feq
       if (mp < -1) v = wgt(j) * 2.0 * (mp == LBM_MARK_INLET ? kp.rho_in : kp.rho_out) - v;
       if (layout == LBM_LAYOUT_AA_ODD) slot = inv(j);
     }
-    St<PREC>::st(pdf + size_t(slot) * t.Npad + n, R(v - wgt(j) * kp.rho_s), kp.scale);
+    St<PREC>::st(pdf + at(slot, t.npad, n), R(v - wgt(j) * kp.rho_s), kp.scale);
   }
 }
 
@@ -484,7 +503,7 @@ __global__ void __launch_bounds__(kBlock) k_load_canonical(DevTables t, KParams 
       }
       if (layout == LBM_LAYOUT_AA_ODD) slot = inv(j);
     }
-    St<PREC>::st(pdf + size_t(slot) * t.Npad + n, R(v - wgt(j) * kp.rho_s), kp.scale);
+    St<PREC>::st(pdf + at(slot, t.npad, n), R(v - wgt(j) * kp.rho_s), kp.scale);
   }
 }
 
@@ -510,11 +529,11 @@ __device__ __forceinline__ bool node_canonical(const DevTables& t, const KParams
   R d[kQ];
   if (layout == LBM_LAYOUT_AA_EVEN) {
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) d[i] = St<PREC>::ld(pdf + size_t(i) * t.Npad + n, kp.inv_scale);
+    for (int i = 0; i < kQ; ++i) d[i] = St<PREC>::ld(pdf + at(i, t.npad, n), kp.inv_scale);
   } else if (layout == LBM_LAYOUT_OSNT) {
-    gather<PREC, false>(pdf, t.Npad, n, m, d, kp.inv_scale, c);
+    gather<PREC, false>(pdf, t.npad, n, m, d, kp.inv_scale, c, t.pressure);
   } else {
-    gather<PREC, true>(pdf, t.Npad, n, m, d, kp.inv_scale, c);
+    gather<PREC, true>(pdf, t.npad, n, m, d, kp.inv_scale, c, t.pressure);
   }
 #pragma unroll
   for (int i = 0; i < kQ; ++i) F[i] = double(d[i]) + wgt(i) * kp.rho_s;

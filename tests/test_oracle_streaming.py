@@ -146,3 +146,15 @@ def test_pressure_driven_duct_flows_downhill():
     prof = np.array([float(rho[torch.as_tensor(x == k)].mean()) for k in range(12)])
     assert float(u[0].mean()) > 0
     assert np.all(np.diff(prof) < 0)
+
+
+def test_stream_at_equals_stream():
+    """Pointwise evaluation of the pull at chosen nodes equals the full stream."""
+    solid = geometry.random_voxels(9, 7, 6, 0.25, 90)
+    T = tables.Tables(solid, periodic=(0, 1, 0), x_pressure=True)
+    p = lbm.Params(rho_in=1.01, rho_out=0.99)
+    P = _perturbed_state(T, p, 7)
+    full = lbm.stream(P, T.adj, p)
+    targets = torch.as_tensor(np.random.default_rng(0).choice(T.N, 40, replace=False))
+    part = lbm.stream_at(lambda i, nodes: P[i, nodes], targets, T.adj, p)
+    assert torch.equal(part, full[:, targets])
