@@ -37,11 +37,11 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 # FP64 pipe of GB300: 152 SMs x 2 DP lanes/clk x 2.07 GHz (measured 0.60 T DFMA/s burst)
 FP64_PEAK_GINSTR = 152 * 2 * 2.07e9 / 1e9
-# FP64-pipe instructions per node of the AA odd step with RIA and body force
-# (adds, multiplies, FMAs, the reciprocal's iterations and selects each take one
-# FP64 slot): 198, from ncu's FP64-pipe utilisation (86.6 % of a 476.7 us launch
-# over 1,310,203 nodes at 2.07 GHz, 152 SMs x 2 lanes).
-COLL_DP_INSTR = 198
+# FP64-pipe instructions per node of the AA steps with body force (adds,
+# multiplies, FMAs and the reciprocal's iterations each take one FP64 slot):
+# sm__inst_executed_pipe_fp64.sum = 6,510,096 warp instructions for 1,310,203
+# nodes (128^3 bed), i.e. 159 per node, the same for the even and odd step.
+COLL_DP_INSTR = 159
 
 WORKLOAD = dict(name="packed_bed_256_rsa_r12", X=256, Y=256, Z=256, radius=12.0, seed=1, rejections=20000,
                 periodic=(1, 0, 0), g=(1e-6, 0.0, 0.0), omega_plus=1.0, magic=3.0 / 16.0)

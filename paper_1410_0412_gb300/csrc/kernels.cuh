@@ -33,7 +33,12 @@ __host__ __device__ constexpr int wclass(int i) { return i == 0 ? 0 : (i <= 6 ? 
 __host__ __device__ constexpr double wgt(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
 
 constexpr int kBlock = 128;  // nodes per CTA of the step kernels (one node per thread)
-constexpr int kMinCtas = 5;  // step kernels: keep <= 102 registers so 5 CTAs (20 warps) fit per SM
+// Minimum resident CTAs per SM of the step kernels (caps registers at
+// 65536 / (128 * n)): 5 (<= 102 registers) for the FP64/FP32/FP16 paths, 6
+// (<= 85) for the double-float path, whose AA odd step needs the extra warps
+// to hide its three dependent memory round trips.
+template <int PREC> struct MinCtas { static constexpr int value = 5; };
+template <> struct MinCtas<LBM_F64_DF> { static constexpr int value = 6; };
 static_assert(kBlock % kWarpNodes == 0, "a warp must cover one run-index group");
 
 // ---- storage traits -----------------------------------------------------------------
@@ -330,7 +335,7 @@ __device__ __forceinline__ void gather(const typename St<PREC>::T* g, uint32_t n
 // OS-NT step: pull (indirect) from src, collide, store locally into dst with
 // evict-first stores so the write stream does not push src out of L2.
 template <int PREC, bool RIA, bool FORCE, bool DRAG>
-__global__ void __launch_bounds__(kBlock, kMinCtas) k_osnt(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
+__global__ void __launch_bounds__(kBlock, MinCtas<PREC>::value) k_osnt(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
                                                  const typename St<PREC>::T* __restrict__ src,
                                                  typename St<PREC>::T* __restrict__ dst, const float* __restrict__ s,
                                                  int N) {
@@ -356,7 +361,7 @@ __global__ void __launch_bounds__(kBlock, kMinCtas) k_osnt(DevTables t, KParams 
 // AA even step: direct read of the 19 local PDFs, collide, write to the
 // opposite local slots (no index loads at all).
 template <int PREC, bool FORCE, bool DRAG>
-__global__ void __launch_bounds__(kBlock, kMinCtas) k_aa_even(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
+__global__ void __launch_bounds__(kBlock, MinCtas<PREC>::value) k_aa_even(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
                                                     typename St<PREC>::T* __restrict__ A,
                                                     const float* __restrict__ s, int N) {
   using R = typename St<PREC>::R;
@@ -374,7 +379,7 @@ __global__ void __launch_bounds__(kBlock, kMinCtas) k_aa_even(DevTables t, KPara
 // AA odd step: read f_i from the neighbour's opposite slot A[inv i][m_i], collide,
 // write p_i to A[i][m_{inv i}] -- the same 19 slots, so in place and race-free.
 template <int PREC, bool RIA, bool FORCE, bool DRAG>
-__global__ void __launch_bounds__(kBlock, kMinCtas) k_aa_odd(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
+__global__ void __launch_bounds__(kBlock, MinCtas<PREC>::value) k_aa_odd(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
                                                    typename St<PREC>::T* __restrict__ A,
                                                    const float* __restrict__ s, int N) {
   using R = typename St<PREC>::R;
@@ -395,10 +400,15 @@ __global__ void __launch_bounds__(kBlock, kMinCtas) k_aa_odd(DevTables t, KParam
   const R sn = DRAG ? R(__ldg(s + n)) : R(0);
   collide<R, FORCE, DRAG>(d, c, sn);
   St<PREC>::st(A + n, d[0], kp.scale);
+  // who pulls p_i next: node mo[inv(i) - 1], or this node through a marker;
+  // all 18 re-reads are issued before the first store
+  int mo_[18];
+#pragma unroll
+  for (int j = 0; j < 18; ++j) mo_[j] = nbr_again<RIA>(t, cur, n, j);
   if (t.pressure) {
 #pragma unroll
     for (int i = 1; i < kQ; ++i) {
-      const int mo = nbr_again<RIA>(t, cur, n, inv(i) - 1);  // who pulls p_i next: node mo, or this node
+      const int mo = mo_[inv(i) - 1];
       R v = d[i];
       if (mo < -1) v = (mo == LBM_MARK_INLET ? c.abb_in[wclass(i) - 1] : c.abb_out[wclass(i) - 1]) - v;
       const int dir = mo >= 0 ? i : inv(i);
@@ -408,7 +418,7 @@ __global__ void __launch_bounds__(kBlock, kMinCtas) k_aa_odd(DevTables t, KParam
   } else {
 #pragma unroll
     for (int i = 1; i < kQ; ++i) {
-      const int mo = nbr_again<RIA>(t, cur, n, inv(i) - 1);
+      const int mo = mo_[inv(i) - 1];
       const int dir = mo >= 0 ? i : inv(i);
       const int node = mo >= 0 ? mo : n;
       St<PREC>::st(A + at(dir, t.npad, node), d[i], kp.scale);

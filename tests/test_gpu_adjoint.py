@@ -125,3 +125,29 @@ def test_fp32_adjoint_error_vs_fp64():
         grads[prec] = lbm.lbm_flux_backward(lat, prec, lps, s.cuda(), steps, K, ws, ria=False).cpu()
     rel = float((grads["f32"] - grads["f64"]).abs().max() / grads["f64"].abs().max())
     assert rel <= 1e-3
+
+
+def test_config4_crop_vs_taped_oracle():
+    """32^3 fully periodic crop of the Brinkman-field box (smoothed noise, sigma 3, seed 2),
+    g = 1e-5 x, T = 100 steps, checkpoint every 10: FP64 gradient vs the taped oracle to 1e-10,
+    FP32 storage with FP64 accumulation within the stated 1e-3."""
+    n, steps, K = 32, 100, 10
+    solid = geometry.empty_box(n, n, n)
+    T = otables.Tables(solid, periodic=(1, 1, 1))
+    lat = lbm.Lattice(solid, periodic=(1, 1, 1)).upload()
+    field = geometry.smooth_noise(n, n, n, 3.0, 2)
+    s = torch.as_tensor(geometry.node_field(field, T.node_xyz))
+    kw = dict(omega_plus=1.0, magic=3 / 16, g=(1e-5, 0.0, 0.0))
+    op = olbm.Params(**kw)
+    G0o = olbm.from_canonical(olbm.uniform_state(T.N, op), 0, T.adj, op)
+    J_ref, dJ_ref = oadj.flux_and_gradient(G0o, T.adj, op, s.to(torch.float64), steps)
+    for prec, tol in (("f64", 1e-10), ("f64df", 1e-10), ("f32", 1e-3)):
+        lp = lbm.Params(shifted=(prec != "f64"), **kw)
+        G0 = lat.new_grid(prec)
+        lbm.lbm_init_equilibrium(lat, prec, lp, G0, lbm.LBM_LAYOUT_OSNT, 1.0)
+        ws = torch.empty((lbm.lbm_ckpt_workspace_bytes(lat, prec, steps, K) + 7) // 8, dtype=torch.float64,
+                         device="cuda")
+        J = lbm.lbm_flux_forward(lat, prec, lp, G0, s.cuda(), steps, K, ws, ria=True)
+        grad = lbm.lbm_flux_backward(lat, prec, lp, s.cuda(), steps, K, ws, ria=True).cpu()
+        assert abs(float(J) - float(J_ref)) <= max(tol, 1e-13) * abs(float(J_ref))
+        assert float((grad - dJ_ref).abs().max() / dJ_ref.abs().max()) <= tol
