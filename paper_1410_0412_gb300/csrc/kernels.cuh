@@ -34,11 +34,16 @@ __host__ __device__ constexpr double wgt(int i) { return i == 0 ? 1.0 / 3.0 : (i
 
 constexpr int kBlock = 128;  // nodes per CTA of the step kernels (one node per thread)
 // Minimum resident CTAs per SM of the step kernels (caps registers at
-// 65536 / (128 * n)): 5 (<= 102 registers) for the FP64/FP32/FP16 paths, 6
-// (<= 85) for the double-float path, whose AA odd step needs the extra warps
-// to hide its three dependent memory round trips.
+// 65536 / (128 * n)).  The AA odd step is latency-bound (index loads, then
+// gathers, then scattered stores), so it trades a few spills for warps: 8
+// CTAs (<= 64 registers) for FP32/FP16 and 7 for the double-float path were
+// the fastest caps measured on GB300; the native FP64 path stays at 5 (it is
+// FP64-pipe bound, and 8 spills hundreds of bytes).
 template <int PREC> struct MinCtas { static constexpr int value = 5; };
 template <> struct MinCtas<LBM_F64_DF> { static constexpr int value = 6; };
+template <int PREC> struct MinCtasOdd { static constexpr int value = 8; };
+template <> struct MinCtasOdd<LBM_F64> { static constexpr int value = 5; };
+template <> struct MinCtasOdd<LBM_F64_DF> { static constexpr int value = 7; };
 static_assert(kBlock % kWarpNodes == 0, "a warp must cover one run-index group");
 
 // ---- storage traits -----------------------------------------------------------------
@@ -376,10 +381,38 @@ __global__ void __launch_bounds__(kBlock, MinCtas<PREC>::value) k_aa_even(DevTab
   for (int i = 0; i < kQ; ++i) St<PREC>::st(A + at(inv(i), t.npad, n), d[i], kp.scale);
 }
 
+// AA even step for shifted FP16 storage, two consecutive nodes per thread: one
+// 4-byte half2 access per direction and thread keeps twice the bytes in flight
+// of the one-node form (Npad is a multiple of 128, so every pair is aligned;
+// a pair's second node may be padding, which is computed and stored but never
+// read as a node).
+template <bool FORCE, bool DRAG>
+__global__ void __launch_bounds__(kBlock) k_aa_even_h2(DevTables t, KParams kp, CollConst<float> c,
+                                                       __half* __restrict__ A, const float* __restrict__ s,
+                                                       int N) {
+  const int n = 2 * (blockIdx.x * kBlock + threadIdx.x);
+  if (n >= N) return;
+  float d0[kQ], d1[kQ];
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const float2 v = __half22float2(__ldg(reinterpret_cast<const __half2*>(A + at(i, t.npad, n))));
+    d0[i] = v.x * kp.inv_scale;
+    d1[i] = v.y * kp.inv_scale;
+  }
+  const float s0 = DRAG ? __ldg(s + n) : 0.0f;
+  const float s1 = DRAG ? (n + 1 < N ? __ldg(s + n + 1) : 0.0f) : 0.0f;
+  collide<float, FORCE, DRAG>(d0, c, s0);
+  collide<float, FORCE, DRAG>(d1, c, s1);
+#pragma unroll
+  for (int i = 0; i < kQ; ++i)
+    *reinterpret_cast<__half2*>(A + at(inv(i), t.npad, n)) =
+        __floats2half2_rn(d0[i] * kp.scale, d1[i] * kp.scale);
+}
+
 // AA odd step: read f_i from the neighbour's opposite slot A[inv i][m_i], collide,
 // write p_i to A[i][m_{inv i}] -- the same 19 slots, so in place and race-free.
 template <int PREC, bool RIA, bool FORCE, bool DRAG>
-__global__ void __launch_bounds__(kBlock, MinCtas<PREC>::value) k_aa_odd(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
+__global__ void __launch_bounds__(kBlock, MinCtasOdd<PREC>::value) k_aa_odd(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
                                                    typename St<PREC>::T* __restrict__ A,
                                                    const float* __restrict__ s, int N) {
   using R = typename St<PREC>::R;
@@ -688,6 +721,17 @@ int launch_aa_t(const lbm_lattice* L, const KParams& kp, void* pdf, int parity, 
   const int N = int(L->N);
   const bool f = has_force(kp);
   const auto c = dev::make_coll<typename dev::St<PREC>::R>(kp);
+  if constexpr (PREC == LBM_F16S) {
+    if (parity == 0) {
+    const unsigned g2 = unsigned((L->N + 2 * dev::kBlock - 1) / (2 * dev::kBlock));
+    __half* H = reinterpret_cast<__half*>(pdf);
+    const auto cf = dev::make_coll<float>(kp);
+    if (s) dev::k_aa_even_h2<true, true><<<g2, dev::kBlock, 0, st>>>(L->dev, kp, cf, H, s, N);
+    else if (f) dev::k_aa_even_h2<true, false><<<g2, dev::kBlock, 0, st>>>(L->dev, kp, cf, H, s, N);
+    else dev::k_aa_even_h2<false, false><<<g2, dev::kBlock, 0, st>>>(L->dev, kp, cf, H, s, N);
+    return cuda_check("AA even step launch");
+    }
+  }
   if (parity == 0) {
     if (s) dev::k_aa_even<PREC, true, true><<<g, dev::kBlock, 0, st>>>(L->dev, kp, c, A, s, N);
     else if (f) dev::k_aa_even<PREC, true, false><<<g, dev::kBlock, 0, st>>>(L->dev, kp, c, A, s, N);
