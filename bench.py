@@ -514,6 +514,41 @@ def main():
     else:
         roofline = roofline_hbm
 
+    # ---- the same pair with the double-float collision (FP64 grids, same FP64 parity bar) -------------
+    companion = None
+    if hp == "f64" and not args.no_variants:
+        sdf = lbm.Solver(lat, "f64df", params, form="aa", ria=True)
+        sdf.init_equilibrium(1.0)
+        for _ in range(args.warmup):
+            sdf.step(2)
+        evd = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+                torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        barrier()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for k in range(K):
+            evd[k][0].record(stream)
+            lbm.lbm_step_aa(lat, "f64df", params, sdf.pdf, 0, None, True)
+            evd[k][1].record(stream)
+            lbm.lbm_step_aa(lat, "f64df", params, sdf.pdf, 1, None, True)
+            evd[k][2].record(stream)
+        c1.record(stream)
+        barrier()
+        cms = c0.elapsed_time(c1)
+        e_ms = sum(e[0].elapsed_time(e[1]) for e in evd) / K
+        o_ms = sum(e[1].elapsed_time(e[2]) for e in evd) / K
+        cval = world * 2 * N * K / (cms / 1e3) / 1e9
+        cbl = loop_balance("aa_odd_r", 8, r)
+        companion = {"value": cval, "unit": "GFLUP/s", "ms_per_step": cms / K,
+                     "what": "the timed AA-R pair on the same FP64 grids with the collision in double-float "
+                             "(FP32-pair, 48-bit) arithmetic; held to the same 1e-12 FP64 parity bar",
+                     "kernel_ms": {"even": e_ms, "odd": o_ms},
+                     "roofline_hbm": {"kernel": "aa_odd_ria_f64df", "bound": "hbm",
+                                      "achieved": cbl * N / (o_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                                      "frac": cbl * N / (o_ms / 1e3) / 1e9 / hbm}}
+        del sdf
+        torch.cuda.empty_cache()
+
     # ---- end to end through host buffers: H2D state, one pair, D2H state -------------------------------
     e2e = None
     if rank == 0 or world > 1:
@@ -588,7 +623,8 @@ def main():
                    "step": "AA even + odd with RIA (2 lattice updates)", "parallelism": "replicas" if world > 1
                    else "single GPU", "l2": "inputs larger than L2 (state %.2f GB)" % (19 * lat.Npad * 8 / 1e9),
                    "setup_s": setup_s, "mass_after": mass},
-        "roofline": roofline, "roofline_hbm": roofline_hbm, "variants": variants, "cpu_baseline": cpu,
+        "roofline": roofline, "roofline_hbm": roofline_hbm, "f64_double_float": companion,
+        "variants": variants, "cpu_baseline": cpu,
         "e2e": e2e, "gpu_launches": 2 * K, "clocks": clk.summary(),
     }
     if rank == 0:

@@ -125,24 +125,6 @@ __device__ __forceinline__ RiaCursor ria_locate(const DevTables& t, int n) {
   return c;
 }
 
-// One adjacency entry re-read after the collision, so that the 18 entries need
-// not stay in registers across it (the volatile load is never merged with the
-// first read; it hits L1).
-__device__ __forceinline__ int ld_index_again(const int32_t* p) {
-  int v;
-  asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(p));
-  return v;
-}
-
-template <bool RIA>
-__device__ __forceinline__ int nbr_again(const DevTables& t, RiaCursor c, int n, int i) {
-  if (RIA) {
-    const int a = ld_index_again(t.run_adj + at(i, t.rpad, c.r));
-    return a >= 0 ? a + c.off : a;
-  }
-  return ld_index_again(t.adj + at(i, t.npad, n));
-}
-
 __device__ __forceinline__ void nbr_ria(const DevTables& t, RiaCursor c, int (&m)[18]) {
 #pragma unroll
   for (int i = 0; i < 18; ++i) {
@@ -170,6 +152,7 @@ template <class R> struct CollConst {
   R fs;       // 9 a+ / 18 = a+/2   (axis-class scale of F in S+)
   R fo;       // 3 a- / 18 = a-/6   (axis-class scale of F in S-)
   R omlp;     // 1 - l+
+  R gs[10], go[10];  // per pair k (first direction a = 2k-1): w_a-class S+ / S- scales times c_a . g
   R rho_s;
   R abb_in[2], abb_out[2];  // 2 w (rho_bc - rho_s) for w = 1/18 and 1/36
 };
@@ -191,6 +174,14 @@ template <class R> inline CollConst<R> make_coll(const KParams& kp) {
   c.fs = R(ap / 2.0);
   c.fo = R(am / 6.0);
   c.omlp = R(1.0 - kp.lp);
+  for (int k = 1; k <= 9; ++k) {
+    const int a = 2 * k - 1;
+    const double cg = kCX[a] * kp.g[0] + kCY[a] * kp.g[1] + kCZ[a] * kp.g[2];
+    const double wscale = a <= 6 ? 1.0 : 0.5;  // diagonal class: half of the axis-class scale
+    c.gs[k] = R(wscale * (ap / 2.0) * cg);
+    c.go[k] = R(wscale * (am / 6.0) * cg);
+  }
+  c.gs[0] = c.go[0] = R(0.0);
   c.rho_s = R(kp.rho_s);
   for (int k = 0; k < 2; ++k) {
     const double w = k == 0 ? 1.0 / 18.0 : 1.0 / 36.0;
@@ -235,6 +226,23 @@ __device__ __forceinline__ void coll_pair(R (&d)[kQ], const R sa, const R da, co
   d[b] = Ep - Op;
 }
 
+// Same pair update with the force projections c.F (already scaled) given.
+template <class R, int K>
+__device__ __forceinline__ void coll_pair_f(R (&d)[kQ], const R sa, const R da, const R ux, const R uy, const R uz,
+                                            const R K0, const R K1, const R K2, const R cFs, const R cFo,
+                                            const R qp, const R qm) {
+  using ::fma;
+  constexpr int a = 2 * K - 1, b = 2 * K;
+  const R cu = cdot<R, cx(a), cy(a), cz(a)>(ux, uy, uz);
+  const R t = fma(K1, cu, cFs);
+  const R o = fma(K2, cu, cFo);
+  const R e = fma(cu, t, K0);
+  const R Ep = fma(qp, sa, e);
+  const R Op = fma(qm, da, o);
+  d[a] = Ep + Op;
+  d[b] = Ep - Op;
+}
+
 // s: Brinkman solid fraction of the node (DRAG only).
 template <class R, bool FORCE, bool DRAG>
 __device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const R s) {
@@ -258,6 +266,26 @@ __device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const
   R ux = fma(jx, irho, c.hg[0]);
   R uy = fma(jy, irho, c.hg[1]);
   R uz = fma(jz, irho, c.hg[2]);
+  const R uu = fma(ux, ux, fma(uy, uy, uz * uz));  // (the drag path recomputes it after scaling u)
+  if (FORCE && !DRAG) {
+    // uniform body force F = rho g: its projections are rho times per-pair constants
+    const R base = fma(-1.5f * rho, uu, drho);  // drho - 3/2 rho u.u
+    const R uF = rho * fma(ux, c.g[0], fma(uy, c.g[1], uz * c.g[2]));
+    const R K0a = fma(c.k0a, base, -c.k0b * uF);
+    const R K1a = c.k1 * rho, K2a = c.k2 * rho;
+    const R K0b = half(K0a), K1b = half(K1a), K2b = half(K2a);
+    coll_pair_f<R, 1>(d, sa[1], da[1], ux, uy, uz, K0a, K1a, K2a, rho * c.gs[1], rho * c.go[1], c.qp, c.qm);
+    coll_pair_f<R, 2>(d, sa[2], da[2], ux, uy, uz, K0a, K1a, K2a, rho * c.gs[2], rho * c.go[2], c.qp, c.qm);
+    coll_pair_f<R, 3>(d, sa[3], da[3], ux, uy, uz, K0a, K1a, K2a, rho * c.gs[3], rho * c.go[3], c.qp, c.qm);
+    coll_pair_f<R, 4>(d, sa[4], da[4], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[4], rho * c.go[4], c.qp, c.qm);
+    coll_pair_f<R, 5>(d, sa[5], da[5], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[5], rho * c.go[5], c.qp, c.qm);
+    coll_pair_f<R, 6>(d, sa[6], da[6], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[6], rho * c.go[6], c.qp, c.qm);
+    coll_pair_f<R, 7>(d, sa[7], da[7], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[7], rho * c.go[7], c.qp, c.qm);
+    coll_pair_f<R, 8>(d, sa[8], da[8], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[8], rho * c.go[8], c.qp, c.qm);
+    coll_pair_f<R, 9>(d, sa[9], da[9], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[9], rho * c.go[9], c.qp, c.qm);
+    d[0] = fma(c.omlp, d[0], 6.0f * K0a);
+    return;
+  }
   R Fx = R(0), Fy = R(0), Fz = R(0);
   if (DRAG) {
     const R kd = recip(R(1) + half(s));
@@ -268,16 +296,12 @@ __device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const
     Fx = fma(-rs, ux, rho * c.g[0]);
     Fy = fma(-rs, uy, rho * c.g[1]);
     Fz = fma(-rs, uz, rho * c.g[2]);
-  } else if (FORCE) {
-    Fx = rho * c.g[0];
-    Fy = rho * c.g[1];
-    Fz = rho * c.g[2];
   }
-  const R uu = fma(ux, ux, fma(uy, uy, uz * uz));
-  const R base = fma(-1.5f * rho, uu, drho);  // drho - 3/2 rho u.u
+  const R uuv = DRAG ? fma(ux, ux, fma(uy, uy, uz * uz)) : uu;
+  const R base = fma(-1.5f * rho, uuv, drho);  // drho - 3/2 rho u.u
   R K0a;                                      // axis-class K0 = w (l+ base - 3 a+ u.F)
   R Fsx = R(0), Fsy = R(0), Fsz = R(0), Fox = R(0), Foy = R(0), Foz = R(0);
-  if (FORCE || DRAG) {
+  if (DRAG) {
     const R uF = fma(ux, Fx, fma(uy, Fy, uz * Fz));
     K0a = fma(c.k0a, base, -c.k0b * uF);
     Fsx = c.fs * Fx;
@@ -291,7 +315,7 @@ __device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const
   }
   const R K1a = c.k1 * rho, K2a = c.k2 * rho;
   const R K0b = half(K0a), K1b = half(K1a), K2b = half(K2a);
-  constexpr bool F = FORCE || DRAG;
+  constexpr bool F = DRAG;
   // axis pairs (weight 1/18)
   coll_pair<R, F, 1>(d, sa[1], da[1], ux, uy, uz, K0a, K1a, K2a, Fsx, Fsy, Fsz, Fox, Foy, Foz, c.qp, c.qm);
   coll_pair<R, F, 2>(d, sa[2], da[2], ux, uy, uz, K0a, K1a, K2a, Fsx, Fsy, Fsz, Fox, Foy, Foz, c.qp, c.qm);
@@ -412,36 +436,37 @@ __global__ void __launch_bounds__(kBlock) k_aa_even_h2(DevTables t, KParams kp, 
 // AA odd step: read f_i from the neighbour's opposite slot A[inv i][m_i], collide,
 // write p_i to A[i][m_{inv i}] -- the same 19 slots, so in place and race-free.
 template <int PREC, bool RIA, bool FORCE, bool DRAG>
-__global__ void __launch_bounds__(kBlock, MinCtasOdd<PREC>::value) k_aa_odd(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
-                                                   typename St<PREC>::T* __restrict__ A,
-                                                   const float* __restrict__ s, int N) {
+__global__ void __launch_bounds__(kBlock, MinCtasOdd<PREC>::value) k_aa_odd(DevTables t, KParams kp,
+                                                                              CollConst<typename St<PREC>::R> c,
+                                                                              typename St<PREC>::T* __restrict__ A,
+                                                                              const float* __restrict__ s, int N) {
   using R = typename St<PREC>::R;
+  // the 18 resolved entries wait out the collision in shared memory, not in
+  // registers ([18][kBlock]: lane-consecutive, conflict-free)
+  __shared__ int s_m[18][kBlock];
   const int n = blockIdx.x * kBlock + threadIdx.x;
   if (n >= N) return;
-  RiaCursor cur{0, 0};
   R d[kQ];
   {
     int m[18];
     if (RIA) {
-      cur = ria_locate(t, n);
-      nbr_ria(t, cur, m);
+      nbr_ria(t, ria_locate(t, n), m);
     } else {
       nbr_adj(t, n, m);
     }
+#pragma unroll
+    for (int j = 0; j < 18; ++j) s_m[j][threadIdx.x] = m[j];
     gather<PREC, true>(A, t.npad, n, m, d, kp.inv_scale, c, t.pressure);
   }
   const R sn = DRAG ? R(__ldg(s + n)) : R(0);
   collide<R, FORCE, DRAG>(d, c, sn);
   St<PREC>::st(A + n, d[0], kp.scale);
-  // who pulls p_i next: node mo[inv(i) - 1], or this node through a marker;
-  // all 18 re-reads are issued before the first store
-  int mo_[18];
-#pragma unroll
-  for (int j = 0; j < 18; ++j) mo_[j] = nbr_again<RIA>(t, cur, n, j);
+  // p_i goes to the slot node m_{inv i} pulls it from next (or, through a
+  // marker, to this node's own opposite slot)
   if (t.pressure) {
 #pragma unroll
     for (int i = 1; i < kQ; ++i) {
-      const int mo = mo_[inv(i) - 1];
+      const int mo = s_m[inv(i) - 1][threadIdx.x];
       R v = d[i];
       if (mo < -1) v = (mo == LBM_MARK_INLET ? c.abb_in[wclass(i) - 1] : c.abb_out[wclass(i) - 1]) - v;
       const int dir = mo >= 0 ? i : inv(i);
@@ -451,7 +476,7 @@ __global__ void __launch_bounds__(kBlock, MinCtasOdd<PREC>::value) k_aa_odd(DevT
   } else {
 #pragma unroll
     for (int i = 1; i < kQ; ++i) {
-      const int mo = mo_[inv(i) - 1];
+      const int mo = s_m[inv(i) - 1][threadIdx.x];
       const int dir = mo >= 0 ? i : inv(i);
       const int node = mo >= 0 ? mo : n;
       St<PREC>::st(A + at(dir, t.npad, node), d[i], kp.scale);
