@@ -76,6 +76,23 @@ def loop_balance(variant: str, p: int, r: float) -> float:
     raise ValueError(variant)
 
 
+def job_time_and_value(ms_local, pairs, nodes, world, device=None):
+    """Whole-job timing of replicas: the slowest rank's time and the updates of all ranks.
+
+    Every rank times the same work (``pairs`` AA even+odd pairs over ``nodes``
+    fluid nodes); the job takes as long as the slowest rank (max over ranks),
+    and its throughput counts every rank's updates (weak scaling).
+    """
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t)
+    return ms, world * 2 * nodes * pairs / (ms / 1e3) / 1e9
+
+
 def peaks():
     try:
         with open(MEASURED_PEAKS) as f:
@@ -489,14 +506,9 @@ def main():
         stop.record(stream)
         barrier()
     solver.t += 2 * (args.warmup + K)
-    ms = start.elapsed_time(stop)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t)
+    ms, value = job_time_and_value(start.elapsed_time(stop), K, N, world, dev)
     even_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / K
     odd_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / K
-    value = world * 2 * N * K / (ms / 1e3) / 1e9
     # mass check of the timed run (walls + periodic faces conserve mass)
     _, _, sums = solver.macroscopic(fields=False)
     mass = float(sums[0])

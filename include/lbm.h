@@ -166,6 +166,15 @@ LBM_API int lbm_lattice_info(const lbm_lattice* lat, int64_t* N, int64_t* Npad, 
 LBM_API int lbm_export_tables(const lbm_lattice* lat, int32_t* node_xyz, int32_t* adj,
                       int32_t* run_start, int32_t* run_adj);
 
+/* Adjacency entries of chosen nodes only (lattices too large to export in
+ * full).  nodes: host int64 [count] in [0, N); out: host int32 [18][count]. */
+LBM_API int lbm_export_adjacency_rows(const lbm_lattice* lat, const int64_t* nodes, int64_t count, int32_t* out);
+
+/* LBM_OK if the `count` doubles at device address `values` (e.g. the sums of
+ * lbm_macroscopic) are all finite, LBM_ERR_NONFINITE otherwise.  Synchronises
+ * `stream` to read them; a guard between steps, not for the timed loop. */
+LBM_API int lbm_check_finite(const double* values, int64_t count, void* stream);
+
 /* Check the host tables: entries in range, adjacency reciprocity
  * (adj[i][n] = m >= 0  <=>  adj[inv i][m] = n), run table decoding back to the
  * adjacency list exactly, runs sorted and covering [0, N).  Returns

@@ -165,6 +165,15 @@ class Lattice:
     def validate(self):
         check(_lib.load().lbm_validate_tables(self._h), "lbm_validate_tables")
 
+    def adjacency_rows(self, nodes):
+        """Adjacency entries [18, len(nodes)] of the given nodes (large lattices)."""
+        nodes = np.ascontiguousarray(nodes, dtype=np.int64)
+        out = np.empty((18, len(nodes)), np.int32)
+        check(_lib.load().lbm_export_adjacency_rows(self._h, nodes.ctypes.data_as(ctypes.c_void_p), len(nodes),
+                                                    out.ctypes.data_as(ctypes.c_void_p)),
+              "lbm_export_adjacency_rows")
+        return out
+
     def device_table_bytes(self, which=LBM_TABLES_ADJ | LBM_TABLES_RIA) -> int:
         b = ctypes.c_size_t()
         check(_lib.load().lbm_device_table_bytes(self._h, which, ctypes.byref(b)), "lbm_device_table_bytes")
@@ -294,6 +303,14 @@ def lbm_macroscopic_noalloc(lat, prec, params, pdf, layout, s=None, rho=None, u=
     check(_lib.load().lbm_macroscopic_noalloc(lat.handle, prec, ctypes.byref(params.c()), _ptr(pdf), layout,
                                               _ptr(_check_s(lat, s)), _ptr(rho), _ptr(u), _ptr(sums),
                                               _stream(stream)), "lbm_macroscopic_noalloc")
+
+
+def lbm_check_finite(values, stream=None):
+    """Raise LbmError(LBM_ERR_NONFINITE) if a float64 CUDA tensor holds NaN or Inf."""
+    torch = _torch()
+    if not values.is_cuda or values.dtype != torch.float64 or not values.is_contiguous():
+        raise TypeError("values must be a contiguous CUDA float64 tensor")
+    check(_lib.load().lbm_check_finite(_ptr(values), values.numel(), _stream(stream)), "lbm_check_finite")
 
 
 def _adjoint_dtype(prec):
@@ -462,5 +479,5 @@ __all__ = [
     "lbm_step_osnt", "lbm_step_aa", "lbm_run_aa", "lbm_macroscopic", "LBM_F64", "LBM_F32", "LBM_F16S", "LBM_F64_DF",
     "LBM_LAYOUT_OSNT", "LBM_LAYOUT_AA_EVEN", "LBM_LAYOUT_AA_ODD", "LBM_TABLES_ADJ", "LBM_TABLES_RIA",
     "lbm_objective_flux", "lbm_adjoint_step", "lbm_ckpt_workspace_bytes", "lbm_flux_forward", "lbm_flux_backward",
-    "flux_objective", "new_adjoint", "lbm_macroscopic_noalloc",
+    "flux_objective", "new_adjoint", "lbm_macroscopic_noalloc", "lbm_check_finite",
 ]

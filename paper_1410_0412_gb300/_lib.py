@@ -68,6 +68,8 @@ SIGNATURES = {
     "lbm_lattice_info": [_P, _PI64, _PI64, _PI64, _PI64],
     "lbm_export_tables": [_P, _P, _P, _P, _P],
     "lbm_validate_tables": [_P],
+    "lbm_export_adjacency_rows": [_P, _P, _I64, _P],
+    "lbm_check_finite": [_P, _I64, _P],
     "lbm_device_table_bytes": [_P, _I, _PSZ],
     "lbm_lattice_upload": [_P, _I, _P, _SZ, _P],
     "lbm_pdf_bytes": [_P, _I, _PSZ],

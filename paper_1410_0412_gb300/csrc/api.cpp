@@ -206,6 +206,30 @@ int lbm_export_tables(const lbm_lattice* L, int32_t* node_xyz, int32_t* adj, int
   return LBM_OK;
 }
 
+int lbm_export_adjacency_rows(const lbm_lattice* L, const int64_t* nodes, int64_t count, int32_t* out) {
+  if (int rc = check_lat(L)) return rc;
+  if (count < 0 || (count > 0 && (!nodes || !out))) return set_error(LBM_ERR_ARG, "nodes or out is NULL");
+  for (int64_t k = 0; k < count; ++k)
+    if (nodes[k] < 0 || nodes[k] >= L->N) return set_error(LBM_ERR_ARG, "node index out of range");
+  for (int i = 0; i < 18; ++i)
+    for (int64_t k = 0; k < count; ++k) out[i * count + k] = L->adj[i * L->Npad + nodes[k]];
+  return LBM_OK;
+}
+
+int lbm_check_finite(const double* values, int64_t count, void* stream) {
+  if (count < 0 || (count > 0 && !values)) return set_error(LBM_ERR_ARG, "values is NULL");
+  if (count == 0) return LBM_OK;
+  std::vector<double> h(size_t(count), 0.0);
+  auto st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(h.data(), values, size_t(count) * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return set_error(LBM_ERR_CUDA, std::string("check_finite: ") + cudaGetErrorString(e));
+  for (int64_t k = 0; k < count; ++k)
+    if (!std::isfinite(h[size_t(k)]))
+      return set_error(LBM_ERR_NONFINITE, "non-finite value at index " + std::to_string(k));
+  return LBM_OK;
+}
+
 int lbm_validate_tables(const lbm_lattice* L) {
   if (int rc = check_lat(L)) return rc;
   return validate(L);

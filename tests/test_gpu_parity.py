@@ -231,3 +231,21 @@ def test_missing_tables_and_bad_arguments():
         lbm.lbm_step_aa(lat, "f64", bad, a, 0)
     with pytest.raises(lbm.LbmError):
         lbm.lbm_step_aa(lat, "f16s", lbm.Params(shifted=False), lat.new_grid("f16s"), 0)
+
+
+def test_nonfinite_state_is_reported():
+    """A NaN planted in one PDF surfaces as LBM_ERR_NONFINITE from the FP64 sums guard."""
+    solid = geometry.random_voxels(12, 10, 8, 0.2, 3)
+    lat = lbm.Lattice(solid, periodic=(1, 1, 1)).upload()
+    _, lp = _params()
+    solver = lbm.Solver(lat, "f64", lp, form="aa", ria=True)
+    solver.init_equilibrium(1.0)
+    solver.step(2)
+    _, _, sums = solver.macroscopic(fields=False)
+    lbm.lbm_check_finite(sums)
+    solver.pdf[7, lat.N // 2] = float("nan")
+    solver.step(2)
+    _, _, sums = solver.macroscopic(fields=False)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_check_finite(sums)
+    assert e.value.code == 6

@@ -101,3 +101,13 @@ def test_argument_errors():
     assert e.value.code == 1
     with pytest.raises(lbm.LbmError):
         lbm.Lattice(np.zeros((2, 2, 2), np.uint8), enum="lex", B=0)
+
+
+def test_adjacency_rows_export():
+    solid = geometry.random_voxels(9, 7, 6, 0.2, 12)
+    lat = lbm.Lattice(solid, periodic=(0, 1, 0), x_pressure=True)
+    full = lat.tables()["adj"]
+    nodes = np.array([0, 5, lat.N - 1, 3, 3])
+    assert np.array_equal(lat.adjacency_rows(nodes), full[:, nodes])
+    with pytest.raises(lbm.LbmError):
+        lat.adjacency_rows(np.array([lat.N]))
