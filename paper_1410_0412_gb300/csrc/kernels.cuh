@@ -35,15 +35,14 @@ __host__ __device__ constexpr double wgt(int i) { return i == 0 ? 1.0 / 3.0 : (i
 constexpr int kBlock = 128;  // nodes per CTA of the step kernels (one node per thread)
 // Minimum resident CTAs per SM of the step kernels (caps registers at
 // 65536 / (128 * n)).  The AA odd step is latency-bound (index loads, then
-// gathers, then scattered stores), so it trades a few spills for warps: 8
-// CTAs (<= 64 registers) for FP32/FP16 and 7 for the double-float path were
-// the fastest caps measured on GB300; the native FP64 path stays at 5 (it is
-// FP64-pipe bound, and 8 spills hundreds of bytes).
+// gathers, then scattered stores): 8 CTAs (<= 64 registers) were the fastest
+// caps measured on GB300 for FP32, FP16 and the double-float path; the
+// native FP64 path stays at 5 (it is FP64-pipe bound, and 8 spills hundreds
+// of bytes).
 template <int PREC> struct MinCtas { static constexpr int value = 5; };
 template <> struct MinCtas<LBM_F64_DF> { static constexpr int value = 6; };
 template <int PREC> struct MinCtasOdd { static constexpr int value = 8; };
 template <> struct MinCtasOdd<LBM_F64> { static constexpr int value = 5; };
-template <> struct MinCtasOdd<LBM_F64_DF> { static constexpr int value = 7; };
 static_assert(kBlock % kWarpNodes == 0, "a warp must cover one run-index group");
 
 // ---- storage traits -----------------------------------------------------------------
@@ -123,6 +122,23 @@ __device__ __forceinline__ RiaCursor ria_locate(const DevTables& t, int n) {
   const int head = le ? (w << 5) + (31 - __clz(le)) : __ldg(t.warp_head0 + w);
   c.off = n - head;
   return c;
+}
+
+// One table entry read again after the collision (the volatile load is never
+// merged with the first read; it hits L1).
+__device__ __forceinline__ int ld_index_again(const int32_t* p) {
+  int v;
+  asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
+template <bool RIA>
+__device__ __forceinline__ int nbr_again(const DevTables& t, RiaCursor c, int n, int i) {
+  if (RIA) {
+    const int a = ld_index_again(t.run_adj + at(i, t.rpad, c.r));
+    return a >= 0 ? a + c.off : a;
+  }
+  return ld_index_again(t.adj + at(i, t.npad, n));
 }
 
 __device__ __forceinline__ void nbr_ria(const DevTables& t, RiaCursor c, int (&m)[18]) {
@@ -441,32 +457,42 @@ __global__ void __launch_bounds__(kBlock, MinCtasOdd<PREC>::value) k_aa_odd(DevT
                                                                               typename St<PREC>::T* __restrict__ A,
                                                                               const float* __restrict__ s, int N) {
   using R = typename St<PREC>::R;
-  // the 18 resolved entries wait out the collision in shared memory, not in
-  // registers ([18][kBlock]: lane-consecutive, conflict-free)
-  __shared__ int s_m[18][kBlock];
+  // The 18 resolved entries must survive the collision.  FP32 and the FP64
+  // paths park them in shared memory ([18][kBlock], lane-consecutive,
+  // conflict-free); the FP16 path, short of registers already, reads them
+  // again from L1 after the collision (measured faster for each on GB300).
+  constexpr bool kStash = PREC != LBM_F16S;
+  __shared__ int s_m[kStash ? 18 : 1][kBlock];
   const int n = blockIdx.x * kBlock + threadIdx.x;
   if (n >= N) return;
   R d[kQ];
+  RiaCursor cur{0, 0};
   {
     int m[18];
     if (RIA) {
-      nbr_ria(t, ria_locate(t, n), m);
+      cur = ria_locate(t, n);
+      nbr_ria(t, cur, m);
     } else {
       nbr_adj(t, n, m);
     }
+    if (kStash) {
 #pragma unroll
-    for (int j = 0; j < 18; ++j) s_m[j][threadIdx.x] = m[j];
+      for (int j = 0; j < 18; ++j) s_m[j][threadIdx.x] = m[j];
+    }
     gather<PREC, true>(A, t.npad, n, m, d, kp.inv_scale, c, t.pressure);
   }
   const R sn = DRAG ? R(__ldg(s + n)) : R(0);
   collide<R, FORCE, DRAG>(d, c, sn);
   St<PREC>::st(A + n, d[0], kp.scale);
   // p_i goes to the slot node m_{inv i} pulls it from next (or, through a
-  // marker, to this node's own opposite slot)
+  // marker, to this node's own opposite slot); re-reads are issued first
+  int mo_[18];
+#pragma unroll
+  for (int j = 0; j < 18; ++j) mo_[j] = kStash ? s_m[j][threadIdx.x] : nbr_again<RIA>(t, cur, n, j);
   if (t.pressure) {
 #pragma unroll
     for (int i = 1; i < kQ; ++i) {
-      const int mo = s_m[inv(i) - 1][threadIdx.x];
+      const int mo = mo_[inv(i) - 1];
       R v = d[i];
       if (mo < -1) v = (mo == LBM_MARK_INLET ? c.abb_in[wclass(i) - 1] : c.abb_out[wclass(i) - 1]) - v;
       const int dir = mo >= 0 ? i : inv(i);
@@ -476,7 +502,7 @@ __global__ void __launch_bounds__(kBlock, MinCtasOdd<PREC>::value) k_aa_odd(DevT
   } else {
 #pragma unroll
     for (int i = 1; i < kQ; ++i) {
-      const int mo = s_m[inv(i) - 1][threadIdx.x];
+      const int mo = mo_[inv(i) - 1];
       const int dir = mo >= 0 ? i : inv(i);
       const int node = mo >= 0 ? mo : n;
       St<PREC>::st(A + at(dir, t.npad, node), d[i], kp.scale);
