@@ -150,6 +150,25 @@ LBM_API int lbm_build_lattice(const uint8_t* solid, int X, int Y, int Z, const l
 LBM_API int lbm_lattice_from_adjacency(int64_t N, const int32_t* adj, const int32_t* node_xyz,
                                lbm_lattice** out);
 
+/* Build a lattice whose node order the caller gives: node_xyz (host [N][3],
+ * x y z) must list every fluid voxel of `solid` exactly once.  Adjacency and
+ * RIA tables follow as in lbm_build_lattice.  Used for the paper's two-stage
+ * renumbering (Sect. 6.1) and any other enumeration. */
+LBM_API int lbm_build_lattice_ordered(const uint8_t* solid, int X, int Y, int Z, const lbm_bc* bc,
+                                      const int32_t* node_xyz, int64_t N, lbm_lattice** out);
+
+/* The paper's two-stage renumbering (Sect. 1, Sect. 6.1): cut the current node
+ * order into P equal chunks (chunk p = nodes [N p / P, N (p+1) / P)), as the
+ * paper partitions the adjacency list among processes, and re-sort every chunk
+ * lexicographically (x fastest, B = 1).  Writes the new order to node_xyz_out
+ * (host [N][3]); build it with lbm_build_lattice_ordered. */
+LBM_API int lbm_renumber_partitions(const lbm_lattice* lat, int P, int32_t* node_xyz_out);
+
+/* Ghost PDFs of the same P-chunk partitioning: ghost_pdfs[p] (host int64 [P])
+ * counts the pulls of chunk p's nodes from fluid nodes in other chunks, i.e.
+ * the PDFs chunk p must receive every step (Sect. 6, communication volume). */
+LBM_API int lbm_partition_ghosts(const lbm_lattice* lat, int P, int64_t* ghost_pdfs);
+
 /* Release a handle (NULL is ignored).  Device buffers are the caller's. */
 LBM_API void lbm_free_lattice(lbm_lattice* lat);
 
@@ -271,6 +290,17 @@ LBM_API int lbm_macroscopic(const lbm_lattice* lat, int prec, const lbm_params* 
 LBM_API int lbm_macroscopic_noalloc(const lbm_lattice* lat, int prec, const lbm_params* params, const void* pdf,
                                     int layout, const float* s, double* rho, double* u, double* sums,
                                     void* stream);
+
+/* ---- pattern-specific bandwidth kernels ---------------------------------------- */
+/* The GPU counterparts of the paper's micro-benchmarks (Sect. 5.2, Table 3),
+ * which give the bandwidth b of the roofline P = b / B_l for each access
+ * pattern.  kind 0 (CNT-kA): copy `arrays` arrays of bytes_per_array bytes from
+ * src to dst with streaming stores (the OS-NT pattern); kind 1 (U-kA): update
+ * the arrays of dst in place (the AA even-step pattern; src unused).  The
+ * arrays are consecutive slices of each buffer.  bytes_per_array: a positive
+ * multiple of 16; buffers 16-byte aligned.  One launch, asynchronous. */
+LBM_API int lbm_bandwidth_kernel(int kind, const void* src, void* dst, int64_t bytes_per_array, int arrays,
+                                 void* stream);
 
 /* ---- objective, discrete adjoint and checkpointed gradient ------------------------ */
 /* None of these has a counterpart in the paper: they differentiate the step of

@@ -245,3 +245,31 @@ class Tables:
         self.adj = adjacency(solid, self.node_xyz, self.periodic, self.x_pressure)
         self.run_start, self.run_adj = ria_tables(self.adj)
         self.R = len(self.run_start) - 1
+
+
+# ---------------------------------------------------------------------------
+# Partitioning and the two-stage renumbering (Sect. 1, Sect. 6.1)
+# ---------------------------------------------------------------------------
+
+def partition_bounds(N: int, P: int):
+    """Chunk p of an equal P-way cut of the node list is [N p / P, N (p+1) / P)."""
+    return [(N * p // P, N * (p + 1) // P) for p in range(P)]
+
+
+def renumber_partitions(node_xyz: np.ndarray, P: int) -> np.ndarray:
+    """Cut the node order into P chunks and sort each chunk lexicographically (x fastest)."""
+    out = []
+    for a, b in partition_bounds(len(node_xyz), P):
+        c = node_xyz[a:b]
+        out.append(c[np.lexsort((c[:, 0], c[:, 1], c[:, 2]))])
+    return np.concatenate(out) if out else node_xyz.copy()
+
+
+def partition_ghosts(adj: np.ndarray, P: int) -> np.ndarray:
+    """PDFs each chunk pulls from fluid nodes of other chunks, per step."""
+    N = adj.shape[1]
+    g = np.zeros(P, dtype=np.int64)
+    for p, (a, b) in enumerate(partition_bounds(N, P)):
+        m = adj[:, a:b].astype(np.int64)
+        g[p] = int(((m >= 0) & ((m < a) | (m >= b))).sum())
+    return g

@@ -125,6 +125,36 @@ class Lattice:
         self._info()
 
     @classmethod
+    def from_order(cls, solid, node_xyz, periodic=(0, 0, 0), x_pressure=False):
+        """A lattice with the caller's node order (every fluid voxel once)."""
+        solid = np.ascontiguousarray(solid, dtype=np.uint8)
+        Z, Y, X = solid.shape
+        xyz = np.ascontiguousarray(node_xyz, dtype=np.int32)
+        bc = _lib.lbm_bc()
+        for a in range(3):
+            bc.periodic[a] = 1 if periodic[a] else 0
+        bc.x_pressure = 1 if x_pressure else 0
+        h = ctypes.c_void_p()
+        check(_lib.load().lbm_build_lattice_ordered(solid.ctypes.data_as(ctypes.c_void_p), X, Y, Z, ctypes.byref(bc),
+                                                    xyz.ctypes.data_as(ctypes.c_void_p), len(xyz), ctypes.byref(h)),
+              "lbm_build_lattice_ordered")
+        return cls(_handle=h)
+
+    def renumber_partitions(self, P):
+        """Node order after the two-stage renumbering: P chunks, each re-sorted lexicographically."""
+        out = np.empty((self.N, 3), np.int32)
+        check(_lib.load().lbm_renumber_partitions(self._h, int(P), out.ctypes.data_as(ctypes.c_void_p)),
+              "lbm_renumber_partitions")
+        return out
+
+    def partition_ghosts(self, P):
+        """Ghost PDFs per chunk of a P-way split of the node list."""
+        out = np.empty(int(P), np.int64)
+        check(_lib.load().lbm_partition_ghosts(self._h, int(P), out.ctypes.data_as(ctypes.c_void_p)),
+              "lbm_partition_ghosts")
+        return out
+
+    @classmethod
     def from_adjacency(cls, adj, node_xyz=None):
         adj = np.ascontiguousarray(adj, dtype=np.int32)
         N = adj.shape[1]
@@ -313,6 +343,16 @@ def lbm_check_finite(values, stream=None):
     check(_lib.load().lbm_check_finite(_ptr(values), values.numel(), _stream(stream)), "lbm_check_finite")
 
 
+def lbm_bandwidth_kernel(kind, dst, src=None, arrays=1, stream=None):
+    """One launch of the CNT-kA (kind 0, copy src -> dst with streaming stores) or
+    U-kA (kind 1, update dst in place) bandwidth kernel over ``arrays`` equal
+    slices of the CUDA tensors (their byte size / arrays each)."""
+    nbytes = dst.numel() * dst.element_size()
+    per = nbytes // arrays
+    check(_lib.load().lbm_bandwidth_kernel(int(kind), _ptr(src), _ptr(dst), per, int(arrays), _stream(stream)),
+          "lbm_bandwidth_kernel")
+
+
 def _adjoint_dtype(prec):
     torch = _torch()
     return torch.float64 if prec in (LBM_F64, LBM_F64_DF) else torch.float32
@@ -479,5 +519,5 @@ __all__ = [
     "lbm_step_osnt", "lbm_step_aa", "lbm_run_aa", "lbm_macroscopic", "LBM_F64", "LBM_F32", "LBM_F16S", "LBM_F64_DF",
     "LBM_LAYOUT_OSNT", "LBM_LAYOUT_AA_EVEN", "LBM_LAYOUT_AA_ODD", "LBM_TABLES_ADJ", "LBM_TABLES_RIA",
     "lbm_objective_flux", "lbm_adjoint_step", "lbm_ckpt_workspace_bytes", "lbm_flux_forward", "lbm_flux_backward",
-    "flux_objective", "new_adjoint", "lbm_macroscopic_noalloc", "lbm_check_finite",
+    "flux_objective", "new_adjoint", "lbm_macroscopic_noalloc", "lbm_check_finite", "lbm_bandwidth_kernel",
 ]

@@ -64,6 +64,9 @@ SIGNATURES = {
     "lbm_last_error": [],
     "lbm_build_lattice": [_P, _I, _I, _I, ctypes.POINTER(lbm_bc), _I, _I, ctypes.POINTER(_P)],
     "lbm_lattice_from_adjacency": [_I64, _P, _P, ctypes.POINTER(_P)],
+    "lbm_build_lattice_ordered": [_P, _I, _I, _I, ctypes.POINTER(lbm_bc), _P, _I64, ctypes.POINTER(_P)],
+    "lbm_renumber_partitions": [_P, _I, _P],
+    "lbm_partition_ghosts": [_P, _I, _P],
     "lbm_free_lattice": [_P],
     "lbm_lattice_info": [_P, _PI64, _PI64, _PI64, _PI64],
     "lbm_export_tables": [_P, _P, _P, _P, _P],
@@ -81,6 +84,7 @@ SIGNATURES = {
     "lbm_run_aa": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _I, _P, _I, _P],
     "lbm_reduce_workspace_bytes": [_P, _PSZ],
     "lbm_macroscopic": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _P, _P, _P, _P, _P, _SZ, _P],
+    "lbm_bandwidth_kernel": [_I, _P, _P, _I64, _I, _P],
     "lbm_macroscopic_noalloc": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _P, _P, _P, _P, _P],
     "lbm_objective_flux": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _P, _P, _P, _P, _P, _SZ, _P],
     "lbm_adjoint_step": [_P, _I, ctypes.POINTER(lbm_params), _P, _P, _P, _P, _P, _I, _P],

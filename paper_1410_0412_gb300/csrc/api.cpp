@@ -153,6 +153,52 @@ int lbm_build_lattice(const uint8_t* solid, int X, int Y, int Z, const lbm_bc* b
   return LBM_OK;
 }
 
+int lbm_build_lattice_ordered(const uint8_t* solid, int X, int Y, int Z, const lbm_bc* bc, const int32_t* node_xyz,
+                              int64_t N, lbm_lattice** out) {
+  if (!out) return set_error(LBM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!solid || !bc || (N > 0 && !node_xyz)) return set_error(LBM_ERR_ARG, "solid, bc or node_xyz is NULL");
+  if (X < 1 || Y < 1 || Z < 1) return set_error(LBM_ERR_ARG, "box dimensions must be >= 1");
+  if (int64_t(X) * Y * Z >= (int64_t(1) << 40)) return set_error(LBM_ERR_ARG, "box too large");
+  if (N < 0 || N > INT32_MAX) return set_error(LBM_ERR_ARG, "N out of range");
+  if (bc->x_pressure && bc->periodic[0]) return set_error(LBM_ERR_ARG, "x cannot be periodic and a pressure axis");
+  lbm_lattice* L = new (std::nothrow) lbm_lattice();
+  if (!L) return set_error(LBM_ERR_ALLOC, "out of host memory");
+  L->X = X;
+  L->Y = Y;
+  L->Z = Z;
+  for (int a = 0; a < 3; ++a) L->bc.periodic[a] = bc->periodic[a] ? 1 : 0;
+  L->bc.x_pressure = bc->x_pressure ? 1 : 0;
+  L->enumeration = -1;
+  int rc;
+  try {
+    rc = build_tables_from_order(L, solid, node_xyz, N);
+  } catch (const std::bad_alloc&) {
+    rc = set_error(LBM_ERR_ALLOC, "out of host memory while building tables");
+  }
+  if (rc) {
+    delete L;
+    return rc;
+  }
+  *out = L;
+  return LBM_OK;
+}
+
+int lbm_renumber_partitions(const lbm_lattice* L, int P, int32_t* node_xyz_out) {
+  if (int rc = check_lat(L)) return rc;
+  if (P < 1 || P > L->N) return set_error(LBM_ERR_ARG, "P must be in [1, N]");
+  if (!node_xyz_out) return set_error(LBM_ERR_ARG, "node_xyz_out is NULL");
+  if (int64_t(L->node_xyz.size()) != 3 * L->N) return set_error(LBM_ERR_ARG, "lattice has no node coordinates");
+  return renumber_partitions(L, P, node_xyz_out);
+}
+
+int lbm_partition_ghosts(const lbm_lattice* L, int P, int64_t* ghost_pdfs) {
+  if (int rc = check_lat(L)) return rc;
+  if (P < 1 || P > std::max<int64_t>(L->N, 1)) return set_error(LBM_ERR_ARG, "P must be in [1, N]");
+  if (!ghost_pdfs) return set_error(LBM_ERR_ARG, "ghost_pdfs is NULL");
+  return partition_ghosts(L, P, ghost_pdfs);
+}
+
 int lbm_lattice_from_adjacency(int64_t N, const int32_t* adj, const int32_t* node_xyz, lbm_lattice** out) {
   if (!out) return set_error(LBM_ERR_ARG, "out is NULL");
   *out = nullptr;

@@ -66,6 +66,9 @@ int set_error(int code, const std::string& msg);
 
 // Host table construction (lattice.cpp).
 int build_tables(lbm_lattice* L, const uint8_t* solid);
+int build_tables_from_order(lbm_lattice* L, const uint8_t* solid, const int32_t* node_xyz, int64_t N);
+int renumber_partitions(const lbm_lattice* L, int P, int32_t* out);
+int partition_ghosts(const lbm_lattice* L, int P, int64_t* ghosts);
 int derive_ria(lbm_lattice* L);
 int validate(const lbm_lattice* L);
 

@@ -345,6 +345,64 @@ int derive_ria(lbm_lattice* L) {
   return LBM_OK;
 }
 
+int build_tables_from_order(lbm_lattice* L, const uint8_t* solid, const int32_t* node_xyz, int64_t N) {
+  const int64_t X = L->X, Y = L->Y, Z = L->Z;
+  // every fluid voxel exactly once, nothing else
+  std::vector<uint8_t> seen(X * Y * Z, 0);
+  int64_t fluid = 0;
+  for (int64_t v = 0; v < X * Y * Z; ++v) fluid += solid[v] == 0;
+  if (fluid != N) return set_error(LBM_ERR_ARG, "node list length differs from the number of fluid voxels");
+  for (int64_t n = 0; n < N; ++n) {
+    const int32_t x = node_xyz[3 * n], y = node_xyz[3 * n + 1], z = node_xyz[3 * n + 2];
+    if (x < 0 || x >= X || y < 0 || y >= Y || z < 0 || z >= Z)
+      return set_error(LBM_ERR_ARG, "node outside the box at position " + std::to_string(n));
+    const int64_t v = (int64_t(z) * Y + y) * X + x;
+    if (solid[v] || seen[v]) return set_error(LBM_ERR_ARG, "node list repeats a voxel or names a solid one");
+    seen[v] = 1;
+  }
+  L->N = N;
+  L->node_xyz.assign(node_xyz, node_xyz + 3 * N);
+  L->Npad = round_up(std::max<int64_t>(L->N, 1), kPad);
+  if (int rc = fill_adjacency(L)) return rc;
+  return derive_ria(L);
+}
+
+int renumber_partitions(const lbm_lattice* L, int P, int32_t* out) {
+  const int64_t N = L->N;
+  const int64_t Xs = L->X, Ys = L->Y;
+  std::vector<int64_t> idx(N);
+  for (int64_t n = 0; n < N; ++n) idx[n] = n;
+  auto key = [&](int64_t n) {
+    const int32_t* p = &L->node_xyz[3 * n];
+    return (int64_t(p[2]) * Ys + p[1]) * Xs + p[0];
+  };
+  parallel_for(P, [&](int64_t pb, int64_t pe) {
+    for (int64_t p = pb; p < pe; ++p) {
+      const int64_t a = N * p / P, b = N * (p + 1) / P;
+      std::sort(idx.begin() + a, idx.begin() + b, [&](int64_t u, int64_t v) { return key(u) < key(v); });
+    }
+  });
+  for (int64_t n = 0; n < N; ++n) std::memcpy(out + 3 * n, &L->node_xyz[3 * idx[n]], 3 * sizeof(int32_t));
+  return LBM_OK;
+}
+
+int partition_ghosts(const lbm_lattice* L, int P, int64_t* ghosts) {
+  const int64_t N = L->N, Np = L->Npad;
+  parallel_for(P, [&](int64_t pb, int64_t pe) {
+    for (int64_t p = pb; p < pe; ++p) {
+      const int64_t a = N * p / P, b = N * (p + 1) / P;
+      int64_t g = 0;
+      for (int i = 0; i < 18; ++i)
+        for (int64_t n = a; n < b; ++n) {
+          const int32_t m = L->adj[i * Np + n];
+          g += m >= 0 && (m < a || m >= b);
+        }
+      ghosts[p] = g;
+    }
+  });
+  return LBM_OK;
+}
+
 int build_tables(lbm_lattice* L, const uint8_t* solid) {
   int rc = (L->enumeration == LBM_ENUM_HILBERT) ? enumerate_hilbert(L, solid)
                                                  : enumerate_lex(L, solid, L->block_B);
