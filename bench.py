@@ -468,7 +468,34 @@ def suite_partition(args, lbm, torch):
     return out
 
 
-SUITES = {"bandwidth": suite_bandwidth, "partition": suite_partition, "channel": suite_channel, "sweep": suite_sweep, "foam": suite_foam, "adjoint": suite_adjoint,
+def suite_graph(args, lbm, torch):
+    """Launch overhead on the small sphere box (64x32x32, ~46k nodes): direct launches vs CUDA graph replay."""
+    solid = geometry.sphere_box_64x32x32(0)
+    lat = lbm.Lattice(solid, periodic=(1, 0, 0)).upload()
+    out = {"suite": "graph", "fluid_nodes": lat.N, "steps": 2000, "variants": {}}
+    w = WORKLOAD
+    for prec in ("f64", "f32"):
+        params = lbm.Params(omega_plus=1.0, magic=3 / 16, g=(1e-6, 0, 0), shifted=(prec == "f32"))
+        for form in ("osnt", "aa"):
+            rec = {}
+            for mode in ("direct", "graph"):
+                sv = lbm.Solver(lat, prec, params, form=form, ria=True)
+                sv.init_equilibrium(1.0)
+                run = sv.step if mode == "direct" else sv.step_graph
+                run(20)
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                run(2000)
+                b.record()
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(b)
+                rec[mode] = {"us_per_step": 1000 * ms / 2000, "GFLUPs": lat.N * 2000 / (ms / 1e3) / 1e9}
+            out["variants"][f"{form}_r_{prec}"] = rec
+    return out
+
+
+SUITES = {"bandwidth": suite_bandwidth, "partition": suite_partition, "graph": suite_graph, "channel": suite_channel, "sweep": suite_sweep, "foam": suite_foam, "adjoint": suite_adjoint,
           "large": suite_large}
 
 
@@ -513,7 +540,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--box", type=int, default=None, help="smaller cubic bed (profiling only)")
     ap.add_argument("--suite", default=None, choices=sorted(["bandwidth", "channel", "sweep", "foam", "adjoint",
-                                                             "large", "partition"]),
+                                                             "large", "partition", "graph"]),
                     help="measure another configuration instead of the headline (one JSON line)")
     ap.add_argument("--radius", type=float, default=None, help="foam strut radius (suites foam/large)")
     ap.add_argument("--foam-steps", type=int, default=2000)

@@ -27,10 +27,37 @@ template <class R> struct AdjConst {
   R qp, qm;          // (1 - l+)/2, (1 - l-)/2
   R g[3], hg[3];
   R rho_s;
+  R w[3];            // D3Q19 weights 1/3, 1/18, 1/36
+  R omlp;            // 1 - l+
+};
+
+// Storage of the adjoint arrays: IEEE double for both FP64 paths (the
+// double-float one converts on load and store), float otherwise.
+template <int PREC> struct Lam {
+  using T = float;
+  static __device__ __forceinline__ float ld(const T* p) { return *p; }
+  static __device__ __forceinline__ void st(T* p, float v) { *p = v; }
+  static __device__ __forceinline__ double to_double(float v) { return double(v); }
+};
+template <> struct Lam<LBM_F64> {
+  using T = double;
+  static __device__ __forceinline__ double ld(const T* p) { return *p; }
+  static __device__ __forceinline__ void st(T* p, double v) { *p = v; }
+  static __device__ __forceinline__ double to_double(double v) { return v; }
+};
+template <> struct Lam<LBM_F64_DF> {
+  using T = double;
+  static __device__ __forceinline__ df ld(const T* p) { return df_from_double(*p); }
+  static __device__ __forceinline__ void st(T* p, df v) { *p = double_from_df(v); }
+  static __device__ __forceinline__ double to_double(df v) { return double_from_df(v); }
 };
 
 template <class R> AdjConst<R> make_adj(const KParams& kp) {
   AdjConst<R> c;
+  c.w[0] = R(1.0 / 3.0);
+  c.w[1] = R(1.0 / 18.0);
+  c.w[2] = R(1.0 / 36.0);
+  c.omlp = R(1.0 - kp.lp);
   c.lp = R(kp.lp);
   c.lm = R(kp.lm);
   c.ap = R(1.0 - kp.lp / 2);
@@ -51,58 +78,57 @@ template <int PREC, bool RIA, bool DRAG>
 __global__ void __launch_bounds__(kBlock) k_adjoint(DevTables t, KParams kp, CollConst<typename St<PREC>::R> cc,
                                                     AdjConst<typename St<PREC>::R> c,
                                                     const typename St<PREC>::T* __restrict__ G,
-                                                    const typename St<PREC>::R* __restrict__ lam_next,
-                                                    typename St<PREC>::R* __restrict__ lam,
+                                                    const typename Lam<PREC>::T* __restrict__ lam_next,
+                                                    typename Lam<PREC>::T* __restrict__ lam,
                                                     const float* __restrict__ s, double* __restrict__ grad_s, int N) {
   using R = typename St<PREC>::R;
+  using L = Lam<PREC>;
   using ::fma;
-  const int n0 = blockIdx.x * kBlock;
-  const int n = n0 + threadIdx.x;
+  const int n = blockIdx.x * kBlock + threadIdx.x;
+  if (n >= N) return;
   int m[18];
   if (RIA) {
-    if (n >= N) return;
     nbr_ria(t, ria_locate(t, n), m);
   } else {
-    if (n >= N) return;
     nbr_adj(t, n, m);
   }
   // forward quantities of F_n
   R d[kQ];
   gather<PREC, false>(G, t.npad, n, m, d, kp.inv_scale, cc, t.pressure);
-  R drho = R(0), jx = R(0), jy = R(0), jz = R(0);
+  R drho = d[0], jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) {
+  for (int i = 1; i < kQ; ++i) {
     drho += d[i];
     if (cx(i)) jx += cx(i) > 0 ? d[i] : -d[i];
     if (cy(i)) jy += cy(i) > 0 ? d[i] : -d[i];
     if (cz(i)) jz += cz(i) > 0 ? d[i] : -d[i];
   }
   const R rho = c.rho_s + drho;
-  const R irho = R(1) / rho;
+  const R irho = recip(rho);
   const R sn = DRAG ? R(__ldg(s + n)) : R(0);
-  const R kd = DRAG ? R(1) / (R(1) + R(0.5) * sn) : R(1);
+  const R kd = DRAG ? recip(R(1) + half(sn)) : R(1);
   const R ux = fma(jx, irho, c.hg[0]) * kd, uy = fma(jy, irho, c.hg[1]) * kd, uz = fma(jz, irho, c.hg[2]) * kd;
   // mu = S^T lambda_{n+1}: slot (j, n) of the post-collision state is pulled by
   // node m_{inv j} (fluid) or, through a marker, by this node's inv j slot
   // (sign -1 for anti-bounce-back).
   R mu[kQ];
-  mu[0] = lam_next[n];
+  mu[0] = L::ld(lam_next + n);
 #pragma unroll
   for (int j = 1; j < kQ; ++j) {
     const int mp = m[inv(j) - 1];
     const int dir = mp >= 0 ? j : inv(j);
     const int node = mp >= 0 ? mp : n;
-    const R v = lam_next[at(dir, t.npad, node)];
+    const R v = L::ld(lam_next + at(dir, t.npad, node));
     mu[j] = mp < -1 ? -v : v;
   }
   // weighted moments of mu (pairs: even part for M0/M2, odd part for M1)
-  R M0 = R(1.0 / 3.0) * mu[0];
+  R M0 = c.w[0] * mu[0];
   R M1x = R(0), M1y = R(0), M1z = R(0);
   R Mxx = R(0), Myy = R(0), Mzz = R(0), Mxy = R(0), Mxz = R(0), Myz = R(0);
 #pragma unroll
   for (int k = 1; k <= 9; ++k) {
     const int a = 2 * k - 1;
-    const R w = R(wgt(a));
+    const R w = c.w[wclass(a)];
     const R sp = w * (mu[a] + mu[a + 1]);
     const R sm = w * (mu[a] - mu[a + 1]);
     M0 += sp;
@@ -116,39 +142,40 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(DevTables t, KParams kp, Col
     if (cx(a) && cz(a)) Mxz += cx(a) * cz(a) > 0 ? sp : -sp;
     if (cy(a) && cz(a)) Myz += cy(a) * cz(a) > 0 ? sp : -sp;
   }
-  const R M2ux = Mxx * ux + Mxy * uy + Mxz * uz;
-  const R M2uy = Mxy * ux + Myy * uy + Myz * uz;
-  const R M2uz = Mxz * ux + Myz * uy + Mzz * uz;
-  const R M2gx = Mxx * c.g[0] + Mxy * c.g[1] + Mxz * c.g[2];
-  const R M2gy = Mxy * c.g[0] + Myy * c.g[1] + Myz * c.g[2];
-  const R M2gz = Mxz * c.g[0] + Myz * c.g[1] + Mzz * c.g[2];
-  const R uu = ux * ux + uy * uy + uz * uz;
-  const R q = ux * M2ux + uy * M2uy + uz * M2uz;
-  const R av = M1x * ux + M1y * uy + M1z * uz;
-  const R ug = ux * c.g[0] + uy * c.g[1] + uz * c.g[2];
-  const R uM2g = ux * M2gx + uy * M2gy + uz * M2gz;
-  const R M1g = M1x * c.g[0] + M1y * c.g[1] + M1z * c.g[2];
+  const R M2ux = fma(Mxx, ux, fma(Mxy, uy, Mxz * uz));
+  const R M2uy = fma(Mxy, ux, fma(Myy, uy, Myz * uz));
+  const R M2uz = fma(Mxz, ux, fma(Myz, uy, Mzz * uz));
+  const R M2gx = fma(Mxx, c.g[0], fma(Mxy, c.g[1], Mxz * c.g[2]));
+  const R M2gy = fma(Mxy, c.g[0], fma(Myy, c.g[1], Myz * c.g[2]));
+  const R M2gz = fma(Mxz, c.g[0], fma(Myz, c.g[1], Mzz * c.g[2]));
+  const R uu = fma(ux, ux, fma(uy, uy, uz * uz));
+  const R q = fma(ux, M2ux, fma(uy, M2uy, uz * M2uz));
+  const R av = fma(M1x, ux, fma(M1y, uy, M1z * uz));
+  const R ug = fma(ux, c.g[0], fma(uy, c.g[1], uz * c.g[2]));
+  const R uM2g = fma(ux, M2gx, fma(uy, M2gy, uz * M2gz));
+  const R M1g = fma(M1x, c.g[0], fma(M1y, c.g[1], M1z * c.g[2]));
   const R lp = c.lp, lm = c.lm, ap = c.ap, am = c.am;
-  R Psi = lp * M0 * (R(1) - R(1.5) * uu) + R(4.5) * lp * q + R(3) * lm * av + R(9) * ap * uM2g -
-          R(3) * ap * M0 * ug + R(3) * am * M1g;
-  // dPsi/du
-  R Px = -R(3) * lp * M0 * ux + R(9) * lp * M2ux + R(3) * lm * M1x + R(9) * ap * M2gx - R(3) * ap * M0 * c.g[0];
-  R Py = -R(3) * lp * M0 * uy + R(9) * lp * M2uy + R(3) * lm * M1y + R(9) * ap * M2gy - R(3) * ap * M0 * c.g[1];
-  R Pz = -R(3) * lp * M0 * uz + R(9) * lp * M2uz + R(3) * lm * M1z + R(9) * ap * M2gz - R(3) * ap * M0 * c.g[2];
+  const R lpM0 = lp * M0, apM0 = ap * M0;
+  // Psi and dPsi/du (see the header comment)
+  R Psi = lpM0 * fma(-1.5f * uu, R(1), R(1)) + 4.5f * (lp * q) + 3.0f * (lm * av) + 9.0f * (ap * uM2g) -
+          3.0f * (apM0 * ug) + 3.0f * (am * M1g);
+  R Px = -3.0f * (lpM0 * ux) + 9.0f * (lp * M2ux) + 3.0f * (lm * M1x) + 9.0f * (ap * M2gx) - 3.0f * (apM0 * c.g[0]);
+  R Py = -3.0f * (lpM0 * uy) + 9.0f * (lp * M2uy) + 3.0f * (lm * M1y) + 9.0f * (ap * M2gy) - 3.0f * (apM0 * c.g[1]);
+  R Pz = -3.0f * (lpM0 * uz) + 9.0f * (lp * M2uz) + 3.0f * (lm * M1z) + 9.0f * (ap * M2gz) - 3.0f * (apM0 * c.g[2]);
+  const R dPsi_ds = -9.0f * (ap * q) + 3.0f * (apM0 * uu) - 3.0f * (am * av);
   if (DRAG) {
-    Psi += sn * (-R(9) * ap * q + R(3) * ap * M0 * uu - R(3) * am * av);
-    Px += sn * (-R(18) * ap * M2ux + R(6) * ap * M0 * ux - R(3) * am * M1x);
-    Py += sn * (-R(18) * ap * M2uy + R(6) * ap * M0 * uy - R(3) * am * M1y);
-    Pz += sn * (-R(18) * ap * M2uz + R(6) * ap * M0 * uz - R(3) * am * M1z);
+    Psi += sn * dPsi_ds;
+    Px += sn * (-18.0f * (ap * M2ux) + 6.0f * (apM0 * ux) - 3.0f * (am * M1x));
+    Py += sn * (-18.0f * (ap * M2uy) + 6.0f * (apM0 * uy) - 3.0f * (am * M1y));
+    Pz += sn * (-18.0f * (ap * M2uz) + 6.0f * (apM0 * uz) - 3.0f * (am * M1z));
   }
   const R A = Psi - (Px * (ux - kd * c.hg[0]) + Py * (uy - kd * c.hg[1]) + Pz * (uz - kd * c.hg[2]));
   const R Bx = kd * Px, By = kd * Py, Bz = kd * Pz;
   if (grad_s) {
-    const R dPsi_ds = -R(9) * ap * q + R(3) * ap * M0 * uu - R(3) * am * av;
-    const R gs = rho * (dPsi_ds - R(0.5) * kd * (Px * ux + Py * uy + Pz * uz));
-    grad_s[n] += double(gs);
+    const R gs = rho * (dPsi_ds - half(kd) * (Px * ux + Py * uy + Pz * uz));
+    grad_s[n] += L::to_double(gs);
   }
-  lam[n] = R(2) * c.qp * mu[0] + A;
+  L::st(lam + n, fma(c.omlp, mu[0], A));
 #pragma unroll
   for (int k = 1; k <= 9; ++k) {
     const int a = 2 * k - 1;
@@ -159,8 +186,8 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(DevTables t, KParams kp, Col
     if (cz(a)) Bc += cz(a) > 0 ? Bz : -Bz;
     const R e = fma(c.qp, sp, A);
     const R o = fma(c.qm, sm, Bc);
-    lam[at(a, t.npad, n)] = e + o;
-    lam[at(a + 1, t.npad, n)] = e - o;
+    L::st(lam + at(a, t.npad, n), e + o);
+    L::st(lam + at(a + 1, t.npad, n), e - o);
   }
 }
 
@@ -259,13 +286,14 @@ int launch_adjoint_t(const lbm_lattice* L, const KParams& kp, const void* G, con
                      const float* s, double* grad_s, int ria, void* stream) {
   using T = typename dev::St<PREC>::T;
   using R = typename dev::St<PREC>::R;
+  using LT = typename dev::Lam<PREC>::T;
   auto st = static_cast<cudaStream_t>(stream);
   const auto cc = dev::make_coll<R>(kp);
   const auto ac = dev::make_adj<R>(kp);
   const unsigned g = grid_of(L->N);
   const T* Gp = static_cast<const T*>(G);
-  const R* ln = static_cast<const R*>(lam_next);
-  R* lo = static_cast<R*>(lam);
+  const LT* ln = static_cast<const LT*>(lam_next);
+  LT* lo = static_cast<LT*>(lam);
   const int N = int(L->N);
 #define LBM_ADJ(R_, D_) dev::k_adjoint<PREC, R_, D_><<<g, dev::kBlock, 0, st>>>(L->dev, kp, cc, ac, Gp, ln, lo, s, grad_s, N)
   if (s) {
@@ -308,6 +336,8 @@ template int launch_adjoint_t<LBM_F32>(const lbm_lattice*, const KParams&, const
                                        const float*, double*, int, void*);
 template int launch_adjoint_t<LBM_F16S>(const lbm_lattice*, const KParams&, const void*, const void*, void*,
                                         const float*, double*, int, void*);
+template int launch_adjoint_t<LBM_F64_DF>(const lbm_lattice*, const KParams&, const void*, const void*, void*,
+                                          const float*, double*, int, void*);
 template int launch_objective_t<LBM_F64>(const lbm_lattice*, const KParams&, const void*, int, const float*, double*,
                                          void*, double*, double*, void*);
 template int launch_objective_t<LBM_F32>(const lbm_lattice*, const KParams&, const void*, int, const float*, double*,

@@ -485,7 +485,8 @@ int lbm_adjoint_step(const lbm_lattice* L, int prec, const lbm_params* params, c
   if (lambda_next == lambda_n) return set_error(LBM_ERR_ARG, "lambda_next and lambda_n must differ");
   if (L->N == 0) return LBM_OK;
   if (int rc = check_tables(L, ria)) return rc;
-  return LBM_DISPATCH(prec, launch_adjoint_t, L, kp, G_n, lambda_next, lambda_n, s, grad_s, ria ? 1 : 0, stream);
+  return LBM_DISPATCH_STEP(prec, launch_adjoint_t, L, kp, G_n, lambda_next, lambda_n, s, grad_s, ria ? 1 : 0,
+                           stream);
 }
 
 }  // extern "C"
@@ -611,7 +612,8 @@ int lbm_flux_backward(const lbm_lattice* L, int prec, const lbm_params* params, 
                                      ria ? 1 : 0, stream))
         return rc;
     for (int t = t1 - 1; t >= t0; --t) {
-      if (int rc = LBM_DISPATCH(prec, launch_adjoint_t, L, kp, state(t), lamA, lamB, s, grad_s, ria ? 1 : 0, stream))
+      if (int rc = LBM_DISPATCH_STEP(prec, launch_adjoint_t, L, kp, state(t), lamA, lamB, s, grad_s, ria ? 1 : 0,
+                                     stream))
         return rc;
       std::swap(lamA, lamB);
     }

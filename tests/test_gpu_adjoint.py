@@ -33,7 +33,8 @@ def _setup(seed=0, shape=(10, 9, 8), per=(1, 0, 1), xp=False, g=(1e-3, 0, 0)):
 
 @pytest.mark.parametrize("ria", [False, True])
 @pytest.mark.parametrize("xp", [False, True])
-def test_one_step_vjp(ria, xp):
+@pytest.mark.parametrize("prec", ["f64", "f64df"])
+def test_one_step_vjp(ria, xp, prec):
     T, lat, op, lp, s = _setup(1, per=(0, 0, 1) if xp else (1, 0, 1), xp=xp)
     gen = torch.Generator().manual_seed(3)
     F = olbm.uniform_state(T.N, op, 1.0, (0.02, -0.01, 0.0))
@@ -44,13 +45,13 @@ def test_one_step_vjp(ria, xp):
     sr = s64.clone().requires_grad_(True)
     out = olbm.stream(olbm.collide(Fr, op, sr), T.adj, op)
     ref_lam, ref_gs = torch.autograd.grad(out, [Fr, sr], lam1)
-    G = lat.new_grid("f64")
-    lbm.lbm_load_canonical(lat, "f64", lp, F.cuda(), G, lbm.LBM_LAYOUT_OSNT)
-    ln = lbm.new_adjoint(lat, "f64")
+    G = lat.new_grid(prec)
+    lbm.lbm_load_canonical(lat, prec, lp, F.cuda(), G, lbm.LBM_LAYOUT_OSNT)
+    ln = lbm.new_adjoint(lat, prec)
     ln[:, :T.N] = lam1.cuda()
-    lo = lbm.new_adjoint(lat, "f64")
+    lo = lbm.new_adjoint(lat, prec)
     gs = torch.zeros(T.N, dtype=torch.float64, device="cuda")
-    lbm.lbm_adjoint_step(lat, "f64", lp, G, ln, lo, s.cuda(), gs, ria)
+    lbm.lbm_adjoint_step(lat, prec, lp, G, ln, lo, s.cuda(), gs, ria)
     got = lo[:, :T.N].cpu()
     assert float((got - ref_lam).abs().max() / ref_lam.abs().max()) <= 1e-12
     assert float((gs.cpu() - ref_gs).abs().max() / ref_gs.abs().max()) <= 1e-12
