@@ -468,6 +468,66 @@ def suite_partition(args, lbm, torch):
     return out
 
 
+def suite_exchange(args, lbm, torch):
+    """P chunks with a ghost-PDF exchange every step, all on one GPU (Sect. 6): the partitioned
+    AA-R and OS-NT-R steps against the whole-lattice ones, and the exchange kernel alone."""
+    solid = make_geometry(args.box)
+    w = WORKLOAD
+    hbm, kind = peaks()
+    out = {"suite": "exchange", "workload": WORKLOAD["name"] if not args.box else f"packed_bed_{args.box}",
+           "pairs": args.steps, "cases": {}}
+    hil = lbm.Lattice(solid, periodic=w["periodic"], enum="hilbert")
+    cases = [("lex1", lbm.Lattice(solid, periodic=w["periodic"], enum="lex", B=1), 16),
+             ("hilbert", hil, 16)]
+    for P in (16, 64):
+        cases.append((f"hilbert_renum{P}", lbm.Lattice.from_order(solid, hil.renumber_partitions(P),
+                                                                   periodic=w["periodic"]), P))
+    for name, lat, P in cases:
+        lat.upload()
+        part = lbm.Partitioning(lat, P).upload()
+        E = int(sum(part.ghost_pdfs))
+        rec = {"P": P, "r": lat.R / lat.N, "r_chunks": sum(q.R for q in part.parts) / lat.N,
+               "ghost_pdfs": E, "ghost_share": E / (18 * lat.N)}
+        for prec, pb in (("f32", 4), ("f64df", 8)):
+            params = lbm.Params(omega_plus=w["omega_plus"], magic=w["magic"], g=w["g"], shifted=(prec == "f32"))
+            for form in ("aa", "osnt"):
+                sv, whole = _time_variant(lbm, torch, lat, prec, params, form, True, args.steps)
+                del sv
+                ps = lbm.PartitionedSolver(part, prec, params, form=form, ria=True)
+                ps.init_equilibrium(1.0)
+                ps.step(4)
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                ps.step(2 * args.steps)
+                b.record()
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(b)
+                # the exchange alone: the two copies of one pair (gather + scatter, or two OS-NT fills)
+                modes = ((lbm.LBM_HALO_AA_GATHER, lbm.LBM_HALO_AA_SCATTER) if form == "aa"
+                         else (lbm.LBM_HALO_OSNT, lbm.LBM_HALO_OSNT))
+                ptrs = lbm.Partitioning.pointers(ps.grids)
+                a.record()
+                for _ in range(args.steps):
+                    for m in modes:
+                        lbm.lbm_halo_exchange(part, prec, ptrs, m)
+                b.record()
+                torch.cuda.synchronize()
+                ex_ms = a.elapsed_time(b) / args.steps
+                ex_bytes = 2 * E * (2 * pb + 8)
+                rec[f"{form}_r_{prec}"] = {
+                    "whole_GFLUPs": whole, "partitioned_GFLUPs": 2 * lat.N * args.steps / (ms / 1e3) / 1e9,
+                    "exchange_ms_per_pair": ex_ms, "exchange_GBs": ex_bytes / (ex_ms / 1e3) / 1e9,
+                    "exchange_bytes_per_pair": ex_bytes, "pair_ms": ms / args.steps}
+                del ps
+                torch.cuda.empty_cache()
+        out["cases"][name] = rec
+        del part
+        torch.cuda.empty_cache()
+    out["hbm_peak_GBs"] = hbm
+    return out
+
+
 def suite_graph(args, lbm, torch):
     """Launch overhead on the small sphere box (64x32x32, ~46k nodes): direct launches vs CUDA graph replay."""
     solid = geometry.sphere_box_64x32x32(0)
@@ -495,7 +555,8 @@ def suite_graph(args, lbm, torch):
     return out
 
 
-SUITES = {"bandwidth": suite_bandwidth, "partition": suite_partition, "graph": suite_graph, "channel": suite_channel, "sweep": suite_sweep, "foam": suite_foam, "adjoint": suite_adjoint,
+SUITES = {"bandwidth": suite_bandwidth, "partition": suite_partition, "exchange": suite_exchange,
+          "graph": suite_graph, "channel": suite_channel, "sweep": suite_sweep, "foam": suite_foam, "adjoint": suite_adjoint,
           "large": suite_large}
 
 
@@ -539,7 +600,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--box", type=int, default=None, help="smaller cubic bed (profiling only)")
-    ap.add_argument("--suite", default=None, choices=sorted(["bandwidth", "channel", "sweep", "foam", "adjoint",
+    ap.add_argument("--suite", default=None, choices=sorted(["bandwidth", "channel", "sweep", "foam", "adjoint", "exchange",
                                                              "large", "partition", "graph"]),
                     help="measure another configuration instead of the headline (one JSON line)")
     ap.add_argument("--radius", type=float, default=None, help="foam strut radius (suites foam/large)")

@@ -172,6 +172,105 @@ LBM_API int lbm_partition_ghosts(const lbm_lattice* lat, int P, int64_t* ghost_p
 /* Release a handle (NULL is ignored).  Device buffers are the caller's. */
 LBM_API void lbm_free_lattice(lbm_lattice* lat);
 
+/* ---- partitions with a ghost-PDF exchange (Sect. 6, Sect. 6.1) --------------------
+ * The distributed form of the step: the node vector is cut into the same P
+ * chunks as above and each chunk is updated on its own grids, after receiving
+ * the PDFs its nodes pull from other chunks.  One GPU holds all P grids here
+ * (the exchange kernel copies between them); the tables and the exchange are
+ * those a one-chunk-per-GPU run would use.
+ *
+ * Chunk p becomes an ordinary lattice handle ("local lattice") with N_p =
+ * |chunk| nodes in the chunk's order, followed by ghost slots: a pull of PDF i
+ * from a node of another chunk points at slot N_p + k, k counting that
+ * chunk's earlier such pulls of direction i in node order.  The local
+ * lattice's Npad covers the slots, and its RIA table is derived from the local
+ * adjacency list, so lbm_step_osnt, lbm_step_aa (one AA step at a time
+ * between exchanges), lbm_init_equilibrium and lbm_load_canonical (layout
+ * LBM_LAYOUT_AA_EVEN) work on it unchanged.  lbm_canonical_pdfs and
+ * lbm_macroscopic in the OS-NT or AA-odd layout gather through the ghost
+ * slots, so they need the ghosts filled first.  The objective, adjoint and
+ * checkpointed-gradient calls, and lbm_load_canonical in a pulled layout,
+ * return LBM_ERR_UNSUPPORTED on a local lattice. */
+typedef struct lbm_partitioning lbm_partitioning;
+
+#define LBM_HALO_OSNT 0        /* before an OS-NT step: fill slot s of array i from the owner's P_i  */
+#define LBM_HALO_AA_GATHER 1   /* before an AA odd step: fill slot s of array inv(i)                  */
+#define LBM_HALO_AA_SCATTER 2  /* after an AA odd step: return slot s of array inv(i) to the owner     */
+
+/* Partition `lat` into P chunks [N p / P, N (p+1) / P), 1 <= P <= max(N, 1),
+ * and build the local lattices and the exchange table on the host.  The
+ * result does not refer to `lat` afterwards.  LBM_ERR_UNSUPPORTED if a chunk
+ * needs more than 2^27 nodes plus ghost slots or the lattice more than 2^31
+ * ghost PDFs. */
+LBM_API int lbm_partition_build(const lbm_lattice* lat, int P, lbm_partitioning** out);
+
+/* Release a partitioning and its local lattices (NULL is ignored). */
+LBM_API void lbm_free_partitioning(lbm_partitioning* part);
+
+/* Chunk p: its first node in the partitioned lattice, its node count, its
+ * ghost PDFs per exchange (equal to lbm_partition_ghosts) and its ghost slots
+ * per direction array (the largest per-direction count).  Outputs may be NULL. */
+LBM_API int lbm_partition_info(const lbm_partitioning* part, int p, int64_t* first_node, int64_t* N_p,
+                               int64_t* ghost_pdfs, int64_t* ghost_slots);
+
+/* The local lattice of chunk p, owned by `part` (never free it; it lives as
+ * long as `part`).  Upload its tables with lbm_lattice_upload as usual. */
+LBM_API int lbm_partition_local(lbm_partitioning* part, int p, lbm_lattice** local);
+
+/* Chunk p's ghost PDFs (host int32 arrays of ghost_pdfs entries, any may be
+ * NULL), in exchange order: owner chunk, pulled direction i (1..18), local
+ * slot, and the source node as a local index of the owner. */
+LBM_API int lbm_partition_export_ghosts(const lbm_partitioning* part, int p, int32_t* src_part, int32_t* dir,
+                                        int32_t* slot, int32_t* src_node);
+
+/* Check that every local adjacency list, read through the ghost map, equals
+ * `lat`'s rows of its chunk, that the ghost map is in range and one-to-one,
+ * and that each local RIA table decodes to its adjacency list.  LBM_ERR_TABLE
+ * names the first violation. */
+LBM_API int lbm_partition_validate(const lbm_partitioning* part, const lbm_lattice* lat);
+
+/* Bytes of the caller-owned device buffer for the exchange table (8 B per
+ * ghost PDF plus per-CTA and per-chunk words). */
+LBM_API int lbm_halo_table_bytes(const lbm_partitioning* part, size_t* bytes);
+
+/* Copy the exchange table into dev (device, 256-byte aligned, >=
+ * lbm_halo_table_bytes) on `stream`; same ownership rules as
+ * lbm_lattice_upload. */
+LBM_API int lbm_halo_upload(lbm_partitioning* part, void* dev, size_t bytes, void* stream);
+
+/* One exchange of all chunks' ghost PDFs on `stream` (one launch).  grids:
+ * DEVICE array of P pointers, grids[p] = chunk p's grid ([19][Npad_p] of the
+ * precision's element type).  mode: LBM_HALO_*.  A sequence for OS-NT is
+ * exchange(OSNT, src grids), then the P steps src -> dst; for the AA pattern,
+ * the P even steps, exchange(AA_GATHER), the P odd steps,
+ * exchange(AA_SCATTER).  Asynchronous; LBM_ERR_ARG if the table was not
+ * uploaded. */
+LBM_API int lbm_halo_exchange(const lbm_partitioning* part, int prec, void* const* grids, int mode, void* stream);
+
+/* `steps` AA steps of all chunks from parity start_parity: even steps are the
+ * P local even steps; odd steps are exchange(AA_GATHER), the P odd steps and
+ * exchange(AA_SCATTER).  grids_host: host array of the P chunk grids; grids_dev:
+ * device array holding the same P pointers.  s: Brinkman field of the whole
+ * partitioned lattice (device float [N], chunk p uses s + first_node(p)) or
+ * NULL.  ria selects the addressing as for lbm_step_aa.  Asynchronous with
+ * respect to `stream`: the chunks of one step run concurrently on up to 16
+ * side streams that the partitioning creates on its first run (on the device
+ * current then, which all later runs must use) and joins back into `stream`
+ * before the next exchange, so work queued on `stream` before and after the
+ * call is ordered with it as usual. */
+LBM_API int lbm_partition_run_aa(const lbm_partitioning* part, int prec, const lbm_params* params,
+                                 void* const* grids_host, void* const* grids_dev, const float* s, int start_parity,
+                                 int steps, int ria, void* stream);
+
+/* `steps` OS-NT steps of all chunks, ping-ponging two grid sets: grids_host /
+ * grids_dev hold 2P pointers, set 0 (entries 0..P-1) the current source.  Step
+ * k is exchange(OSNT) on set k mod 2, then the P steps from set k mod 2 into
+ * the other set; after an odd count set 1 holds the state.  Streams as for
+ * lbm_partition_run_aa. */
+LBM_API int lbm_partition_run_osnt(const lbm_partitioning* part, int prec, const lbm_params* params,
+                                   void* const* grids_host, void* const* grids_dev, const float* s, int steps,
+                                   int ria, void* stream);
+
 /* Sizes of a lattice.  Any output pointer may be NULL.  run_hist[b], b = 0..32,
  * counts RIA runs of length in [2^b, 2^(b+1)). */
 LBM_API int lbm_lattice_info(const lbm_lattice* lat, int64_t* N, int64_t* Npad, int64_t* R,

@@ -133,17 +133,22 @@ def _rho_bc(mark, p: Params, dtype):
 
 
 def stream(P, adj, p: Params):
-    """Canonical pull: F'[i][n] from P via adj (node indices and markers)."""
+    """Canonical pull: F'[i][n] from P via adj (node indices and markers).
+
+    P may hold more columns than adj has nodes (a chunk's ghost slots, Sect. 6):
+    nodes are the first adj.shape[1] columns, pulls may read any column.
+    """
     adj = as_t(adj, torch.int64)
-    Fn = torch.empty_like(P)
-    Fn[0] = P[0]
+    N = adj.shape[1]
+    Fn = torch.empty((Q, N), dtype=P.dtype)
+    Fn[0] = P[0, :N]
     for i in range(1, Q):
         m = adj[i - 1]
         fluid = m >= 0
         ii = int(_INV[i])
         from_nb = P[i][m.clamp(min=0)]
-        bb = P[ii]
-        abb = -P[ii] + 2 * float(_W[i]) * _rho_bc(m, p, P.dtype)
+        bb = P[ii, :N]
+        abb = -bb + 2 * float(_W[i]) * _rho_bc(m, p, P.dtype)
         Fn[i] = torch.where(fluid, from_nb, torch.where(m == -1, bb, abb))
     return Fn
 
@@ -282,6 +287,28 @@ def objective_flux(F, p: Params, s=None):
     """J = (1/N) sum_n rho_n u_x,n (mean x-momentum flux)."""
     rho, _, u = moments(F, p, s)
     return (rho * u[0]).sum() / F.shape[1]
+
+
+def partitioned_osnt_step(grids, parts, p: Params, s=None):
+    """One OS-NT step of a P-chunk split (Sect. 6): every chunk first receives
+    its ghost PDFs (slot `slot` of array i <- the owner's P_i at `node`), then
+    pulls and collides its own nodes.  grids[k]: chunk k's grid [19, Np + slots]
+    (post-collision state in the node columns); parts from
+    ``tables.partition_local_tables``.  Returns the new chunk grids."""
+    for G, part in zip(grids, parts):
+        for q in np.unique(part["q"]):
+            e = part["q"] == q
+            d = torch.as_tensor(part["dir"][e], dtype=torch.int64)
+            G[d, torch.as_tensor(part["slot"][e], dtype=torch.int64)] = \
+                grids[int(q)][d, torch.as_tensor(part["node"][e], dtype=torch.int64)]
+    out = []
+    for G, part in zip(grids, parts):
+        a, n = part["first"], part["N"]
+        sk = None if s is None else s[a:a + n]
+        Gn = torch.zeros_like(G)
+        Gn[:, :n] = collide(stream(G, part["adj"], p), p, sk)
+        out.append(Gn)
+    return out
 
 
 def run_osnt(G, adj, p: Params, steps: int, s=None):

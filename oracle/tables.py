@@ -273,3 +273,50 @@ def partition_ghosts(adj: np.ndarray, P: int) -> np.ndarray:
         m = adj[:, a:b].astype(np.int64)
         g[p] = int(((m >= 0) & ((m < a) | (m >= b))).sum())
     return g
+
+
+def partition_local_tables(adj: np.ndarray, P: int):
+    """Chunk-local tables of the P-way split (Sect. 6, Sect. 6.1).
+
+    Each process of the paper's distributed run owns chunk p of the node
+    vector and receives, every step, the PDFs its nodes pull from other
+    chunks.  Reading (the paper does not fix a local layout): chunk p's local
+    index space is its own nodes 0 .. Np-1 in order, then ghost slots; a pull
+    of direction i from a node of another chunk gets slot Np + k, where k
+    numbers chunk p's pulls of direction i from other chunks in local node
+    order.  Returns one dict per chunk: ``first``, ``N``, ``adj`` [18, Np]
+    (local indices and markers), ``slots`` (largest per-direction ghost count)
+    and the ghost map ``q`` (owner chunk), ``dir`` (1..18), ``slot``, ``node``
+    (owner-local source node), ordered by owner, direction, slot.
+    """
+    N = adj.shape[1]
+    bounds = partition_bounds(N, P)
+    starts = np.array([a for a, _ in bounds], dtype=np.int64)
+    out = []
+    for a, b in bounds:
+        Np = b - a
+        A = adj[:, a:b].astype(np.int64)
+        local = np.where(A >= 0, A - a, A)
+        foreign = (A >= 0) & ((A < a) | (A >= b))
+        q_l, d_l, s_l, m_l = [], [], [], []
+        slots = 0
+        for i in range(18):
+            cols = np.nonzero(foreign[i])[0]           # local nodes, ascending
+            slot = Np + np.arange(len(cols))
+            local[i, cols] = slot
+            src = A[i, cols]
+            q = np.searchsorted(starts, src, side="right") - 1
+            q_l.append(q)
+            d_l.append(np.full(len(cols), i + 1))
+            s_l.append(slot)
+            m_l.append(src - starts[q])
+            slots = max(slots, len(cols))
+        q = np.concatenate(q_l) if q_l else np.zeros(0, np.int64)
+        order = np.argsort(q, kind="stable")
+        out.append({
+            "first": a, "N": Np, "adj": local.astype(np.int32), "slots": slots,
+            "q": q[order].astype(np.int32), "dir": np.concatenate(d_l)[order].astype(np.int32),
+            "slot": np.concatenate(s_l)[order].astype(np.int32),
+            "node": np.concatenate(m_l)[order].astype(np.int32),
+        })
+    return out

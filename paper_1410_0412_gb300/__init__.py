@@ -17,7 +17,8 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _lib
-from ._lib import (LBM_ENUM_HILBERT, LBM_ENUM_LEX, LBM_F16S, LBM_F32, LBM_F64, LBM_F64_DF, LBM_LAYOUT_AA_EVEN,
+from ._lib import (LBM_ENUM_HILBERT, LBM_ENUM_LEX, LBM_F16S, LBM_F32, LBM_F64, LBM_F64_DF, LBM_HALO_AA_GATHER,
+                   LBM_HALO_AA_SCATTER, LBM_HALO_OSNT, LBM_LAYOUT_AA_EVEN,
                    LBM_LAYOUT_AA_ODD, LBM_LAYOUT_OSNT, LBM_TABLES_ADJ, LBM_TABLES_RIA, LbmError, check)
 
 _lib.load()
@@ -103,9 +104,11 @@ def _check_s(lat, s):
 class Lattice:
     """A sparse lattice (``lbm_build_lattice``): enumeration, adjacency and RIA tables."""
 
-    def __init__(self, solid=None, periodic=(0, 0, 0), x_pressure=False, enum="lex", B=1, _handle=None):
+    def __init__(self, solid=None, periodic=(0, 0, 0), x_pressure=False, enum="lex", B=1, _handle=None,
+                 _owner=None):
         self._h = ctypes.c_void_p()
         self._dev = None
+        self._owner = _owner  # a Partitioning that owns this handle (never freed here)
         self.uploaded = 0
         if _handle is not None:
             self._h = _handle
@@ -236,8 +239,107 @@ class Lattice:
         return b.value
 
     def close(self):
-        if self._h:
+        if self._h and self._owner is None:
             _lib.load().lbm_free_lattice(self._h)
+        self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Partitioning:
+    """P chunks of a lattice's node vector, each a local lattice with ghost slots (``lbm_partition_build``).
+
+    Chunk p holds nodes [N p / P, N (p+1) / P) of ``lat`` (Sect. 6.1); ``parts[p]``
+    is its local lattice, usable with the step functions, and the exchange
+    table moves the ghost PDFs between the chunks' grids each step (Sect. 6).
+    """
+
+    def __init__(self, lat: Lattice, P: int):
+        self._h = ctypes.c_void_p()
+        lib = _lib.load()
+        check(lib.lbm_partition_build(lat.handle, int(P), ctypes.byref(self._h)), "lbm_partition_build")
+        self.P = int(P)
+        self.N = lat.N
+        self.first, self.sizes, self.ghost_pdfs, self.ghost_slots, self.parts = [], [], [], [], []
+        for p in range(self.P):
+            f, n, g, gs = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+            check(lib.lbm_partition_info(self._h, p, ctypes.byref(f), ctypes.byref(n), ctypes.byref(g),
+                                         ctypes.byref(gs)), "lbm_partition_info")
+            self.first.append(f.value)
+            self.sizes.append(n.value)
+            self.ghost_pdfs.append(g.value)
+            self.ghost_slots.append(gs.value)
+            h = ctypes.c_void_p()
+            check(lib.lbm_partition_local(self._h, p, ctypes.byref(h)), "lbm_partition_local")
+            self.parts.append(Lattice(_handle=h, _owner=self))
+        self._dev = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def ghosts(self, p):
+        """Chunk p's ghost PDFs in exchange order: owner chunk, direction 1..18, local slot, owner-local node."""
+        n = self.ghost_pdfs[p]
+        out = {k: np.empty(n, np.int32) for k in ("src_part", "dir", "slot", "src_node")}
+        q = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        check(_lib.load().lbm_partition_export_ghosts(self._h, int(p), q(out["src_part"]), q(out["dir"]),
+                                                      q(out["slot"]), q(out["src_node"])),
+              "lbm_partition_export_ghosts")
+        return out
+
+    def validate(self, lat: Lattice):
+        check(_lib.load().lbm_partition_validate(self._h, lat.handle), "lbm_partition_validate")
+
+    def upload(self, which=LBM_TABLES_ADJ | LBM_TABLES_RIA, device="cuda", stream=None):
+        """Upload every local lattice's tables and the exchange table (torch-owned buffers)."""
+        torch = _torch()
+        for lat in self.parts:
+            lat.upload(which, device, stream)
+        nbytes = ctypes.c_size_t()
+        check(_lib.load().lbm_halo_table_bytes(self._h, ctypes.byref(nbytes)), "lbm_halo_table_bytes")
+        buf = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=device)
+        check(_lib.load().lbm_halo_upload(self._h, _ptr(buf), nbytes.value, _stream(stream)), "lbm_halo_upload")
+        torch.cuda.synchronize(buf.device)
+        self._dev = buf
+        return self
+
+    def new_grids(self, prec, device="cuda"):
+        """One zeroed grid [19, Npad_p] per chunk."""
+        return [lat.new_grid(prec, device) for lat in self.parts]
+
+    @staticmethod
+    def pointers(grids, device=None):
+        """The device array of grid addresses that ``lbm_halo_exchange`` takes."""
+        torch = _torch()
+        dev = device or grids[0].device
+        return torch.tensor([g.data_ptr() for g in grids], dtype=torch.int64, device=dev)
+
+    def scatter(self, grid, grids):
+        """Copy a whole-lattice grid [19, >= N] into the chunks' node slots."""
+        for p, g in enumerate(grids):
+            a, n = self.first[p], self.sizes[p]
+            g[:, :n].copy_(grid[:, a:a + n])
+
+    def gather(self, grids, out=None):
+        """The chunks' node slots as one whole-lattice grid [19, N]."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty((19, self.N), dtype=grids[0].dtype, device=grids[0].device)
+        for p, g in enumerate(grids):
+            a, n = self.first[p], self.sizes[p]
+            out[:, a:a + n].copy_(g[:, :n])
+        return out
+
+    def close(self):
+        for lat in self.parts:
+            lat.close()
+        if self._h:
+            _lib.load().lbm_free_partitioning(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):
@@ -333,6 +435,48 @@ def lbm_macroscopic_noalloc(lat, prec, params, pdf, layout, s=None, rho=None, u=
     check(_lib.load().lbm_macroscopic_noalloc(lat.handle, prec, ctypes.byref(params.c()), _ptr(pdf), layout,
                                               _ptr(_check_s(lat, s)), _ptr(rho), _ptr(u), _ptr(sums),
                                               _stream(stream)), "lbm_macroscopic_noalloc")
+
+
+def lbm_halo_exchange(part, prec, pointers, mode, stream=None):
+    """One ghost exchange of all chunks; ``pointers`` from ``Partitioning.pointers``."""
+    torch = _torch()
+    if not pointers.is_cuda or pointers.dtype != torch.int64 or pointers.numel() != part.P:
+        raise TypeError("pointers must be a CUDA int64 tensor with one address per chunk")
+    check(_lib.load().lbm_halo_exchange(part.handle, _prec(prec), _ptr(pointers), int(mode), _stream(stream)),
+          "lbm_halo_exchange")
+
+
+def _host_ptrs(grids):
+    arr = (ctypes.c_void_p * len(grids))(*[g.data_ptr() for g in grids])
+    return arr
+
+
+def lbm_partition_run_aa(part, prec, params, grids, pointers, start_parity, steps, s=None, ria=False, stream=None):
+    prec = _prec(prec)
+    for lat, g in zip(part.parts, grids):
+        _check_grid(lat, prec, g, "grid")
+    if s is not None:
+        _check_s(_Sized(part.N), s)
+    check(_lib.load().lbm_partition_run_aa(part.handle, prec, ctypes.byref(params.c()), _host_ptrs(grids),
+                                           _ptr(pointers), _ptr(s), int(start_parity), int(steps), 1 if ria else 0,
+                                           _stream(stream)), "lbm_partition_run_aa")
+
+
+def lbm_partition_run_osnt(part, prec, params, grids, pointers, steps, s=None, ria=False, stream=None):
+    """grids: 2P grids (set 0 then set 1); pointers: their 2P addresses on the device."""
+    prec = _prec(prec)
+    for k, g in enumerate(grids):
+        _check_grid(part.parts[k % part.P], prec, g, "grid")
+    if s is not None:
+        _check_s(_Sized(part.N), s)
+    check(_lib.load().lbm_partition_run_osnt(part.handle, prec, ctypes.byref(params.c()), _host_ptrs(grids),
+                                             _ptr(pointers), _ptr(s), int(steps), 1 if ria else 0, _stream(stream)),
+          "lbm_partition_run_osnt")
+
+
+class _Sized:
+    def __init__(self, N):
+        self.N = N
 
 
 def lbm_check_finite(values, stream=None):
@@ -561,3 +705,69 @@ __all__ = [
     "lbm_objective_flux", "lbm_adjoint_step", "lbm_ckpt_workspace_bytes", "lbm_flux_forward", "lbm_flux_backward",
     "flux_objective", "new_adjoint", "lbm_macroscopic_noalloc", "lbm_check_finite", "lbm_bandwidth_kernel",
 ]
+
+
+class PartitionedSolver:
+    """The step on the P chunks of a ``Partitioning``, with a ghost exchange per step (Sect. 6).
+
+    Holds one grid per chunk (two for OS-NT) and their device address tables;
+    ``step`` runs ``lbm_partition_run_aa`` / ``lbm_partition_run_osnt``.  The
+    state moves between this and a whole-lattice ``Solver`` grid with
+    ``load_global`` / ``to_global`` (node slots only; ghost slots are refilled
+    by the next exchange).
+    """
+
+    def __init__(self, part: Partitioning, prec="f64", params: Params | None = None, form="aa", ria=True, s=None,
+                 device="cuda"):
+        self.part = part
+        self.prec = _prec(prec)
+        self.params = params or Params()
+        self.form = form
+        self.ria = bool(ria)
+        self.s = s
+        self.t = 0
+        if form == "osnt":
+            self.sets = [part.new_grids(self.prec, device), part.new_grids(self.prec, device)]
+        elif form == "aa":
+            self.sets = [part.new_grids(self.prec, device)]
+        else:
+            raise ValueError(form)
+        self._refresh()
+
+    def _refresh(self):
+        flat = [g for grids in self.sets for g in grids]
+        self._ptrs = Partitioning.pointers(flat)
+
+    @property
+    def grids(self):
+        """The chunk grids holding the current state."""
+        return self.sets[0]
+
+    def init_equilibrium(self, rho0=1.0, u0=(0.0, 0.0, 0.0), stream=None):
+        self.t = 0
+        layout = LBM_LAYOUT_OSNT if self.form == "osnt" else LBM_LAYOUT_AA_EVEN
+        for lat, g in zip(self.part.parts, self.sets[0]):
+            lbm_init_equilibrium(lat, self.prec, self.params, g, layout, rho0, u0, stream)
+
+    def load_global(self, grid, t=0):
+        """Take the state of a whole-lattice grid (same form and layout) after t steps."""
+        if self.form == "aa" and t % 2:
+            raise ValueError("load an AA state after an even step count")
+        self.t = t
+        self.part.scatter(grid, self.sets[0])
+
+    def to_global(self, out=None):
+        return self.part.gather(self.sets[0], out)
+
+    def step(self, n=1, stream=None):
+        P = self.part.P
+        if self.form == "osnt":
+            lbm_partition_run_osnt(self.part, self.prec, self.params, self.sets[0] + self.sets[1], self._ptrs, n,
+                                   self.s, self.ria, stream)
+            if n % 2:
+                self.sets.reverse()
+                self._refresh()
+        else:
+            lbm_partition_run_aa(self.part, self.prec, self.params, self.sets[0], self._ptrs[:P], self.t % 2, n,
+                                 self.s, self.ria, stream)
+        self.t += n

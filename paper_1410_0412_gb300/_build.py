@@ -21,7 +21,7 @@ LIB = os.path.join(PKG, "liblbm.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden", "-I" + os.path.join(ROOT, "include")]
-SOURCES = ["api.cpp", "lattice.cpp", "kernels_f64.cu", "kernels_f64df.cu", "kernels_f32.cu", "kernels_f16s.cu", "adjoint.cu", "noalloc.cu", "bandwidth.cu"]
+SOURCES = ["api.cpp", "lattice.cpp", "kernels_f64.cu", "kernels_f64df.cu", "kernels_f32.cu", "kernels_f16s.cu", "adjoint.cu", "noalloc.cu", "bandwidth.cu", "partition.cpp", "halo.cu"]
 
 
 def nvcc() -> str:

@@ -30,6 +30,9 @@ LBM_LAYOUT_AA_EVEN = 1
 LBM_LAYOUT_AA_ODD = 2
 LBM_TABLES_ADJ = 1
 LBM_TABLES_RIA = 2
+LBM_HALO_OSNT = 0
+LBM_HALO_AA_GATHER = 1
+LBM_HALO_AA_SCATTER = 2
 
 _ERRNAMES = {1: "LBM_ERR_ARG", 2: "LBM_ERR_ALLOC", 3: "LBM_ERR_CUDA", 4: "LBM_ERR_TABLE",
              5: "LBM_ERR_UNSUPPORTED", 6: "LBM_ERR_NONFINITE"}
@@ -68,6 +71,17 @@ SIGNATURES = {
     "lbm_renumber_partitions": [_P, _I, _P],
     "lbm_partition_ghosts": [_P, _I, _P],
     "lbm_free_lattice": [_P],
+    "lbm_partition_build": [_P, _I, ctypes.POINTER(_P)],
+    "lbm_free_partitioning": [_P],
+    "lbm_partition_info": [_P, _I, _PI64, _PI64, _PI64, _PI64],
+    "lbm_partition_local": [_P, _I, ctypes.POINTER(_P)],
+    "lbm_partition_export_ghosts": [_P, _I, _P, _P, _P, _P],
+    "lbm_partition_validate": [_P, _P],
+    "lbm_halo_table_bytes": [_P, _PSZ],
+    "lbm_halo_upload": [_P, _P, _SZ, _P],
+    "lbm_halo_exchange": [_P, _I, _P, _I, _P],
+    "lbm_partition_run_aa": [_P, _I, ctypes.POINTER(lbm_params), _P, _P, _P, _I, _I, _I, _P],
+    "lbm_partition_run_osnt": [_P, _I, ctypes.POINTER(lbm_params), _P, _P, _P, _I, _I, _P],
     "lbm_lattice_info": [_P, _PI64, _PI64, _PI64, _PI64],
     "lbm_export_tables": [_P, _P, _P, _P, _P],
     "lbm_validate_tables": [_P],
@@ -92,7 +106,7 @@ SIGNATURES = {
     "lbm_flux_forward": [_P, _I, ctypes.POINTER(lbm_params), _P, _P, _I, _I, _I, _P, _SZ, _P, _P],
     "lbm_flux_backward": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _I, _I, _P, _SZ, _P, _P, _P],
 }
-_RESTYPES = {"lbm_last_error": ctypes.c_char_p, "lbm_free_lattice": None}
+_RESTYPES = {"lbm_last_error": ctypes.c_char_p, "lbm_free_lattice": None, "lbm_free_partitioning": None}
 
 _lib = None
 

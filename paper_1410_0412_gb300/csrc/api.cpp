@@ -107,6 +107,14 @@ int any_tables(const lbm_lattice* L, int* ria) {
   return set_error(LBM_ERR_ARG, "no device tables uploaded");
 }
 
+// Whole-lattice operations that a partition's local lattice cannot do alone
+// (its ghost slots are not nodes).
+int check_whole(const lbm_lattice* L, const char* what) {
+  if (L->partition_local)
+    return set_error(LBM_ERR_UNSUPPORTED, std::string(what) + " needs a whole lattice, not a partition's local lattice");
+  return LBM_OK;
+}
+
 int check_layout(int layout) {
   if (layout < LBM_LAYOUT_OSNT || layout > LBM_LAYOUT_AA_ODD) return set_error(LBM_ERR_ARG, "unknown layout");
   return LBM_OK;
@@ -364,6 +372,8 @@ int lbm_load_canonical(const lbm_lattice* L, int prec, const lbm_params* params,
   KParams kp;
   if (int rc = make_kparams(params, prec, &kp)) return rc;
   if (int rc = check_layout(layout)) return rc;
+  if (layout != LBM_LAYOUT_AA_EVEN)
+    if (int rc = check_whole(L, "loading a pulled layout")) return rc;
   if (!pdf || (!F && L->N > 0)) return set_error(LBM_ERR_ARG, "pdf or F is NULL");
   if (layout != LBM_LAYOUT_AA_EVEN && L->N > 0) {
     int ria;
@@ -460,6 +470,7 @@ int lbm_objective_flux(const lbm_lattice* L, int prec, const lbm_params* params,
                        const float* s, double* J, void* lambda_T, double* grad_s, void* workspace, size_t ws_bytes,
                        void* stream) {
   if (int rc = check_lat(L)) return rc;
+  if (int rc = check_whole(L, "the objective")) return rc;
   KParams kp;
   if (int rc = make_kparams(params, prec, &kp)) return rc;
   if (int rc = check_layout(layout)) return rc;
@@ -479,6 +490,7 @@ int lbm_adjoint_step(const lbm_lattice* L, int prec, const lbm_params* params, c
                      const void* lambda_next, void* lambda_n, const float* s, double* grad_s, int ria,
                      void* stream) {
   if (int rc = check_lat(L)) return rc;
+  if (int rc = check_whole(L, "the adjoint step")) return rc;
   KParams kp;
   if (int rc = make_kparams(params, prec, &kp)) return rc;
   if (!G_n || !lambda_next || !lambda_n) return set_error(LBM_ERR_ARG, "G_n, lambda_next or lambda_n is NULL");
@@ -541,6 +553,7 @@ extern "C" {
 
 int lbm_ckpt_workspace_bytes(const lbm_lattice* L, int prec, int T, int K, size_t* bytes) {
   if (int rc = check_lat(L)) return rc;
+  if (int rc = check_whole(L, "the checkpointed gradient")) return rc;
   if (!bytes) return set_error(LBM_ERR_ARG, "bytes is NULL");
   if (T < 0 || K < 1) return set_error(LBM_ERR_ARG, "T must be >= 0 and K >= 1");
   if (prec < LBM_F64 || prec > LBM_F64_DF) return set_error(LBM_ERR_ARG, "unknown precision");
@@ -551,6 +564,7 @@ int lbm_ckpt_workspace_bytes(const lbm_lattice* L, int prec, int T, int K, size_
 int lbm_flux_forward(const lbm_lattice* L, int prec, const lbm_params* params, const void* G0, const float* s,
                      int T, int K, int ria, void* ws, size_t ws_bytes, double* J, void* stream) {
   if (int rc = check_lat(L)) return rc;
+  if (int rc = check_whole(L, "the checkpointed gradient")) return rc;
   KParams kp;
   if (int rc = make_kparams(params, prec, &kp)) return rc;
   CkptLayout c;
@@ -585,6 +599,7 @@ int lbm_flux_forward(const lbm_lattice* L, int prec, const lbm_params* params, c
 int lbm_flux_backward(const lbm_lattice* L, int prec, const lbm_params* params, const float* s, int T, int K,
                       int ria, void* ws, size_t ws_bytes, double* grad_s, void* lambda_0, void* stream) {
   if (int rc = check_lat(L)) return rc;
+  if (int rc = check_whole(L, "the checkpointed gradient")) return rc;
   KParams kp;
   if (int rc = make_kparams(params, prec, &kp)) return rc;
   CkptLayout c;

@@ -40,6 +40,30 @@ struct DevTables {
   int pressure = 0;                     // the lattice has inlet/outlet markers
 };
 
+// Ghost slots of a partition: local node index space [0, N_p) followed by the
+// slots; slot numbers and direction share one 32-bit word on the device.
+constexpr int kSlotBits = 27;
+constexpr int kHaloBlock = 256;
+
+// One ghost PDF of a partition: the pull of direction dir + 1 that lands in
+// local slot `slot` comes from node `node` (local index) of partition q.
+struct GhostEntry {
+  int32_t q, dir, slot, node;
+};
+
+// Device addresses of the uploaded exchange table (one caller buffer).
+struct HaloDev {
+  const uint32_t* e_dirslot = nullptr;  // [E]  dir << kSlotBits | slot
+  const int32_t* e_node = nullptr;      // [E]  source node, local to the owner
+  const int32_t* grp_p = nullptr;       // [G]  receiving partition of each (receiver, owner) group
+  const int32_t* grp_q = nullptr;       // [G]  owning partition
+  const int32_t* grp_end = nullptr;     // [G]  one past the group's last entry
+  const int32_t* blk_group = nullptr;   // [B]  group of each CTA
+  const int32_t* blk_first = nullptr;   // [B]  first entry of each CTA
+  const int64_t* npad = nullptr;        // [P]  grid stride of each partition
+  int64_t E = 0, G = 0, B = 0;
+};
+
 }  // namespace lbm
 
 struct lbm_lattice {
@@ -56,7 +80,32 @@ struct lbm_lattice {
   std::vector<int32_t> warp_head0; // [nwarps]  first node of that run
   int64_t hist[33] = {0};
   int uploaded = 0;                // LBM_TABLES_* bits present on the device
+  int partition_local = 0;         // a partition's local lattice: entries >= N are ghost slots
   lbm::DevTables dev;
+};
+
+struct lbm_partitioning {
+  int P = 0;
+  int64_t N = 0;                                 // nodes of the partitioned lattice
+  std::vector<int64_t> first;                    // [P+1] chunk bounds N p / P
+  std::vector<lbm_lattice*> part;                // [P] local lattices (owned)
+  std::vector<std::vector<lbm::GhostEntry>> ghost;  // [P] ghost entries, by owner, direction, slot
+  std::vector<int64_t> ghost_slots;              // [P] slots behind the local nodes (max over directions)
+  // host copy of the exchange table (the source of lbm_halo_upload)
+  std::vector<uint32_t> h_dirslot;
+  std::vector<int32_t> h_node, h_grp_p, h_grp_q, h_grp_end, h_blk_group, h_blk_first;
+  std::vector<int64_t> h_npad;
+  int uploaded = 0;
+  lbm::HaloDev dev;
+  // Library-owned side streams on which the chunks' steps run concurrently
+  // (fork / join through events on the caller's stream); created on the
+  // first partitioned run, on the device current at that time.
+  std::vector<void*> side_streams, side_done;
+  void* fork_event = nullptr;
+  lbm_partitioning() = default;
+  lbm_partitioning(const lbm_partitioning&) = delete;
+  lbm_partitioning& operator=(const lbm_partitioning&) = delete;
+  ~lbm_partitioning();
 };
 
 namespace lbm {
@@ -69,8 +118,12 @@ int build_tables(lbm_lattice* L, const uint8_t* solid);
 int build_tables_from_order(lbm_lattice* L, const uint8_t* solid, const int32_t* node_xyz, int64_t N);
 int renumber_partitions(const lbm_lattice* L, int P, int32_t* out);
 int partition_ghosts(const lbm_lattice* L, int P, int64_t* ghosts);
+int build_partitioning(const lbm_lattice* G, int P, lbm_partitioning* out);   // partition.cpp
+int validate_partitioning(const lbm_partitioning* S, const lbm_lattice* G);
+int launch_halo(const lbm_partitioning* S, int prec, void* const* grids, int mode, void* stream);  // halo.cu
 int derive_ria(lbm_lattice* L);
 int validate(const lbm_lattice* L);
+int validate_runs(const lbm_lattice* L);  // the RIA tables alone (any index range)
 
 // Kernel-side parameter block, computed on the host from lbm_params.
 struct KParams {

@@ -443,10 +443,17 @@ __global__ void __launch_bounds__(kBlock) k_aa_even_h2(DevTables t, KParams kp, 
   const float s1 = DRAG ? (n + 1 < N ? __ldg(s + n + 1) : 0.0f) : 0.0f;
   collide<float, FORCE, DRAG>(d0, c, s0);
   collide<float, FORCE, DRAG>(d1, c, s1);
+  // the pair's second node may lie past N (odd N): write node slots only, as
+  // the slot after the last node can be a partition's ghost slot
+  if (n + 1 < N) {
 #pragma unroll
-  for (int i = 0; i < kQ; ++i)
-    *reinterpret_cast<__half2*>(A + at(inv(i), t.npad, n)) =
-        __floats2half2_rn(d0[i] * kp.scale, d1[i] * kp.scale);
+    for (int i = 0; i < kQ; ++i)
+      *reinterpret_cast<__half2*>(A + at(inv(i), t.npad, n)) =
+          __floats2half2_rn(d0[i] * kp.scale, d1[i] * kp.scale);
+  } else {
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) A[at(inv(i), t.npad, n)] = __float2half_rn(d0[i] * kp.scale);
+  }
 }
 
 // AA odd step: read f_i from the neighbour's opposite slot A[inv i][m_i], collide,

@@ -413,7 +413,16 @@ int build_tables(lbm_lattice* L, const uint8_t* solid) {
 }
 
 int validate(const lbm_lattice* L) {
-  const int64_t N = L->N, Np = L->Npad, R = L->R;
+  const int64_t N = L->N, Np = L->Npad;
+  if (L->partition_local) {
+    // a partition's local lattice: entries may point at ghost slots in
+    // [N, Npad), so only ranges and the run table are checked here (the ghost
+    // map itself is checked against the whole lattice by partition validation)
+    for (int64_t k = 0; k < 18 * Np; ++k)
+      if (L->adj[k] < LBM_MARK_OUTLET || L->adj[k] >= Np)
+        return set_error(LBM_ERR_TABLE, "adjacency entry out of range at node " + std::to_string(k % Np));
+    return validate_runs(L);
+  }
   const int32_t* adj = L->adj.data();
   std::atomic<int64_t> bad{-1};
   std::atomic<int> kind{0};
@@ -444,6 +453,18 @@ int validate(const lbm_lattice* L) {
     return set_error(LBM_ERR_TABLE, std::string(kind == 1 ? "adjacency entry out of range"
                                                           : "adjacency not reciprocal") +
                                         " at node " + std::to_string(int64_t(bad)));
+  return validate_runs(L);
+}
+
+int validate_runs(const lbm_lattice* L) {
+  const int64_t N = L->N, Np = L->Npad, R = L->R;
+  const int32_t* adj = L->adj.data();
+  std::atomic<int64_t> bad{-1};
+  std::atomic<int> kind{0};
+  auto flag = [&](int64_t n, int k) {
+    int64_t cur = -1;
+    if (bad.compare_exchange_strong(cur, n)) kind = k;
+  };
   if (int64_t(L->run_start.size()) != R + 1 || L->run_start[0] != 0 || L->run_start[R] != N)
     return set_error(LBM_ERR_TABLE, "run table does not cover [0, N)");
   for (int64_t r = 0; r < R; ++r)
