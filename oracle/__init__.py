@@ -18,6 +18,8 @@ lattices"):
   anti-bounce-back, and the two storage forms OS-NT (two grids) and the AA
   pattern (one grid, even/odd steps) of Sect. 4; macroscopic moments and the
   mean-flux objective.
+* ``esotwist`` - the Esoteric Twist single-grid form that Sect. 1 and Sect. 4
+  name without evaluating (its slot rules are a reading, stated there).
 * ``dense``   - the same LBM on the full voxel array with push streaming; it
   never builds an adjacency list, so it checks tables and streaming.
 * ``adjoint`` - the reverse sweep of T steps taped by torch autograd over
