@@ -73,6 +73,8 @@ def loop_balance(variant: str, p: int, r: float) -> float:
         return dpdf + 72
     if variant == "aa_odd_r":
         return dpdf + 76 * r
+    if variant == "et":
+        return dpdf + 28            # six int32 locations + one uint32 link mask, every step
     raise ValueError(variant)
 
 
@@ -204,7 +206,8 @@ def _time_variant(lbm, torch, lat, prec, params, form, ria, pairs, warm=2, s=Non
 def suite_channel(args, lbm, torch):
     """The paper's channel (Sect. 5.1): 100 x 100 x 500, long axis z, 1-voxel walls, periodic z."""
     solid = geometry.square_channel(100, 100, 500)
-    lat = lbm.Lattice(solid, periodic=(0, 0, 1), enum="lex", B=1).upload()
+    lat = lbm.Lattice(solid, periodic=(0, 0, 1), enum="lex", B=1).upload(
+        lbm.LBM_TABLES_ADJ | lbm.LBM_TABLES_RIA | lbm.LBM_TABLES_ET)
     r = lat.R / lat.N
     hbm, kind = peaks()
     out = {"suite": "channel", "fluid_nodes": lat.N, "runs": lat.R, "r": r, "r_times_98": r * 98,
@@ -213,7 +216,7 @@ def suite_channel(args, lbm, torch):
     for prec, pb in (("f64", 8), ("f64df", 8), ("f32", 4), ("f16s", 2)):
         params = lbm.Params(omega_plus=w["omega_plus"], magic=w["magic"], g=(0.0, 0.0, 1e-6),
                             shifted=prec in ("f32", "f16s"))
-        for form, ria in (("osnt", False), ("osnt", True), ("aa", False), ("aa", True)):
+        for form, ria in (("osnt", False), ("osnt", True), ("aa", False), ("aa", True), ("et", False)):
             name = f"{form}{'_r' if ria else ''}"
             sv, g = _time_variant(lbm, torch, lat, prec, params, form, ria, args.steps)
             bl = loop_balance(name, pb, r)
@@ -639,7 +642,7 @@ def main():
     t0 = time.time()
     solid = make_geometry(args.box)
     lat = lbm.Lattice(solid, periodic=w["periodic"], enum="lex", B=1)
-    lat.upload(lbm.LBM_TABLES_ADJ | lbm.LBM_TABLES_RIA, device=dev)
+    lat.upload(lbm.LBM_TABLES_ADJ | lbm.LBM_TABLES_RIA | lbm.LBM_TABLES_ET, device=dev)
     setup_s = time.time() - t0
     N, R = lat.N, lat.R
     r = R / N
@@ -771,7 +774,7 @@ def main():
         for prec, pb in (("f64", 8), ("f64df", 8), ("f32", 4), ("f16s", 2)):
             vp = lbm.Params(omega_plus=w["omega_plus"], magic=w["magic"], g=w["g"],
                             shifted=(prec in ("f32", "f16s")))
-            for form, ria in (("osnt", False), ("osnt", True), ("aa", False), ("aa", True)):
+            for form, ria in (("osnt", False), ("osnt", True), ("aa", False), ("aa", True), ("et", False)):
                 name = f"{form}{'_r' if ria else ''}"
                 sv = lbm.Solver(lat, prec, vp, form=form, ria=ria)
                 sv.init_equilibrium(1.0)

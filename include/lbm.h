@@ -36,7 +36,10 @@
  *  - Grid layouts: LBM_LAYOUT_OSNT = an OS-NT grid (holds post-collision
  *    PDFs; the canonical state is one pull gather away); LBM_LAYOUT_AA_EVEN =
  *    the AA grid after an even number of steps (holds the canonical state);
- *    LBM_LAYOUT_AA_ODD = the AA grid after an odd number of steps.
+ *    LBM_LAYOUT_AA_ODD = the AA grid after an odd number of steps;
+ *    LBM_LAYOUT_ET_EVEN / LBM_LAYOUT_ET_ODD = the Esoteric Twist grid after
+ *    an even / odd number of steps.  Esoteric Twist grids have the stride
+ *    Spad of lbm_et_info instead of Npad: they also hold phantom locations.
  */
 #ifndef LBM_H
 #define LBM_H
@@ -79,9 +82,12 @@ extern "C" {
 #define LBM_LAYOUT_OSNT 0
 #define LBM_LAYOUT_AA_EVEN 1
 #define LBM_LAYOUT_AA_ODD 2
+#define LBM_LAYOUT_ET_EVEN 3 /* Esoteric Twist grid after an even number of steps */
+#define LBM_LAYOUT_ET_ODD 4  /* Esoteric Twist grid after an odd number of steps  */
 
 #define LBM_TABLES_ADJ 1     /* full adjacency list, 18 x int32 per node (Sect. 4)   */
 #define LBM_TABLES_RIA 2     /* RIA run table (Sect. 4.1)                            */
+#define LBM_TABLES_ET 4      /* Esoteric Twist locations and link mask, 28 B per node */
 
 #define LBM_MARK_WALL (-1)   /* adjacency marker: halfway bounce-back               */
 #define LBM_MARK_INLET (-2)  /* adjacency marker: pressure inlet face x = -1         */
@@ -357,6 +363,46 @@ LBM_API int lbm_step_aa(const lbm_lattice* lat, int prec, const lbm_params* para
 /* `steps` consecutive AA steps starting with parity start_parity. */
 LBM_API int lbm_run_aa(const lbm_lattice* lat, int prec, const lbm_params* params, void* pdf,
                int start_parity, int steps, const float* s, int ria, void* stream);
+
+/* ---- Esoteric Twist: the third single-grid form (named in Sect. 1 and Sect. 4) ----
+ * The paper lists Geier's Esoteric Twist with OS-NT and the AA pattern as the
+ * lowest-loop-balance propagation schemes but does not evaluate it.  Layout
+ * used here: the link between node n and n + c_i keeps its two slots at
+ * location n + max(c_i, 0), so every step touches the node itself and the six
+ * locations +x, +y, +z, +x+y, +x+z, +y+z.  Even step: node n reads f_i from
+ * slot i at n + max(-c_i, 0) and writes P_j to slot inv(j) at n + max(c_j, 0);
+ * odd step: slots inv(i) and j.  A link to a wall or a pressure face writes the
+ * bounced value (P_j, or 2 w rho_bc - P_j) into the pair's other slot, which
+ * the node reads next.  Locations that are not fluid nodes but hold slots get
+ * "phantom" storage indices N .. S-1, ordered lexicographically (x fastest) by
+ * their coordinates (wrapped on periodic axes; up to X, Y, Z on the far faces).
+ * Tables: 6 int32 locations and one uint32 link mask per node, so
+ * B_l = 38p + 28 B/FLUP on every step.  Grid: [19][Spad] of the precision's
+ * element type. */
+
+/* Esoteric Twist sizes, deriving its tables on first use: S = N + phantom
+ * locations, Spad = the grid stride (S rounded up to 128), and optionally the
+ * phantoms' coordinates (host int32 [S-N][3], x y z).  LBM_ERR_UNSUPPORTED for
+ * a partition's local lattice, or a lattice without node coordinates that
+ * needs phantoms. */
+LBM_API int lbm_et_info(lbm_lattice* lat, int64_t* S, int64_t* Spad, int32_t* phantom_xyz);
+
+/* The Esoteric Twist tables on the host (bit-exact comparison): nb (int32
+ * [6][N]) the storage index of n + (+x, +y, +z, +x+y, +x+z, +y+z); mask (uint32
+ * [N]) bit i-1 set when the pull of direction i at n meets a marker, bit
+ * 18 + r when that marker is a pressure face, r the rank of i among the ten
+ * directions with c_ix != 0 (1, 2, 7, ..., 14).  Either may be NULL. */
+LBM_API int lbm_export_et_tables(lbm_lattice* lat, int32_t* nb, uint32_t* mask);
+
+/* One Esoteric Twist step of the grid `pdf` ([19][Spad], layout ET_EVEN before
+ * a parity-0 step, ET_ODD before a parity-1 one), in place.  Needs the
+ * LBM_TABLES_ET tables uploaded.  s: Brinkman field or NULL. */
+LBM_API int lbm_step_et(const lbm_lattice* lat, int prec, const lbm_params* params, void* pdf, int parity,
+                        const float* s, void* stream);
+
+/* `steps` consecutive Esoteric Twist steps starting with parity start_parity. */
+LBM_API int lbm_run_et(const lbm_lattice* lat, int prec, const lbm_params* params, void* pdf, int start_parity,
+                       int steps, const float* s, void* stream);
 
 /* ---- macroscopic quantities and reductions ------------------------------------- */
 

@@ -18,7 +18,8 @@ import numpy as np
 
 from . import _lib
 from ._lib import (LBM_ENUM_HILBERT, LBM_ENUM_LEX, LBM_F16S, LBM_F32, LBM_F64, LBM_F64_DF, LBM_HALO_AA_GATHER,
-                   LBM_HALO_AA_SCATTER, LBM_HALO_OSNT, LBM_LAYOUT_AA_EVEN,
+                   LBM_HALO_AA_SCATTER, LBM_HALO_OSNT, LBM_LAYOUT_AA_EVEN, LBM_LAYOUT_ET_EVEN, LBM_LAYOUT_ET_ODD,
+                   LBM_TABLES_ET,
                    LBM_LAYOUT_AA_ODD, LBM_LAYOUT_OSNT, LBM_TABLES_ADJ, LBM_TABLES_RIA, LbmError, check)
 
 _lib.load()
@@ -82,14 +83,16 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
-def _check_grid(lat, prec, t, name):
+def _check_grid(lat, prec, t, name, layout=None):
     torch = _torch()
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
     if t.dtype != _dtype(prec):
         raise TypeError(f"{name} has dtype {t.dtype}, precision needs {_dtype(prec)}")
-    if not t.is_contiguous() or t.numel() < 19 * lat.Npad:
-        raise ValueError(f"{name} must be contiguous with at least 19 * Npad elements")
+    et = layout is not None and layout >= LBM_LAYOUT_ET_EVEN
+    stride = lat.et_info()[1] if et else lat.Npad
+    if not t.is_contiguous() or t.numel() < 19 * stride:
+        raise ValueError(f"{name} must be contiguous with at least 19 * {'Spad' if et else 'Npad'} elements")
 
 
 def _check_s(lat, s):
@@ -229,9 +232,28 @@ class Lattice:
         check(_lib.load().lbm_pdf_bytes(self._h, _prec(prec), ctypes.byref(b)), "lbm_pdf_bytes")
         return b.value
 
-    def new_grid(self, prec, device="cuda"):
+    def new_grid(self, prec, device="cuda", et=False):
+        """A zeroed grid [19, Npad] (or [19, Spad] for the Esoteric Twist form)."""
         torch = _torch()
-        return torch.zeros((19, self.Npad), dtype=_dtype(_prec(prec)), device=device)
+        return torch.zeros((19, self.et_info()[1] if et else self.Npad), dtype=_dtype(_prec(prec)), device=device)
+
+    def et_info(self):
+        """(S, Spad, phantom_xyz [S-N, 3]) of the Esoteric Twist form (``lbm_et_info``)."""
+        if getattr(self, "_et", None) is None:
+            S, Sp = ctypes.c_int64(), ctypes.c_int64()
+            check(_lib.load().lbm_et_info(self._h, ctypes.byref(S), ctypes.byref(Sp), None), "lbm_et_info")
+            ph = np.empty((S.value - self.N, 3), np.int32)
+            check(_lib.load().lbm_et_info(self._h, None, None, ph.ctypes.data_as(ctypes.c_void_p)), "lbm_et_info")
+            self._et = (S.value, Sp.value, ph)
+        return self._et
+
+    def et_tables(self):
+        """Esoteric Twist tables on the host: nb [6, N] int32 and mask [N] uint32."""
+        nb = np.empty((6, self.N), np.int32)
+        mask = np.empty(self.N, np.uint32)
+        check(_lib.load().lbm_export_et_tables(self._h, nb.ctypes.data_as(ctypes.c_void_p),
+                                               mask.ctypes.data_as(ctypes.c_void_p)), "lbm_export_et_tables")
+        return nb, mask
 
     def reduce_workspace_bytes(self) -> int:
         b = ctypes.c_size_t()
@@ -353,7 +375,7 @@ class Partitioning:
 
 def lbm_init_equilibrium(lat, prec, params, pdf, layout, rho0=1.0, u0=(0.0, 0.0, 0.0), stream=None):
     prec = _prec(prec)
-    _check_grid(lat, prec, pdf, "pdf")
+    _check_grid(lat, prec, pdf, "pdf", layout)
     u = (ctypes.c_double * 3)(*[float(v) for v in u0])
     check(_lib.load().lbm_init_equilibrium(lat.handle, prec, ctypes.byref(params.c()), _ptr(pdf), layout,
                                            float(rho0), u, _stream(stream)), "lbm_init_equilibrium")
@@ -362,7 +384,7 @@ def lbm_init_equilibrium(lat, prec, params, pdf, layout, rho0=1.0, u0=(0.0, 0.0,
 def lbm_load_canonical(lat, prec, params, F, pdf, layout, stream=None):
     torch = _torch()
     prec = _prec(prec)
-    _check_grid(lat, prec, pdf, "pdf")
+    _check_grid(lat, prec, pdf, "pdf", layout)
     if not F.is_cuda or F.dtype != torch.float64 or tuple(F.shape) != (19, lat.N) or not F.is_contiguous():
         raise TypeError("F must be a contiguous CUDA float64 tensor [19, N]")
     check(_lib.load().lbm_load_canonical(lat.handle, prec, ctypes.byref(params.c()), _ptr(F), _ptr(pdf), layout,
@@ -372,7 +394,7 @@ def lbm_load_canonical(lat, prec, params, F, pdf, layout, stream=None):
 def lbm_canonical_pdfs(lat, prec, params, pdf, layout, F=None, stream=None):
     torch = _torch()
     prec = _prec(prec)
-    _check_grid(lat, prec, pdf, "pdf")
+    _check_grid(lat, prec, pdf, "pdf", layout)
     if F is None:
         F = torch.empty((19, lat.N), dtype=torch.float64, device=pdf.device)
     check(_lib.load().lbm_canonical_pdfs(lat.handle, prec, ctypes.byref(params.c()), _ptr(pdf), layout, _ptr(F),
@@ -403,11 +425,25 @@ def lbm_run_aa(lat, prec, params, pdf, start_parity, steps, s=None, ria=False, s
           "lbm_run_aa")
 
 
+def lbm_step_et(lat, prec, params, pdf, parity, s=None, stream=None):
+    prec = _prec(prec)
+    _check_grid(lat, prec, pdf, "pdf", LBM_LAYOUT_ET_EVEN)
+    check(_lib.load().lbm_step_et(lat.handle, prec, ctypes.byref(params.c()), _ptr(pdf), int(parity),
+                                  _ptr(_check_s(lat, s)), _stream(stream)), "lbm_step_et")
+
+
+def lbm_run_et(lat, prec, params, pdf, start_parity, steps, s=None, stream=None):
+    prec = _prec(prec)
+    _check_grid(lat, prec, pdf, "pdf", LBM_LAYOUT_ET_EVEN)
+    check(_lib.load().lbm_run_et(lat.handle, prec, ctypes.byref(params.c()), _ptr(pdf), int(start_parity),
+                                 int(steps), _ptr(_check_s(lat, s)), _stream(stream)), "lbm_run_et")
+
+
 def lbm_macroscopic(lat, prec, params, pdf, layout, s=None, fields=True, sums=True, workspace=None, stream=None):
     """(rho [N], u [3, N], sums [4]) as FP64 CUDA tensors (None where not asked for)."""
     torch = _torch()
     prec = _prec(prec)
-    _check_grid(lat, prec, pdf, "pdf")
+    _check_grid(lat, prec, pdf, "pdf", layout)
     dev = pdf.device
     rho = torch.empty(lat.N, dtype=torch.float64, device=dev) if fields else None
     u = torch.empty((3, lat.N), dtype=torch.float64, device=dev) if fields else None
@@ -518,7 +554,7 @@ def lbm_objective_flux(lat, prec, params, pdf, layout, s=None, lambda_T=None, gr
     """J (CUDA float64 [1]); optionally fills lambda_T = dJ/dF and grad_s = direct dJ/ds."""
     torch = _torch()
     prec = _prec(prec)
-    _check_grid(lat, prec, pdf, "pdf")
+    _check_grid(lat, prec, pdf, "pdf", layout)
     _check_adj(lat, prec, lambda_T, "lambda_T")
     J = torch.empty(1, dtype=torch.float64, device=pdf.device)
     ws_bytes = lat.reduce_workspace_bytes()
@@ -604,7 +640,7 @@ def flux_objective(s, lat, prec, params, G0, T, K, ria=False):
 
 
 class Solver:
-    """A running simulation in one storage form ("osnt" or "aa") and precision."""
+    """A running simulation in one storage form ("osnt", "aa" or "et" = Esoteric Twist) and precision."""
 
     def __init__(self, lat: Lattice, prec="f64", params: Params | None = None, form="aa", ria=True, s=None,
                  device="cuda"):
@@ -619,6 +655,10 @@ class Solver:
             self.grids = [lat.new_grid(self.prec, device), lat.new_grid(self.prec, device)]
         elif form == "aa":
             self.grids = [lat.new_grid(self.prec, device)]
+        elif form == "et":
+            if not lat.uploaded & LBM_TABLES_ET:
+                raise ValueError("the Esoteric Twist form needs lat.upload(which=... | LBM_TABLES_ET)")
+            self.grids = [lat.new_grid(self.prec, device, et=True)]
         else:
             raise ValueError(form)
 
@@ -626,6 +666,8 @@ class Solver:
     def layout(self):
         if self.form == "osnt":
             return LBM_LAYOUT_OSNT
+        if self.form == "et":
+            return LBM_LAYOUT_ET_EVEN if self.t % 2 == 0 else LBM_LAYOUT_ET_ODD
         return LBM_LAYOUT_AA_EVEN if self.t % 2 == 0 else LBM_LAYOUT_AA_ODD
 
     @property
@@ -646,6 +688,9 @@ class Solver:
                 lbm_step_osnt(self.lat, self.prec, self.params, self.grids[0], self.grids[1], self.s, self.ria, stream)
                 self.grids.reverse()
                 self.t += 1
+        elif self.form == "et":
+            lbm_run_et(self.lat, self.prec, self.params, self.grids[0], self.t % 2, n, self.s, stream)
+            self.t += n
         else:
             lbm_run_aa(self.lat, self.prec, self.params, self.grids[0], self.t % 2, n, self.s, self.ria, stream)
             self.t += n
@@ -679,6 +724,8 @@ class Solver:
                 if self.form == "osnt":
                     lbm_step_osnt(self.lat, self.prec, self.params, self.grids[0], self.grids[1], self.s, self.ria, st)
                     lbm_step_osnt(self.lat, self.prec, self.params, self.grids[1], self.grids[0], self.s, self.ria, st)
+                elif self.form == "et":
+                    lbm_run_et(self.lat, self.prec, self.params, self.grids[0], 0, 2, self.s, st)
                 else:
                     lbm_step_aa(self.lat, self.prec, self.params, self.grids[0], 0, self.s, self.ria, st)
                     lbm_step_aa(self.lat, self.prec, self.params, self.grids[0], 1, self.s, self.ria, st)
@@ -702,6 +749,8 @@ __all__ = [
     "Params", "Lattice", "Solver", "LbmError", "lbm_init_equilibrium", "lbm_load_canonical", "lbm_canonical_pdfs",
     "lbm_step_osnt", "lbm_step_aa", "lbm_run_aa", "lbm_macroscopic", "LBM_F64", "LBM_F32", "LBM_F16S", "LBM_F64_DF",
     "LBM_LAYOUT_OSNT", "LBM_LAYOUT_AA_EVEN", "LBM_LAYOUT_AA_ODD", "LBM_TABLES_ADJ", "LBM_TABLES_RIA",
+    "LBM_LAYOUT_ET_EVEN", "LBM_LAYOUT_ET_ODD", "LBM_TABLES_ET", "lbm_step_et", "lbm_run_et", "Partitioning",
+    "PartitionedSolver", "lbm_halo_exchange", "lbm_partition_run_aa", "lbm_partition_run_osnt",
     "lbm_objective_flux", "lbm_adjoint_step", "lbm_ckpt_workspace_bytes", "lbm_flux_forward", "lbm_flux_backward",
     "flux_objective", "new_adjoint", "lbm_macroscopic_noalloc", "lbm_check_finite", "lbm_bandwidth_kernel",
 ]

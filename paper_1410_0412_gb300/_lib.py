@@ -28,8 +28,11 @@ LBM_F64_DF = 3
 LBM_LAYOUT_OSNT = 0
 LBM_LAYOUT_AA_EVEN = 1
 LBM_LAYOUT_AA_ODD = 2
+LBM_LAYOUT_ET_EVEN = 3
+LBM_LAYOUT_ET_ODD = 4
 LBM_TABLES_ADJ = 1
 LBM_TABLES_RIA = 2
+LBM_TABLES_ET = 4
 LBM_HALO_OSNT = 0
 LBM_HALO_AA_GATHER = 1
 LBM_HALO_AA_SCATTER = 2
@@ -96,6 +99,10 @@ SIGNATURES = {
     "lbm_step_osnt": [_P, _I, ctypes.POINTER(lbm_params), _P, _P, _P, _I, _P],
     "lbm_step_aa": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _P, _I, _P],
     "lbm_run_aa": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _I, _P, _I, _P],
+    "lbm_et_info": [_P, _PI64, _PI64, _P],
+    "lbm_export_et_tables": [_P, _P, _P],
+    "lbm_step_et": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _P, _P],
+    "lbm_run_et": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _I, _P, _P],
     "lbm_reduce_workspace_bytes": [_P, _PSZ],
     "lbm_macroscopic": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _P, _P, _P, _P, _P, _SZ, _P],
     "lbm_bandwidth_kernel": [_I, _P, _P, _I64, _I, _P],

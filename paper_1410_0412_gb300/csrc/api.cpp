@@ -57,7 +57,7 @@ namespace {
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct TableLayout {
-  size_t adj = 0, run_adj = 0, head_bits = 0, warp_run0 = 0, warp_head0 = 0, total = 0;
+  size_t adj = 0, run_adj = 0, head_bits = 0, warp_run0 = 0, warp_head0 = 0, et_nb = 0, et_mask = 0, total = 0;
 };
 
 TableLayout table_layout(const lbm_lattice* L, int which) {
@@ -76,6 +76,12 @@ TableLayout table_layout(const lbm_lattice* L, int which) {
     off = align256(off + size_t(std::max<int64_t>(L->nwarps, 1)) * 4);
     t.warp_head0 = off;
     off = align256(off + size_t(std::max<int64_t>(L->nwarps, 1)) * 4);
+  }
+  if (which & LBM_TABLES_ET) {
+    t.et_nb = off;
+    off = align256(off + size_t(6) * L->Npad * 4);
+    t.et_mask = off;
+    off = align256(off + size_t(L->Npad) * 4);
   }
   t.total = off;
   return t;
@@ -116,9 +122,23 @@ int check_whole(const lbm_lattice* L, const char* what) {
 }
 
 int check_layout(int layout) {
-  if (layout < LBM_LAYOUT_OSNT || layout > LBM_LAYOUT_AA_ODD) return set_error(LBM_ERR_ARG, "unknown layout");
+  if (layout < LBM_LAYOUT_OSNT || layout > LBM_LAYOUT_ET_ODD) return set_error(LBM_ERR_ARG, "unknown layout");
   return LBM_OK;
 }
+
+// The device tables a layout's gathers need: none for AA_EVEN, the Esoteric
+// Twist tables for the ET layouts, any addressing for the others.
+int layout_tables(const lbm_lattice* L, int layout) {
+  if (L->N == 0 || layout == LBM_LAYOUT_AA_EVEN) return LBM_OK;
+  if (layout >= LBM_LAYOUT_ET_EVEN) {
+    if (!(L->uploaded & LBM_TABLES_ET)) return set_error(LBM_ERR_ARG, "Esoteric Twist tables not uploaded to the device");
+    return LBM_OK;
+  }
+  int ria;
+  return any_tables(L, &ria);
+}
+
+constexpr int kAllTables = LBM_TABLES_ADJ | LBM_TABLES_RIA | LBM_TABLES_ET;
 
 }  // namespace
 
@@ -292,14 +312,18 @@ int lbm_validate_tables(const lbm_lattice* L) {
 int lbm_device_table_bytes(const lbm_lattice* L, int which, size_t* bytes) {
   if (int rc = check_lat(L)) return rc;
   if (!bytes) return set_error(LBM_ERR_ARG, "bytes is NULL");
-  if (which <= 0 || which > (LBM_TABLES_ADJ | LBM_TABLES_RIA)) return set_error(LBM_ERR_ARG, "bad table selection");
+  if (which <= 0 || which > kAllTables) return set_error(LBM_ERR_ARG, "bad table selection");
+  if (which & LBM_TABLES_ET)
+    if (int rc = derive_et(const_cast<lbm_lattice*>(L))) return rc;
   *bytes = table_layout(L, which).total;
   return LBM_OK;
 }
 
 int lbm_lattice_upload(lbm_lattice* L, int which, void* dev, size_t bytes, void* stream) {
   if (int rc = check_lat(L)) return rc;
-  if (which <= 0 || which > (LBM_TABLES_ADJ | LBM_TABLES_RIA)) return set_error(LBM_ERR_ARG, "bad table selection");
+  if (which <= 0 || which > kAllTables) return set_error(LBM_ERR_ARG, "bad table selection");
+  if (which & LBM_TABLES_ET)
+    if (int rc = derive_et(L)) return rc;
   TableLayout t = table_layout(L, which);
   if (!dev) return set_error(LBM_ERR_ARG, "device table buffer is NULL");
   if (reinterpret_cast<uintptr_t>(dev) % 256) return set_error(LBM_ERR_ARG, "device table buffer not 256-byte aligned");
@@ -328,6 +352,15 @@ int lbm_lattice_upload(lbm_lattice* L, int which, void* dev, size_t bytes, void*
     L->dev.head_bits = reinterpret_cast<const uint32_t*>(base + t.head_bits);
     L->dev.warp_run0 = reinterpret_cast<const int32_t*>(base + t.warp_run0);
     L->dev.warp_head0 = reinterpret_cast<const int32_t*>(base + t.warp_head0);
+  }
+  if (which & LBM_TABLES_ET) {
+    e = cudaMemcpyAsync(base + t.et_nb, L->et_nb.data(), L->et_nb.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(base + t.et_mask, L->et_mask.data(), L->et_mask.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return set_error(LBM_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+    L->dev.et_nb = reinterpret_cast<const int32_t*>(base + t.et_nb);
+    L->dev.et_mask = reinterpret_cast<const uint32_t*>(base + t.et_mask);
+    L->dev.spad = uint32_t(L->et_Spad);
   }
   L->dev.Npad = L->Npad;
   L->dev.Rpad = L->Rpad;
@@ -359,10 +392,7 @@ int lbm_init_equilibrium(const lbm_lattice* L, int prec, const lbm_params* param
   if (int rc = check_layout(layout)) return rc;
   if (!pdf || !u0) return set_error(LBM_ERR_ARG, "pdf or u0 is NULL");
   if (!(rho0 > 0.0) || !std::isfinite(rho0)) return set_error(LBM_ERR_ARG, "rho0 must be > 0");
-  if (layout != LBM_LAYOUT_AA_EVEN && L->N > 0) {
-    int ria;
-    if (int rc = any_tables(L, &ria)) return rc;
-  }
+  if (int rc = layout_tables(L, layout)) return rc;
   return LBM_DISPATCH(prec, launch_init_eq_t, L, kp, pdf, layout, rho0, u0, stream);
 }
 
@@ -375,10 +405,7 @@ int lbm_load_canonical(const lbm_lattice* L, int prec, const lbm_params* params,
   if (layout != LBM_LAYOUT_AA_EVEN)
     if (int rc = check_whole(L, "loading a pulled layout")) return rc;
   if (!pdf || (!F && L->N > 0)) return set_error(LBM_ERR_ARG, "pdf or F is NULL");
-  if (layout != LBM_LAYOUT_AA_EVEN && L->N > 0) {
-    int ria;
-    if (int rc = any_tables(L, &ria)) return rc;
-  }
+  if (int rc = layout_tables(L, layout)) return rc;
   return LBM_DISPATCH(prec, launch_load_canonical_t, L, kp, F, pdf, layout, stream);
 }
 
@@ -389,10 +416,7 @@ int lbm_canonical_pdfs(const lbm_lattice* L, int prec, const lbm_params* params,
   if (int rc = make_kparams(params, prec, &kp)) return rc;
   if (int rc = check_layout(layout)) return rc;
   if (!pdf || (!F && L->N > 0)) return set_error(LBM_ERR_ARG, "pdf or F is NULL");
-  if (layout != LBM_LAYOUT_AA_EVEN && L->N > 0) {
-    int ria;
-    if (int rc = any_tables(L, &ria)) return rc;
-  }
+  if (int rc = layout_tables(L, layout)) return rc;
   return LBM_DISPATCH(prec, launch_canonical_t, L, kp, pdf, layout, F, stream);
 }
 
@@ -438,6 +462,45 @@ int lbm_run_aa(const lbm_lattice* L, int prec, const lbm_params* params, void* p
   return LBM_OK;
 }
 
+int lbm_et_info(lbm_lattice* L, int64_t* S, int64_t* Spad, int32_t* phantom_xyz) {
+  if (int rc = check_lat(L)) return rc;
+  if (int rc = derive_et(L)) return rc;
+  if (S) *S = L->et_S;
+  if (Spad) *Spad = L->et_Spad;
+  if (phantom_xyz && !L->et_phantom.empty())
+    std::memcpy(phantom_xyz, L->et_phantom.data(), L->et_phantom.size() * sizeof(int32_t));
+  return LBM_OK;
+}
+
+int lbm_export_et_tables(lbm_lattice* L, int32_t* nb, uint32_t* mask) {
+  if (int rc = check_lat(L)) return rc;
+  if (int rc = derive_et(L)) return rc;
+  if (nb)
+    for (int k = 0; k < 6; ++k) std::memcpy(nb + k * L->N, &L->et_nb[k * L->Npad], size_t(L->N) * 4);
+  if (mask) std::memcpy(mask, L->et_mask.data(), size_t(L->N) * 4);
+  return LBM_OK;
+}
+
+int lbm_run_et(const lbm_lattice* L, int prec, const lbm_params* params, void* pdf, int start_parity, int steps,
+               const float* s, void* stream) {
+  if (int rc = check_lat(L)) return rc;
+  KParams kp;
+  if (int rc = make_kparams(params, prec, &kp)) return rc;
+  if (!pdf) return set_error(LBM_ERR_ARG, "pdf is NULL");
+  if (start_parity != 0 && start_parity != 1) return set_error(LBM_ERR_ARG, "parity must be 0 or 1");
+  if (steps < 0) return set_error(LBM_ERR_ARG, "steps must be >= 0");
+  if (L->N == 0 || steps == 0) return LBM_OK;
+  if (!(L->uploaded & LBM_TABLES_ET)) return set_error(LBM_ERR_ARG, "Esoteric Twist tables not uploaded to the device");
+  for (int t = 0; t < steps; ++t)
+    if (int rc = LBM_DISPATCH_STEP(prec, launch_et_t, L, kp, pdf, (start_parity + t) & 1, s, stream)) return rc;
+  return LBM_OK;
+}
+
+int lbm_step_et(const lbm_lattice* L, int prec, const lbm_params* params, void* pdf, int parity, const float* s,
+                void* stream) {
+  return lbm_run_et(L, prec, params, pdf, parity, 1, s, stream);
+}
+
 int lbm_reduce_workspace_bytes(const lbm_lattice* L, size_t* bytes) {
   if (int rc = check_lat(L)) return rc;
   if (!bytes) return set_error(LBM_ERR_ARG, "bytes is NULL");
@@ -457,10 +520,7 @@ int lbm_macroscopic(const lbm_lattice* L, int prec, const lbm_params* params, co
   if (sums && (!workspace || ws_bytes < size_t(parts) * 4 * sizeof(double)))
     return set_error(LBM_ERR_ARG, "reduction workspace missing or too small");
   if (reinterpret_cast<uintptr_t>(workspace) % 8) return set_error(LBM_ERR_ARG, "workspace not 8-byte aligned");
-  if (layout != LBM_LAYOUT_AA_EVEN && L->N > 0) {
-    int ria;
-    if (int rc = any_tables(L, &ria)) return rc;
-  }
+  if (int rc = layout_tables(L, layout)) return rc;
   return LBM_DISPATCH(prec, launch_macroscopic_t, L, kp, pdf, layout, s, rho, u, sums,
                       static_cast<double*>(workspace), parts, stream);
 }
@@ -478,10 +538,7 @@ int lbm_objective_flux(const lbm_lattice* L, int prec, const lbm_params* params,
   const int64_t parts = reduce_parts(L);
   if (!workspace || ws_bytes < size_t(parts) * 4 * sizeof(double))
     return set_error(LBM_ERR_ARG, "reduction workspace missing or too small");
-  if (layout != LBM_LAYOUT_AA_EVEN && L->N > 0) {
-    int ria;
-    if (int rc = any_tables(L, &ria)) return rc;
-  }
+  if (int rc = layout_tables(L, layout)) return rc;
   return LBM_DISPATCH(prec, launch_objective_t, L, kp, pdf, layout, s, J, lambda_T, grad_s,
                       static_cast<double*>(workspace), stream);
 }

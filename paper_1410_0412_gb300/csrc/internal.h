@@ -38,6 +38,9 @@ struct DevTables {
   int64_t Npad = 0, Rpad = 0, R = 0, nwarps = 0;
   uint32_t npad = 0, rpad = 0;          // the same strides as 32-bit values (N < 2^31)
   int pressure = 0;                     // the lattice has inlet/outlet markers
+  const int32_t* et_nb = nullptr;       // [6][Npad]   Esoteric Twist neighbour locations
+  const uint32_t* et_mask = nullptr;    // [Npad]      Esoteric Twist link kinds
+  uint32_t spad = 0;                    // Esoteric Twist grid stride (nodes + phantoms, padded)
 };
 
 // Ghost slots of a partition: local node index space [0, N_p) followed by the
@@ -79,6 +82,12 @@ struct lbm_lattice {
   std::vector<int32_t> warp_run0;  // [nwarps]  run holding node 32w
   std::vector<int32_t> warp_head0; // [nwarps]  first node of that run
   int64_t hist[33] = {0};
+  // Esoteric Twist tables, derived on first use (derive_et)
+  int et_ready = 0;
+  int64_t et_S = 0, et_Spad = 0;   // storage locations (nodes + phantoms) and the padded grid stride
+  std::vector<int32_t> et_nb;      // [6][Npad] storage index of n + (+x, +y, +z, +x+y, +x+z, +y+z)
+  std::vector<uint32_t> et_mask;   // [Npad] bit i-1: pull i meets a marker; bits 18..27: pressure faces
+  std::vector<int32_t> et_phantom; // [S-N][3] coordinates of the phantom locations
   int uploaded = 0;                // LBM_TABLES_* bits present on the device
   int partition_local = 0;         // a partition's local lattice: entries >= N are ghost slots
   lbm::DevTables dev;
@@ -122,6 +131,7 @@ int build_partitioning(const lbm_lattice* G, int P, lbm_partitioning* out);   //
 int validate_partitioning(const lbm_partitioning* S, const lbm_lattice* G);
 int launch_halo(const lbm_partitioning* S, int prec, void* const* grids, int mode, void* stream);  // halo.cu
 int derive_ria(lbm_lattice* L);
+int derive_et(lbm_lattice* L);   // Esoteric Twist tables (idempotent)
 int validate(const lbm_lattice* L);
 int validate_runs(const lbm_lattice* L);  // the RIA tables alone (any index range)
 
@@ -144,6 +154,8 @@ int launch_osnt_t(const lbm_lattice* L, const KParams& kp, const void* src, void
 template <int PREC>
 int launch_aa_t(const lbm_lattice* L, const KParams& kp, void* pdf, int parity, const float* s, int ria,
                 void* stream);
+template <int PREC>
+int launch_et_t(const lbm_lattice* L, const KParams& kp, void* pdf, int parity, const float* s, void* stream);
 template <int PREC>
 int launch_init_eq_t(const lbm_lattice* L, const KParams& kp, void* pdf, int layout, double rho0, const double* u0,
                      void* stream);

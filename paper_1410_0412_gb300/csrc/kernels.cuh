@@ -43,6 +43,10 @@ template <int PREC> struct MinCtas { static constexpr int value = 5; };
 template <> struct MinCtas<LBM_F64_DF> { static constexpr int value = 6; };
 template <int PREC> struct MinCtasOdd { static constexpr int value = 8; };
 template <> struct MinCtasOdd<LBM_F64> { static constexpr int value = 5; };
+// The Esoteric Twist step keeps seven locations and the link mask live across
+// the collision: the double-float path gets 6 CTAs (<= 85 registers).
+template <int PREC> struct MinCtasEt { static constexpr int value = MinCtasOdd<PREC>::value; };
+template <> struct MinCtasEt<LBM_F64_DF> { static constexpr int value = 6; };
 static_assert(kBlock % kWarpNodes == 0, "a warp must cover one run-index group");
 
 // ---- storage traits -----------------------------------------------------------------
@@ -517,6 +521,85 @@ __global__ void __launch_bounds__(kBlock, MinCtasOdd<PREC>::value) k_aa_odd(DevT
   }
 }
 
+// ---- Esoteric Twist: one grid, in place (named in Sect. 1 and Sect. 4) ------------------
+// The link between n and n + c_i keeps its two slots (one per travel
+// direction) at location n + c_i^+, c^+ = componentwise max(c, 0), so a node
+// touches only itself and six neighbour locations, whose storage indices are
+// the table et_nb[6][Npad] (+x, +y, +z, +x+y, +x+z, +y+z; phantom locations
+// past N hold the slots of links through non-fluid cells).  Even step: read
+// f_i from slot i at n + c_inv(i)^+, write P_j to slot inv(j) at n + c_j^+ (the
+// slot f_inv(j) came from).  Odd step: slots inv(i) and j.  A link to a wall
+// or a pressure face (et_mask bit inv(j) - 1) stores the bounced value in the
+// pair's other slot, the one this node reads next step.
+__host__ __device__ constexpr int et_row(int i) {
+  return (cx(i) > 0 ? 1 : 0) + (cy(i) > 0 ? 2 : 0) + (cz(i) > 0 ? 4 : 0) == 0   ? -1
+         : (cx(i) > 0 ? 1 : 0) + (cy(i) > 0 ? 2 : 0) + (cz(i) > 0 ? 4 : 0) == 1 ? 0
+         : (cx(i) > 0 ? 1 : 0) + (cy(i) > 0 ? 2 : 0) + (cz(i) > 0 ? 4 : 0) == 2 ? 1
+         : (cx(i) > 0 ? 1 : 0) + (cy(i) > 0 ? 2 : 0) + (cz(i) > 0 ? 4 : 0) == 4 ? 2
+         : (cx(i) > 0 ? 1 : 0) + (cy(i) > 0 ? 2 : 0) + (cz(i) > 0 ? 4 : 0) == 3 ? 3
+         : (cx(i) > 0 ? 1 : 0) + (cy(i) > 0 ? 2 : 0) + (cz(i) > 0 ? 4 : 0) == 5 ? 4
+                                                                                : 5;
+}
+// et_mask bit of "pull direction i (c_ix != 0) meets a pressure face"
+__host__ __device__ constexpr int et_xbit(int i) { return i <= 2 ? 17 + i : 13 + i; }
+static_assert(et_row(1) == 0 && et_row(2) == -1 && et_row(7) == 3 && et_row(9) == 0 && et_row(10) == 1 &&
+                  et_row(11) == 4 && et_row(14) == 2 && et_row(15) == 5 && et_row(17) == 1 && et_row(18) == 2,
+              "ET location rows");
+static_assert(et_xbit(1) == 18 && et_xbit(2) == 19 && et_xbit(7) == 20 && et_xbit(14) == 27, "ET pressure bits");
+
+__device__ __forceinline__ void et_locations(const DevTables& t, int n, int (&loc)[7]) {
+  loc[0] = n;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) loc[k + 1] = __ldg(t.et_nb + at(k, t.npad, n));
+}
+
+template <int PREC, bool ODD, bool FORCE, bool DRAG>
+__global__ void __launch_bounds__(kBlock, MinCtasEt<PREC>::value) k_et(DevTables t, KParams kp,
+                                                                          CollConst<typename St<PREC>::R> c,
+                                                                          typename St<PREC>::T* __restrict__ A,
+                                                                          const float* __restrict__ s, int N) {
+  using R = typename St<PREC>::R;
+  // As in the AA odd step, the wider precisions park the six locations and
+  // the mask in shared memory across the collision (lane-consecutive, no bank
+  // conflicts); FP16 keeps them in registers.
+  constexpr bool kStash = PREC != LBM_F16S;
+  __shared__ int s_loc[kStash ? 7 : 1][kBlock];
+  const int n = blockIdx.x * kBlock + threadIdx.x;
+  if (n >= N) return;
+  int loc[7];
+  et_locations(t, n, loc);
+  R d[kQ];
+  d[0] = St<PREC>::ld(A + n, kp.inv_scale);
+#pragma unroll
+  for (int i = 1; i < kQ; ++i)
+    d[i] = St<PREC>::ld(A + at(ODD ? inv(i) : i, t.spad, loc[et_row(inv(i)) + 1]), kp.inv_scale);
+  unsigned mask = __ldg(t.et_mask + n);
+  if (kStash) {
+#pragma unroll
+    for (int k = 1; k < 7; ++k) s_loc[k - 1][threadIdx.x] = loc[k];
+    s_loc[6][threadIdx.x] = int(mask);
+  }
+  const R sn = DRAG ? R(__ldg(s + n)) : R(0);
+  collide<R, FORCE, DRAG>(d, c, sn);
+  St<PREC>::st(A + n, d[0], kp.scale);
+  if (kStash) {
+#pragma unroll
+    for (int k = 1; k < 7; ++k) loc[k] = s_loc[k - 1][threadIdx.x];
+    mask = unsigned(s_loc[6][threadIdx.x]);
+  }
+#pragma unroll
+  for (int j = 1; j < kQ; ++j) {
+    const int jj = inv(j);
+    const bool link = !((mask >> (jj - 1)) & 1u);
+    R v = d[j];
+    if (cx(jj) != 0) {
+      if (t.pressure && ((mask >> et_xbit(jj)) & 1u))
+        v = (cx(jj) > 0 ? c.abb_in[wclass(j) - 1] : c.abb_out[wclass(j) - 1]) - v;
+    }
+    St<PREC>::st(A + at(link != ODD ? jj : j, t.spad, loc[et_row(j) + 1]), v, kp.scale);
+  }
+}
+
 }  // namespace dev
 }  // namespace lbm
 
@@ -541,6 +624,17 @@ __global__ void __launch_bounds__(kBlock) k_init_eq(DevTables t, KParams kp, Feq
   using R = typename St<PREC>::R;
   const int n0 = blockIdx.x * kBlock;
   const int n = n0 + threadIdx.x;
+  if (layout >= LBM_LAYOUT_ET_EVEN) {  // every slot a node reads holds its f_i directly
+    if (n >= N) return;
+    int loc[7];
+    et_locations(t, n, loc);
+    St<PREC>::st(pdf + n, R(feq.v[0] - wgt(0) * kp.rho_s), kp.scale);
+#pragma unroll
+    for (int i = 1; i < kQ; ++i)
+      St<PREC>::st(pdf + at(layout == LBM_LAYOUT_ET_ODD ? inv(i) : i, t.spad, loc[et_row(inv(i)) + 1]),
+                   R(feq.v[i] - wgt(i) * kp.rho_s), kp.scale);
+    return;
+  }
   int m[18];
   if (layout != LBM_LAYOUT_AA_EVEN) {
     if (RIA) {
@@ -576,6 +670,17 @@ __global__ void __launch_bounds__(kBlock) k_load_canonical(DevTables t, KParams 
   using R = typename St<PREC>::R;
   const int n0 = blockIdx.x * kBlock;
   const int n = n0 + threadIdx.x;
+  if (layout >= LBM_LAYOUT_ET_EVEN) {
+    if (n >= N) return;
+    int loc[7];
+    et_locations(t, n, loc);
+    St<PREC>::st(pdf + n, R(F[n] - wgt(0) * kp.rho_s), kp.scale);
+#pragma unroll
+    for (int i = 1; i < kQ; ++i)
+      St<PREC>::st(pdf + at(layout == LBM_LAYOUT_ET_ODD ? inv(i) : i, t.spad, loc[et_row(inv(i)) + 1]),
+                   R(F[size_t(i) * N + n] - wgt(i) * kp.rho_s), kp.scale);
+    return;
+  }
   int m[18];
   if (layout != LBM_LAYOUT_AA_EVEN) {
     if (RIA) {
@@ -615,6 +720,20 @@ __device__ __forceinline__ bool node_canonical(const DevTables& t, const KParams
                                                const typename St<PREC>::T* pdf, int layout, int n, int N,
                                                double (&F)[kQ]) {
   using R = typename St<PREC>::R;
+  R d[kQ];
+  if (layout >= LBM_LAYOUT_ET_EVEN) {
+    if (n >= N) return false;
+    int loc[7];
+    et_locations(t, n, loc);
+    d[0] = St<PREC>::ld(pdf + n, kp.inv_scale);
+#pragma unroll
+    for (int i = 1; i < kQ; ++i)
+      d[i] = St<PREC>::ld(pdf + at(layout == LBM_LAYOUT_ET_ODD ? inv(i) : i, t.spad, loc[et_row(inv(i)) + 1]),
+                          kp.inv_scale);
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) F[i] = double(d[i]) + wgt(i) * kp.rho_s;
+    return true;
+  }
   int m[18];
   if (layout != LBM_LAYOUT_AA_EVEN) {
     if (RIA) {
@@ -627,7 +746,6 @@ __device__ __forceinline__ bool node_canonical(const DevTables& t, const KParams
   } else if (n >= N) {
     return false;
   }
-  R d[kQ];
   if (layout == LBM_LAYOUT_AA_EVEN) {
 #pragma unroll
     for (int i = 0; i < kQ; ++i) d[i] = St<PREC>::ld(pdf + at(i, t.npad, n), kp.inv_scale);
@@ -809,6 +927,27 @@ int launch_aa_t(const lbm_lattice* L, const KParams& kp, void* pdf, int parity, 
 }
 
 template <int PREC>
+int launch_et_t(const lbm_lattice* L, const KParams& kp, void* pdf, int parity, const float* s, void* stream) {
+  using T = typename dev::St<PREC>::T;
+  auto st = static_cast<cudaStream_t>(stream);
+  const unsigned g = grid_of(L->N);
+  T* A = static_cast<T*>(pdf);
+  const int N = int(L->N);
+  const bool f = has_force(kp);
+  const auto c = dev::make_coll<typename dev::St<PREC>::R>(kp);
+#define LBM_ET(O_, F_, D_) dev::k_et<PREC, O_, F_, D_><<<g, dev::kBlock, 0, st>>>(L->dev, kp, c, A, s, N)
+  if (s) {
+    if (parity) LBM_ET(true, true, true); else LBM_ET(false, true, true);
+  } else if (f) {
+    if (parity) LBM_ET(true, true, false); else LBM_ET(false, true, false);
+  } else {
+    if (parity) LBM_ET(true, false, false); else LBM_ET(false, false, false);
+  }
+#undef LBM_ET
+  return cuda_check("Esoteric Twist step launch");
+}
+
+template <int PREC>
 int launch_init_eq_t(const lbm_lattice* L, const KParams& kp, void* pdf, int layout, double rho0, const double u0[3],
                      void* stream) {
   using T = typename dev::St<PREC>::T;
@@ -889,11 +1028,13 @@ int launch_macroscopic_t(const lbm_lattice* L, const KParams& kp, const void* pd
 
 #define LBM_INSTANTIATE_STEP_LAUNCHERS(P)                                                                          \
   template int launch_osnt_t<P>(const lbm_lattice*, const KParams&, const void*, void*, const float*, int, void*); \
-  template int launch_aa_t<P>(const lbm_lattice*, const KParams&, void*, int, const float*, int, void*);
+  template int launch_aa_t<P>(const lbm_lattice*, const KParams&, void*, int, const float*, int, void*);           \
+  template int launch_et_t<P>(const lbm_lattice*, const KParams&, void*, int, const float*, void*);
 
 #define LBM_INSTANTIATE_LAUNCHERS(P)                                                                               \
   template int launch_osnt_t<P>(const lbm_lattice*, const KParams&, const void*, void*, const float*, int, void*); \
   template int launch_aa_t<P>(const lbm_lattice*, const KParams&, void*, int, const float*, int, void*);           \
+  template int launch_et_t<P>(const lbm_lattice*, const KParams&, void*, int, const float*, void*);                \
   template int launch_init_eq_t<P>(const lbm_lattice*, const KParams&, void*, int, double, const double*, void*);  \
   template int launch_load_canonical_t<P>(const lbm_lattice*, const KParams&, const double*, void*, int, void*);   \
   template int launch_canonical_t<P>(const lbm_lattice*, const KParams&, const void*, int, double*, void*);        \

@@ -403,6 +403,69 @@ int partition_ghosts(const lbm_lattice* L, int P, int64_t* ghosts) {
   return LBM_OK;
 }
 
+// Esoteric Twist tables.  The six locations n + (+x, +y, +z, +x+y, +x+z,
+// +y+z) are the pull sources of directions 2, 4, 6, 8, 12 and 16, so a
+// non-negative adjacency entry already names the fluid node there; every
+// other location gets a phantom storage index N + rank, ranks in
+// lexicographic order of the (wrapped) coordinates, x fastest.
+int derive_et(lbm_lattice* L) {
+  if (L->et_ready) return LBM_OK;
+  if (L->partition_local)
+    return set_error(LBM_ERR_UNSUPPORTED, "Esoteric Twist tables need a whole lattice, not a partition's local one");
+  static const int kSrcDir[6] = {2, 4, 6, 8, 12, 16};
+  static const int kOff[6][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}};
+  const int64_t N = L->N, Np = L->Npad;
+  const bool have_xyz = int64_t(L->node_xyz.size()) == 3 * N;
+  const int64_t X = L->X, Y = L->Y;
+  std::vector<int32_t> nb(size_t(6) * Np, -1);
+  std::vector<uint32_t> mask(Np, 0u);
+  std::vector<std::pair<uint64_t, int64_t>> cand;  // (location key, k * Np + n)
+  for (int k = 0; k < 6; ++k)
+    for (int64_t n = 0; n < N; ++n) {
+      const int32_t m = L->adj[(kSrcDir[k] - 1) * Np + n];
+      if (m >= 0) {
+        nb[k * Np + n] = m;
+        continue;
+      }
+      if (!have_xyz)
+        return set_error(LBM_ERR_UNSUPPORTED, "Esoteric Twist phantom locations need node coordinates");
+      int64_t p[3];
+      const int64_t dim[3] = {L->X, L->Y, L->Z};
+      for (int a = 0; a < 3; ++a) {
+        p[a] = L->node_xyz[3 * n + a] + kOff[k][a];
+        if (L->bc.periodic[a] && p[a] == dim[a]) p[a] = 0;
+      }
+      cand.emplace_back(uint64_t((p[2] * (Y + 1) + p[1]) * (X + 1) + p[0]), k * Np + n);
+    }
+  std::vector<uint64_t> keys(cand.size());
+  for (size_t c = 0; c < cand.size(); ++c) keys[c] = cand[c].first;
+  std::sort(keys.begin(), keys.end());
+  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+  const int64_t M = int64_t(keys.size());
+  if (N + M > INT32_MAX) return set_error(LBM_ERR_UNSUPPORTED, "too many Esoteric Twist storage locations");
+  for (const auto& c : cand)
+    nb[c.second] = int32_t(N + (std::lower_bound(keys.begin(), keys.end(), c.first) - keys.begin()));
+  std::vector<int32_t> ph(size_t(3) * M);
+  for (int64_t r = 0; r < M; ++r) {
+    ph[3 * r] = int32_t(keys[r] % uint64_t(X + 1));
+    ph[3 * r + 1] = int32_t((keys[r] / uint64_t(X + 1)) % uint64_t(Y + 1));
+    ph[3 * r + 2] = int32_t(keys[r] / uint64_t((X + 1) * (Y + 1)));
+  }
+  for (int i = 1; i < kQ; ++i)
+    for (int64_t n = 0; n < N; ++n) {
+      const int32_t m = L->adj[(i - 1) * Np + n];
+      if (m < 0) mask[n] |= 1u << (i - 1);
+      if (kCX[i] != 0 && m <= LBM_MARK_INLET) mask[n] |= 1u << (i <= 2 ? 17 + i : 13 + i);
+    }
+  L->et_nb.swap(nb);
+  L->et_mask.swap(mask);
+  L->et_phantom.swap(ph);
+  L->et_S = N + M;
+  L->et_Spad = round_up(std::max<int64_t>(N + M, 1), kPad);
+  L->et_ready = 1;
+  return LBM_OK;
+}
+
 int build_tables(lbm_lattice* L, const uint8_t* solid) {
   int rc = (L->enumeration == LBM_ENUM_HILBERT) ? enumerate_hilbert(L, solid)
                                                  : enumerate_lex(L, solid, L->block_B);
