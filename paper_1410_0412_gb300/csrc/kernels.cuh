@@ -43,10 +43,12 @@ template <int PREC> struct MinCtas { static constexpr int value = 5; };
 template <> struct MinCtas<LBM_F64_DF> { static constexpr int value = 6; };
 template <int PREC> struct MinCtasOdd { static constexpr int value = 8; };
 template <> struct MinCtasOdd<LBM_F64> { static constexpr int value = 5; };
-// The Esoteric Twist step keeps seven locations and the link mask live across
-// the collision: the double-float path gets 6 CTAs (<= 85 registers).
-template <int PREC> struct MinCtasEt { static constexpr int value = MinCtasOdd<PREC>::value; };
+// The Esoteric Twist step: every step is indirect, and a sweep of 6/8/10/12
+// on GB300 put FP32 and FP16 at 10 CTAs (<= 51 registers; +3-5 % over 8).
+// Double-float keeps 6 (its collision needs the registers), native FP64 5.
+template <int PREC> struct MinCtasEt { static constexpr int value = 10; };
 template <> struct MinCtasEt<LBM_F64_DF> { static constexpr int value = 6; };
+template <> struct MinCtasEt<LBM_F64> { static constexpr int value = 5; };
 static_assert(kBlock % kWarpNodes == 0, "a warp must cover one run-index group");
 
 // ---- storage traits -----------------------------------------------------------------
