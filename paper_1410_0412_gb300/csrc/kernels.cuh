@@ -34,15 +34,20 @@ __host__ __device__ constexpr double wgt(int i) { return i == 0 ? 1.0 / 3.0 : (i
 
 constexpr int kBlock = 128;  // nodes per CTA of the step kernels (one node per thread)
 // Minimum resident CTAs per SM of the step kernels (caps registers at
-// 65536 / (128 * n)).  The AA odd step is latency-bound (index loads, then
-// gathers, then scattered stores): 8 CTAs (<= 64 registers) were the fastest
-// caps measured on GB300 for FP32, FP16 and the double-float path; the
-// native FP64 path stays at 5 (it is FP64-pipe bound, and 8 spills hundreds
-// of bytes).
-template <int PREC> struct MinCtas { static constexpr int value = 5; };
-template <> struct MinCtas<LBM_F64_DF> { static constexpr int value = 6; };
-template <int PREC> struct MinCtasOdd { static constexpr int value = 8; };
-template <> struct MinCtasOdd<LBM_F64> { static constexpr int value = 5; };
+// 65536 / (128 * n)), from sweeps of 4..12 on GB300.  The indirect steps are
+// latency-bound (index words, then gathers, then scattered stores): with RIA
+// (fewer live index registers) FP32 and FP16 are fastest at 10 CTAs
+// (<= 51 registers), with the adjacency list at 8 (AA odd) or 5 (OS-NT).  The
+// double-float path takes 8 (AA odd) and 6 (others).  Native FP64 stays at 5:
+// it is bound by the FP64 pipe, and its time did not move between 4 and 7.
+template <int PREC, bool RIA> struct MinCtasOsnt { static constexpr int value = RIA ? 10 : 5; };
+template <bool RIA> struct MinCtasOsnt<LBM_F64, RIA> { static constexpr int value = 5; };
+template <bool RIA> struct MinCtasOsnt<LBM_F64_DF, RIA> { static constexpr int value = 6; };
+template <int PREC> struct MinCtasEven { static constexpr int value = 5; };
+template <> struct MinCtasEven<LBM_F64_DF> { static constexpr int value = 6; };
+template <int PREC, bool RIA> struct MinCtasOdd { static constexpr int value = RIA ? 10 : 8; };
+template <bool RIA> struct MinCtasOdd<LBM_F64, RIA> { static constexpr int value = 5; };
+template <bool RIA> struct MinCtasOdd<LBM_F64_DF, RIA> { static constexpr int value = 8; };
 // The Esoteric Twist step: every step is indirect, and a sweep of 6/8/10/12
 // on GB300 put FP32 and FP16 at 10 CTAs (<= 51 registers; +3-5 % over 8).
 // Double-float keeps 6 (its collision needs the registers), native FP64 5.
@@ -386,7 +391,7 @@ __device__ __forceinline__ void gather(const typename St<PREC>::T* g, uint32_t n
 // OS-NT step: pull (indirect) from src, collide, store locally into dst with
 // evict-first stores so the write stream does not push src out of L2.
 template <int PREC, bool RIA, bool FORCE, bool DRAG>
-__global__ void __launch_bounds__(kBlock, MinCtas<PREC>::value) k_osnt(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
+__global__ void __launch_bounds__(kBlock, MinCtasOsnt<PREC, RIA>::value) k_osnt(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
                                                  const typename St<PREC>::T* __restrict__ src,
                                                  typename St<PREC>::T* __restrict__ dst, const float* __restrict__ s,
                                                  int N) {
@@ -412,7 +417,7 @@ __global__ void __launch_bounds__(kBlock, MinCtas<PREC>::value) k_osnt(DevTables
 // AA even step: direct read of the 19 local PDFs, collide, write to the
 // opposite local slots (no index loads at all).
 template <int PREC, bool FORCE, bool DRAG>
-__global__ void __launch_bounds__(kBlock, MinCtas<PREC>::value) k_aa_even(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
+__global__ void __launch_bounds__(kBlock, MinCtasEven<PREC>::value) k_aa_even(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
                                                     typename St<PREC>::T* __restrict__ A,
                                                     const float* __restrict__ s, int N) {
   using R = typename St<PREC>::R;
@@ -465,7 +470,7 @@ __global__ void __launch_bounds__(kBlock) k_aa_even_h2(DevTables t, KParams kp, 
 // AA odd step: read f_i from the neighbour's opposite slot A[inv i][m_i], collide,
 // write p_i to A[i][m_{inv i}] -- the same 19 slots, so in place and race-free.
 template <int PREC, bool RIA, bool FORCE, bool DRAG>
-__global__ void __launch_bounds__(kBlock, MinCtasOdd<PREC>::value) k_aa_odd(DevTables t, KParams kp,
+__global__ void __launch_bounds__(kBlock, MinCtasOdd<PREC, RIA>::value) k_aa_odd(DevTables t, KParams kp,
                                                                               CollConst<typename St<PREC>::R> c,
                                                                               typename St<PREC>::T* __restrict__ A,
                                                                               const float* __restrict__ s, int N) {
