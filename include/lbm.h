@@ -263,7 +263,10 @@ LBM_API int lbm_halo_exchange(const lbm_partitioning* part, int prec, void* cons
  * side streams that the partitioning creates on its first run (on the device
  * current then, which all later runs must use) and joins back into `stream`
  * before the next exchange, so work queued on `stream` before and after the
- * call is ordered with it as usual. */
+ * call is ordered with it as usual.  The side streams belong to the
+ * partitioning: runs of one partitioning must not overlap in time (issue them
+ * on one stream, or wait for the previous run); separate partitionings are
+ * independent. */
 LBM_API int lbm_partition_run_aa(const lbm_partitioning* part, int prec, const lbm_params* params,
                                  void* const* grids_host, void* const* grids_dev, const float* s, int start_parity,
                                  int steps, int ria, void* stream);

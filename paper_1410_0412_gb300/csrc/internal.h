@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -111,6 +112,7 @@ struct lbm_partitioning {
   // first partitioned run, on the device current at that time.
   std::vector<void*> side_streams, side_done;
   void* fork_event = nullptr;
+  std::mutex side_mu;  // guards their creation
   lbm_partitioning() = default;
   lbm_partitioning(const lbm_partitioning&) = delete;
   lbm_partitioning& operator=(const lbm_partitioning&) = delete;

@@ -228,6 +228,7 @@ namespace {
 constexpr int kSideStreams = 16;
 
 int ensure_side_streams(lbm_partitioning* S) {
+  std::lock_guard<std::mutex> lock(S->side_mu);
   if (S->fork_event) return LBM_OK;
   const int K = std::min(S->P, kSideStreams);
   cudaError_t e = cudaSuccess;
