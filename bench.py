@@ -37,17 +37,21 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 # FP64 pipe of GB300: 152 SMs x 2 DP lanes/clk x 2.07 GHz (measured 0.60 T DFMA/s burst)
 FP64_PEAK_GINSTR = 152 * 2 * 2.07e9 / 1e9
-# FP64-pipe instructions per node of the AA steps with body force (adds,
-# multiplies, FMAs and the reciprocal's Newton steps each take one FP64 slot):
-# ncu sm__inst_executed_pipe_fp64.sum = 51,760,560 warp instructions per launch
-# on the 10,896,954-node bed, i.e. 152 per node, the same for the even and odd
-# step.
-COLL_DP_INSTR = 152
+# FP64-pipe instructions per node of the AA steps with a uniform body force
+# (adds, multiplies, FMAs and the reciprocal's Newton steps each take one FP64
+# slot), counted by ncu (smsp__sass_thread_inst_executed_op_{dadd,dfma,dmul}
+# _pred_on.sum over the nodes), the same for the even and odd step: 152 in
+# general (64 DADD, 59 DFMA, 29 DMUL); 142 when omega_plus = 1, where the
+# kernels skip the ten products with (1 - l+)/2 = 0 and 1 - l+ = 0
+# (64 DADD, 49 DFMA, 29 DMUL).
+COLL_DP_INSTR_GENERAL = 152
+COLL_DP_INSTR_UNIT_OMEGA = 142
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
-# dominant kernel, the FP64 AA odd step with RIA, on the 10,896,954-node bed:
-# 1,823,011,072 + 1,595,249,152, from one ncu capture of this kernel version
-# (313.7 B/node against the model's 319.7).
-TRAFFIC_AA_ODD_RIA_F64 = 1823011072 + 1595249152
+# dominant kernel, the FP64 AA odd step with RIA (l+ = 1 collision), on the
+# 10,896,954-node bed: 1,823,091,408 + 1,594,950,800, the mean over 16
+# launches of one ncu capture of this kernel version (313.7 B/node against the
+# model's 319.7).
+TRAFFIC_AA_ODD_RIA_F64 = 1823091408 + 1594950800
 
 WORKLOAD = dict(name="packed_bed_256_rsa_r12", X=256, Y=256, Z=256, radius=12.0, seed=1, rejections=20000,
                 periodic=(1, 0, 0), g=(1e-6, 0.0, 0.0), omega_plus=1.0, magic=3.0 / 16.0)
@@ -697,13 +701,14 @@ def main():
                     "peak_kind": hbm_kind, "bytes_per_node": dom_bl,
                     "kernel_ms": {"even": even_ms, "odd": odd_ms}}
     if hp == "f64":
-        dp_rate = COLL_DP_INSTR * N / (dom_ms / 1e3) / 1e9
+        dp_instr = COLL_DP_INSTR_UNIT_OMEGA if w["omega_plus"] == 1.0 else COLL_DP_INSTR_GENERAL
+        dp_rate = dp_instr * N / (dom_ms / 1e3) / 1e9
         full_bed = (args.box is None and N == 10896954 and odd_dom)
         roofline = {"kernel": dom_name, "bound": "alu", "achieved": dp_rate, "peak": FP64_PEAK_GINSTR,
                     "unit": "G FP64-instr/s", "frac": dp_rate / FP64_PEAK_GINSTR,
                     "traffic": TRAFFIC_AA_ODD_RIA_F64 if full_bed else None,
                     "peak_kind": "FP64 pipe from unit counts: 152 SM x 2 DP lanes/clk x 2.07 GHz",
-                    "dp_instr_per_node": COLL_DP_INSTR}
+                    "dp_instr_per_node": dp_instr}
     else:
         roofline = roofline_hbm
 

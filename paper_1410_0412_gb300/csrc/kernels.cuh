@@ -228,7 +228,7 @@ template <class R, int X, int Y, int Z> __device__ __forceinline__ R cdot(R vx, 
   return acc;
 }
 
-template <class R, bool FORCE, int K>
+template <class R, bool FORCE, int K, bool LP1>
 __device__ __forceinline__ void coll_pair(R (&d)[kQ], const R sa, const R da, const R ux, const R uy, const R uz,
                                           const R K0, const R K1, const R K2, const R Fsx, const R Fsy,
                                           const R Fsz, const R Fox, const R Foy, const R Foz, const R qp,
@@ -247,14 +247,14 @@ __device__ __forceinline__ void coll_pair(R (&d)[kQ], const R sa, const R da, co
     o = K2 * cu;
   }
   const R e = fma(cu, t, K0);
-  const R Ep = fma(qp, sa, e);
+  const R Ep = LP1 ? e : fma(qp, sa, e);
   const R Op = fma(qm, da, o);
   d[a] = Ep + Op;
   d[b] = Ep - Op;
 }
 
 // Same pair update with the force projections c.F (already scaled) given.
-template <class R, int K>
+template <class R, int K, bool LP1>
 __device__ __forceinline__ void coll_pair_f(R (&d)[kQ], const R sa, const R da, const R ux, const R uy, const R uz,
                                             const R K0, const R K1, const R K2, const R cFs, const R cFo,
                                             const R qp, const R qm) {
@@ -264,14 +264,17 @@ __device__ __forceinline__ void coll_pair_f(R (&d)[kQ], const R sa, const R da, 
   const R t = fma(K1, cu, cFs);
   const R o = fma(K2, cu, cFo);
   const R e = fma(cu, t, K0);
-  const R Ep = fma(qp, sa, e);
+  const R Ep = LP1 ? e : fma(qp, sa, e);
   const R Op = fma(qm, da, o);
   d[a] = Ep + Op;
   d[b] = Ep - Op;
 }
 
-// s: Brinkman solid fraction of the node (DRAG only).
-template <class R, bool FORCE, bool DRAG>
+// s: Brinkman solid fraction of the node (DRAG only).  LP1: the caller knows
+// l+ = 1, so (1 - l+)/2 = 0 and 1 - l+ = 0: the even parts relax fully to
+// equilibrium, and the ten products with those zeros are skipped
+// (fma(0, x, e) = e, so the values are unchanged).
+template <class R, bool FORCE, bool DRAG, bool LP1 = false>
 __device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const R s) {
   using ::fma;
   R sa[10], da[10];
@@ -301,16 +304,16 @@ __device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const
     const R K0a = fma(c.k0a, base, -c.k0b * uF);
     const R K1a = c.k1 * rho, K2a = c.k2 * rho;
     const R K0b = half(K0a), K1b = half(K1a), K2b = half(K2a);
-    coll_pair_f<R, 1>(d, sa[1], da[1], ux, uy, uz, K0a, K1a, K2a, rho * c.gs[1], rho * c.go[1], c.qp, c.qm);
-    coll_pair_f<R, 2>(d, sa[2], da[2], ux, uy, uz, K0a, K1a, K2a, rho * c.gs[2], rho * c.go[2], c.qp, c.qm);
-    coll_pair_f<R, 3>(d, sa[3], da[3], ux, uy, uz, K0a, K1a, K2a, rho * c.gs[3], rho * c.go[3], c.qp, c.qm);
-    coll_pair_f<R, 4>(d, sa[4], da[4], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[4], rho * c.go[4], c.qp, c.qm);
-    coll_pair_f<R, 5>(d, sa[5], da[5], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[5], rho * c.go[5], c.qp, c.qm);
-    coll_pair_f<R, 6>(d, sa[6], da[6], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[6], rho * c.go[6], c.qp, c.qm);
-    coll_pair_f<R, 7>(d, sa[7], da[7], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[7], rho * c.go[7], c.qp, c.qm);
-    coll_pair_f<R, 8>(d, sa[8], da[8], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[8], rho * c.go[8], c.qp, c.qm);
-    coll_pair_f<R, 9>(d, sa[9], da[9], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[9], rho * c.go[9], c.qp, c.qm);
-    d[0] = fma(c.omlp, d[0], 6.0f * K0a);
+    coll_pair_f<R, 1, LP1>(d, sa[1], da[1], ux, uy, uz, K0a, K1a, K2a, rho * c.gs[1], rho * c.go[1], c.qp, c.qm);
+    coll_pair_f<R, 2, LP1>(d, sa[2], da[2], ux, uy, uz, K0a, K1a, K2a, rho * c.gs[2], rho * c.go[2], c.qp, c.qm);
+    coll_pair_f<R, 3, LP1>(d, sa[3], da[3], ux, uy, uz, K0a, K1a, K2a, rho * c.gs[3], rho * c.go[3], c.qp, c.qm);
+    coll_pair_f<R, 4, LP1>(d, sa[4], da[4], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[4], rho * c.go[4], c.qp, c.qm);
+    coll_pair_f<R, 5, LP1>(d, sa[5], da[5], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[5], rho * c.go[5], c.qp, c.qm);
+    coll_pair_f<R, 6, LP1>(d, sa[6], da[6], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[6], rho * c.go[6], c.qp, c.qm);
+    coll_pair_f<R, 7, LP1>(d, sa[7], da[7], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[7], rho * c.go[7], c.qp, c.qm);
+    coll_pair_f<R, 8, LP1>(d, sa[8], da[8], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[8], rho * c.go[8], c.qp, c.qm);
+    coll_pair_f<R, 9, LP1>(d, sa[9], da[9], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[9], rho * c.go[9], c.qp, c.qm);
+    d[0] = LP1 ? 6.0f * K0a : fma(c.omlp, d[0], 6.0f * K0a);
     return;
   }
   R Fx = R(0), Fy = R(0), Fz = R(0);
@@ -344,20 +347,20 @@ __device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const
   const R K0b = half(K0a), K1b = half(K1a), K2b = half(K2a);
   constexpr bool F = DRAG;
   // axis pairs (weight 1/18)
-  coll_pair<R, F, 1>(d, sa[1], da[1], ux, uy, uz, K0a, K1a, K2a, Fsx, Fsy, Fsz, Fox, Foy, Foz, c.qp, c.qm);
-  coll_pair<R, F, 2>(d, sa[2], da[2], ux, uy, uz, K0a, K1a, K2a, Fsx, Fsy, Fsz, Fox, Foy, Foz, c.qp, c.qm);
-  coll_pair<R, F, 3>(d, sa[3], da[3], ux, uy, uz, K0a, K1a, K2a, Fsx, Fsy, Fsz, Fox, Foy, Foz, c.qp, c.qm);
+  coll_pair<R, F, 1, LP1>(d, sa[1], da[1], ux, uy, uz, K0a, K1a, K2a, Fsx, Fsy, Fsz, Fox, Foy, Foz, c.qp, c.qm);
+  coll_pair<R, F, 2, LP1>(d, sa[2], da[2], ux, uy, uz, K0a, K1a, K2a, Fsx, Fsy, Fsz, Fox, Foy, Foz, c.qp, c.qm);
+  coll_pair<R, F, 3, LP1>(d, sa[3], da[3], ux, uy, uz, K0a, K1a, K2a, Fsx, Fsy, Fsz, Fox, Foy, Foz, c.qp, c.qm);
   // diagonal pairs (weight 1/36): every class constant halves
   const R hFsx = half(Fsx), hFsy = half(Fsy), hFsz = half(Fsz);
   const R hFox = half(Fox), hFoy = half(Foy), hFoz = half(Foz);
-  coll_pair<R, F, 4>(d, sa[4], da[4], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
-  coll_pair<R, F, 5>(d, sa[5], da[5], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
-  coll_pair<R, F, 6>(d, sa[6], da[6], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
-  coll_pair<R, F, 7>(d, sa[7], da[7], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
-  coll_pair<R, F, 8>(d, sa[8], da[8], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
-  coll_pair<R, F, 9>(d, sa[9], da[9], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
+  coll_pair<R, F, 4, LP1>(d, sa[4], da[4], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
+  coll_pair<R, F, 5, LP1>(d, sa[5], da[5], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
+  coll_pair<R, F, 6, LP1>(d, sa[6], da[6], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
+  coll_pair<R, F, 7, LP1>(d, sa[7], da[7], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
+  coll_pair<R, F, 8, LP1>(d, sa[8], da[8], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
+  coll_pair<R, F, 9, LP1>(d, sa[9], da[9], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
   // rest PDF: p0 = (1 - l+) d0 + w0 (l+ base - 3 a+ u.F), w0 = 6 w_axis
-  d[0] = fma(c.omlp, d[0], 6.0f * K0a);
+  d[0] = LP1 ? 6.0f * K0a : fma(c.omlp, d[0], 6.0f * K0a);
 }
 
 // ---- PDF gathers of the storage layouts ----------------------------------------------
@@ -390,7 +393,7 @@ __device__ __forceinline__ void gather(const typename St<PREC>::T* g, uint32_t n
 // ---- kernels -----------------------------------------------------------------------------
 // OS-NT step: pull (indirect) from src, collide, store locally into dst with
 // evict-first stores so the write stream does not push src out of L2.
-template <int PREC, bool RIA, bool FORCE, bool DRAG>
+template <int PREC, bool RIA, bool FORCE, bool DRAG, bool LP1 = false>
 __global__ void __launch_bounds__(kBlock, MinCtasOsnt<PREC, RIA>::value) k_osnt(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
                                                  const typename St<PREC>::T* __restrict__ src,
                                                  typename St<PREC>::T* __restrict__ dst, const float* __restrict__ s,
@@ -409,14 +412,14 @@ __global__ void __launch_bounds__(kBlock, MinCtasOsnt<PREC, RIA>::value) k_osnt(
   R d[kQ];
   gather<PREC, false>(src, t.npad, n, m, d, kp.inv_scale, c, t.pressure);
   const R sn = DRAG ? R(__ldg(s + n)) : R(0);
-  collide<R, FORCE, DRAG>(d, c, sn);
+  collide<R, FORCE, DRAG, LP1>(d, c, sn);
 #pragma unroll
   for (int i = 0; i < kQ; ++i) St<PREC>::st_stream(dst + at(i, t.npad, n), d[i], kp.scale);
 }
 
 // AA even step: direct read of the 19 local PDFs, collide, write to the
 // opposite local slots (no index loads at all).
-template <int PREC, bool FORCE, bool DRAG>
+template <int PREC, bool FORCE, bool DRAG, bool LP1 = false>
 __global__ void __launch_bounds__(kBlock, MinCtasEven<PREC>::value) k_aa_even(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
                                                     typename St<PREC>::T* __restrict__ A,
                                                     const float* __restrict__ s, int N) {
@@ -427,7 +430,7 @@ __global__ void __launch_bounds__(kBlock, MinCtasEven<PREC>::value) k_aa_even(De
 #pragma unroll
   for (int i = 0; i < kQ; ++i) d[i] = St<PREC>::ld(A + at(i, t.npad, n), kp.inv_scale);
   const R sn = DRAG ? R(__ldg(s + n)) : R(0);
-  collide<R, FORCE, DRAG>(d, c, sn);
+  collide<R, FORCE, DRAG, LP1>(d, c, sn);
 #pragma unroll
   for (int i = 0; i < kQ; ++i) St<PREC>::st(A + at(inv(i), t.npad, n), d[i], kp.scale);
 }
@@ -469,7 +472,7 @@ __global__ void __launch_bounds__(kBlock) k_aa_even_h2(DevTables t, KParams kp, 
 
 // AA odd step: read f_i from the neighbour's opposite slot A[inv i][m_i], collide,
 // write p_i to A[i][m_{inv i}] -- the same 19 slots, so in place and race-free.
-template <int PREC, bool RIA, bool FORCE, bool DRAG>
+template <int PREC, bool RIA, bool FORCE, bool DRAG, bool LP1 = false>
 __global__ void __launch_bounds__(kBlock, MinCtasOdd<PREC, RIA>::value) k_aa_odd(DevTables t, KParams kp,
                                                                               CollConst<typename St<PREC>::R> c,
                                                                               typename St<PREC>::T* __restrict__ A,
@@ -500,7 +503,7 @@ __global__ void __launch_bounds__(kBlock, MinCtasOdd<PREC, RIA>::value) k_aa_odd
     gather<PREC, true>(A, t.npad, n, m, d, kp.inv_scale, c, t.pressure);
   }
   const R sn = DRAG ? R(__ldg(s + n)) : R(0);
-  collide<R, FORCE, DRAG>(d, c, sn);
+  collide<R, FORCE, DRAG, LP1>(d, c, sn);
   St<PREC>::st(A + n, d[0], kp.scale);
   // p_i goes to the slot node m_{inv i} pulls it from next (or, through a
   // marker, to this node's own opposite slot); re-reads are issued first
@@ -560,7 +563,7 @@ __device__ __forceinline__ void et_locations(const DevTables& t, int n, int (&lo
   for (int k = 0; k < 6; ++k) loc[k + 1] = __ldg(t.et_nb + at(k, t.npad, n));
 }
 
-template <int PREC, bool ODD, bool FORCE, bool DRAG>
+template <int PREC, bool ODD, bool FORCE, bool DRAG, bool LP1 = false>
 __global__ void __launch_bounds__(kBlock, MinCtasEt<PREC>::value) k_et(DevTables t, KParams kp,
                                                                           CollConst<typename St<PREC>::R> c,
                                                                           typename St<PREC>::T* __restrict__ A,
@@ -587,7 +590,7 @@ __global__ void __launch_bounds__(kBlock, MinCtasEt<PREC>::value) k_et(DevTables
     s_loc[6][threadIdx.x] = int(mask);
   }
   const R sn = DRAG ? R(__ldg(s + n)) : R(0);
-  collide<R, FORCE, DRAG>(d, c, sn);
+  collide<R, FORCE, DRAG, LP1>(d, c, sn);
   St<PREC>::st(A + n, d[0], kp.scale);
   if (kStash) {
 #pragma unroll
@@ -871,6 +874,26 @@ inline unsigned grid_of(int64_t N) { return unsigned((N + dev::kBlock - 1) / dev
 
 inline bool has_force(const KParams& kp) { return kp.g[0] != 0.0 || kp.g[1] != 0.0 || kp.g[2] != 0.0; }
 
+// The l+ = 1 collision (see collide) is instantiated for the FP64-storage
+// paths only, which are bound by their FP64 arithmetic; the FP32 / FP16 steps
+// are bound by memory and take the general form.
+template <int PREC> constexpr bool kLp1Path = PREC == LBM_F64 || PREC == LBM_F64_DF;
+template <int PREC> inline bool use_lp1(const KParams& kp) { return kLp1Path<PREC> && kp.lp == 1.0; }
+
+// Launch KERNEL<PREC, ARGS..., LP1> with LP1 = lp1 where that instantiation exists.
+#define LBM_LAUNCH_LP1(KERNEL, TARGS, LAUNCH_ARGS)                             \
+  do {                                                                         \
+    if constexpr (kLp1Path<PREC>) {                                            \
+      if (lp1) {                                                               \
+        dev::KERNEL<PREC, TARGS, true><<<g, dev::kBlock, 0, st>>> LAUNCH_ARGS; \
+        break;                                                                 \
+      }                                                                        \
+    }                                                                          \
+    dev::KERNEL<PREC, TARGS, false><<<g, dev::kBlock, 0, st>>> LAUNCH_ARGS;    \
+  } while (0)
+#define LBM_TARGS3(A_, B_, C_) A_, B_, C_
+#define LBM_TARGS2(A_, B_) A_, B_
+
 template <int PREC>
 int launch_osnt_t(const lbm_lattice* L, const KParams& kp, const void* src, void* dst, const float* s, int ria,
                   void* stream) {
@@ -882,7 +905,8 @@ int launch_osnt_t(const lbm_lattice* L, const KParams& kp, const void* src, void
   const int N = int(L->N);
   const bool f = has_force(kp);
   const auto c = dev::make_coll<typename dev::St<PREC>::R>(kp);
-#define LBM_OSNT(R_, F_, D_) dev::k_osnt<PREC, R_, F_, D_><<<g, dev::kBlock, 0, st>>>(L->dev, kp, c, a, b, s, N)
+  const bool lp1 = use_lp1<PREC>(kp);
+#define LBM_OSNT(R_, F_, D_) LBM_LAUNCH_LP1(k_osnt, LBM_TARGS3(R_, F_, D_), (L->dev, kp, c, a, b, s, N))
   if (s) {
     if (ria) LBM_OSNT(true, true, true); else LBM_OSNT(false, true, true);
   } else if (f) {
@@ -903,6 +927,7 @@ int launch_aa_t(const lbm_lattice* L, const KParams& kp, void* pdf, int parity, 
   T* A = static_cast<T*>(pdf);
   const int N = int(L->N);
   const bool f = has_force(kp);
+  const bool lp1 = use_lp1<PREC>(kp);
   const auto c = dev::make_coll<typename dev::St<PREC>::R>(kp);
   if constexpr (PREC == LBM_F16S) {
     if (parity == 0) {
@@ -916,12 +941,12 @@ int launch_aa_t(const lbm_lattice* L, const KParams& kp, void* pdf, int parity, 
     }
   }
   if (parity == 0) {
-    if (s) dev::k_aa_even<PREC, true, true><<<g, dev::kBlock, 0, st>>>(L->dev, kp, c, A, s, N);
-    else if (f) dev::k_aa_even<PREC, true, false><<<g, dev::kBlock, 0, st>>>(L->dev, kp, c, A, s, N);
-    else dev::k_aa_even<PREC, false, false><<<g, dev::kBlock, 0, st>>>(L->dev, kp, c, A, s, N);
+    if (s) LBM_LAUNCH_LP1(k_aa_even, LBM_TARGS2(true, true), (L->dev, kp, c, A, s, N));
+    else if (f) LBM_LAUNCH_LP1(k_aa_even, LBM_TARGS2(true, false), (L->dev, kp, c, A, s, N));
+    else LBM_LAUNCH_LP1(k_aa_even, LBM_TARGS2(false, false), (L->dev, kp, c, A, s, N));
     return cuda_check("AA even step launch");
   }
-#define LBM_AAODD(R_, F_, D_) dev::k_aa_odd<PREC, R_, F_, D_><<<g, dev::kBlock, 0, st>>>(L->dev, kp, c, A, s, N)
+#define LBM_AAODD(R_, F_, D_) LBM_LAUNCH_LP1(k_aa_odd, LBM_TARGS3(R_, F_, D_), (L->dev, kp, c, A, s, N))
   if (s) {
     if (ria) LBM_AAODD(true, true, true); else LBM_AAODD(false, true, true);
   } else if (f) {
@@ -942,7 +967,8 @@ int launch_et_t(const lbm_lattice* L, const KParams& kp, void* pdf, int parity, 
   const int N = int(L->N);
   const bool f = has_force(kp);
   const auto c = dev::make_coll<typename dev::St<PREC>::R>(kp);
-#define LBM_ET(O_, F_, D_) dev::k_et<PREC, O_, F_, D_><<<g, dev::kBlock, 0, st>>>(L->dev, kp, c, A, s, N)
+  const bool lp1 = use_lp1<PREC>(kp);
+#define LBM_ET(O_, F_, D_) LBM_LAUNCH_LP1(k_et, LBM_TARGS3(O_, F_, D_), (L->dev, kp, c, A, s, N))
   if (s) {
     if (parity) LBM_ET(true, true, true); else LBM_ET(false, true, true);
   } else if (f) {
