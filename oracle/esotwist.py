@@ -156,3 +156,30 @@ def run(A, nb, adj, p: Params, steps: int, start_parity: int = 0, s=None):
     for k in range(steps):
         A = step(A, (start_parity + k) % 2, nb, adj, p, s)
     return A
+
+
+def run_tables(nb, mask):
+    """Run-length coding of the ET tables, the RIA idea of Sect. 4.1 applied to them.
+
+    Node n >= 1 continues the run of node n-1 when each of its six locations
+    is n-1's plus one and the link masks are equal (so both nodes' slots sit
+    at the same offsets).  Returns (run_start [R+1], run_nb [6, R], run_mask [R])
+    with the head's entries; decoding adds the offset within the run.
+    """
+    N = nb.shape[1]
+    if N == 0:
+        return np.zeros(1, np.int32), np.zeros((6, 0), np.int32), np.zeros(0, np.uint32)
+    a = nb.astype(np.int64)
+    cont = np.all(a[:, 1:] == a[:, :-1] + 1, axis=0) & (mask[1:] == mask[:-1])
+    heads = np.concatenate([[0], np.nonzero(~cont)[0] + 1])
+    run_start = np.concatenate([heads, [N]]).astype(np.int32)
+    return run_start, np.ascontiguousarray(nb[:, heads]), mask[heads].copy()
+
+
+def decode_runs(run_start, run_nb, run_mask):
+    """Expand the ET run table back into (nb [6, N], mask [N])."""
+    N = int(run_start[-1])
+    lengths = np.diff(run_start.astype(np.int64))
+    run_of = np.repeat(np.arange(len(lengths)), lengths)
+    off = np.arange(N) - run_start[:-1].astype(np.int64)[run_of]
+    return (run_nb[:, run_of].astype(np.int64) + off[None, :]).astype(np.int32), run_mask[run_of]

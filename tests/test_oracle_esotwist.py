@@ -175,3 +175,29 @@ def test_planted_mistake_is_caught(monkeypatch):
     A = et.run(et.from_canonical(F0, 0, nb, T.N + len(ph)), nb, T.adj, p, 2)
     G = lbm.run_osnt(lbm.from_canonical(F0, 0, T.adj, p), T.adj, p, 2)
     assert torch.max(torch.abs(et.canonical(A, 0, nb) - lbm.canonical(G, 0, T.adj, p))) > 1e-6
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_et_runs_decode_and_are_maximal(case):
+    solid = geometry.random_voxels(11, 9, 8, 0.25, 170 + case)
+    T = tables.Tables(solid, **CASES[case])
+    nb, mask, _ = et.tables(solid, T.node_xyz, T.adj, CASES[case]["periodic"])
+    rs, rnb, rmask = et.run_tables(nb, mask)
+    dnb, dmask = et.decode_runs(rs, rnb, rmask)
+    assert np.array_equal(dnb, nb) and np.array_equal(dmask, mask)
+    # maximal: no run head continues its predecessor (brute force per head)
+    for h in rs[1:-1]:
+        same = all(nb[k, h] == nb[k, h - 1] + 1 for k in range(6)) and mask[h] == mask[h - 1]
+        assert not same
+    assert rs[0] == 0 and rs[-1] == T.N and np.all(np.diff(rs) > 0)
+
+
+def test_et_runs_on_the_paper_channel_rows():
+    """A duct with walls on y and z, periodic x: every interior stretch of a row is one run,
+    as in the paper's channel example for RIA (Sect. 4.1)."""
+    solid = geometry.square_channel(40, 7, 6)          # X = 40: rows of 38 fluid nodes along x
+    T = tables.Tables(solid, periodic=(0, 0, 1))
+    nb, mask, _ = et.tables(solid, T.node_xyz, T.adj, (0, 0, 1))
+    rs, _, _ = et.run_tables(nb, mask)
+    # each row: the first node, the 36 interior ones, the last node
+    assert len(rs) - 1 == 3 * 5 * 6
