@@ -79,6 +79,8 @@ def loop_balance(variant: str, p: int, r: float) -> float:
         return dpdf + 76 * r
     if variant == "et":
         return dpdf + 28            # six int32 locations + one uint32 link mask, every step
+    if variant == "et_r":
+        return dpdf + 28 * r        # the same per run (r = ET runs per node), every step
     raise ValueError(variant)
 
 
@@ -213,17 +215,18 @@ def suite_channel(args, lbm, torch):
     lat = lbm.Lattice(solid, periodic=(0, 0, 1), enum="lex", B=1).upload(
         lbm.LBM_TABLES_ADJ | lbm.LBM_TABLES_RIA | lbm.LBM_TABLES_ET)
     r = lat.R / lat.N
+    r_et = (len(lat.et_runs()[0]) - 1) / lat.N
     hbm, kind = peaks()
-    out = {"suite": "channel", "fluid_nodes": lat.N, "runs": lat.R, "r": r, "r_times_98": r * 98,
+    out = {"suite": "channel", "fluid_nodes": lat.N, "runs": lat.R, "r": r, "r_times_98": r * 98, "r_et": r_et,
            "paper_table2_channel_B_l": [376, 306, 340, 305], "variants": {}}
     w = WORKLOAD
     for prec, pb in (("f64", 8), ("f64df", 8), ("f32", 4), ("f16s", 2)):
         params = lbm.Params(omega_plus=w["omega_plus"], magic=w["magic"], g=(0.0, 0.0, 1e-6),
                             shifted=prec in ("f32", "f16s"))
-        for form, ria in (("osnt", False), ("osnt", True), ("aa", False), ("aa", True), ("et", False)):
+        for form, ria in (("osnt", False), ("osnt", True), ("aa", False), ("aa", True), ("et", False), ("et", True)):
             name = f"{form}{'_r' if ria else ''}"
             sv, g = _time_variant(lbm, torch, lat, prec, params, form, ria, args.steps)
-            bl = loop_balance(name, pb, r)
+            bl = loop_balance(name, pb, r_et if name == "et_r" else r)
             out["variants"][f"{name}_{prec}"] = {"GFLUPs": g, "B_l": bl, "frac_hbm": g * bl / hbm,
                                                   "roof_GFLUPs": hbm / bl}
             del sv
@@ -772,6 +775,7 @@ def main():
 
     # ---- per-variant numbers ------------------------------------------------------------------------
     variants = {}
+    r_et = (len(lat.et_runs()[0]) - 1) / max(N, 1)
     if not args.no_variants:
         del solver
         torch.cuda.empty_cache()
@@ -779,7 +783,8 @@ def main():
         for prec, pb in (("f64", 8), ("f64df", 8), ("f32", 4), ("f16s", 2)):
             vp = lbm.Params(omega_plus=w["omega_plus"], magic=w["magic"], g=w["g"],
                             shifted=(prec in ("f32", "f16s")))
-            for form, ria in (("osnt", False), ("osnt", True), ("aa", False), ("aa", True), ("et", False)):
+            for form, ria in (("osnt", False), ("osnt", True), ("aa", False), ("aa", True), ("et", False),
+                              ("et", True)):
                 name = f"{form}{'_r' if ria else ''}"
                 sv = lbm.Solver(lat, prec, vp, form=form, ria=ria)
                 sv.init_equilibrium(1.0)
@@ -792,7 +797,7 @@ def main():
                 barrier()
                 vms = a.elapsed_time(b)
                 g = 2 * N * Kv / (vms / 1e3) / 1e9
-                bl = loop_balance(name, pb, r)
+                bl = loop_balance(name, pb, r_et if name == "et_r" else r)
                 variants[f"{name}_{prec}"] = {"GFLUPs": g, "B_l": bl, "GBs_model": g * bl,
                                               "frac_hbm": g * bl / hbm, "roof_GFLUPs_8TBs": 8000 / bl}
                 del sv
@@ -824,7 +829,7 @@ def main():
         "dtype": {"f64": "f64", "f64df": "f64 storage, f32-pair arithmetic", "f32": "f32",
                   "f16s": "f16 storage, f32 arithmetic"}[hp], "data": "synthetic",
         "config": {"workload": WORKLOAD["name"] if not args.box else f"packed_bed_{args.box}_rsa_r12",
-                   "box": [solid.shape[2], solid.shape[1], solid.shape[0]], "fluid_nodes": N, "runs": R,
+                   "box": [solid.shape[2], solid.shape[1], solid.shape[0]], "fluid_nodes": N, "runs": R, "et_runs_per_node": r_et,
                    "r": r, "porosity": geometry.porosity(solid), "enumeration": "lex B=1",
                    "step": "AA even + odd with RIA (2 lattice updates)", "parallelism": "replicas" if world > 1
                    else "single GPU", "l2": "inputs larger than L2 (state %.2f GB)" % (19 * lat.Npad * 8 / 1e9),

@@ -397,15 +397,26 @@ LBM_API int lbm_et_info(lbm_lattice* lat, int64_t* S, int64_t* Spad, int32_t* ph
  * directions with c_ix != 0 (1, 2, 7, ..., 14).  Either may be NULL. */
 LBM_API int lbm_export_et_tables(lbm_lattice* lat, int32_t* nb, uint32_t* mask);
 
+/* The run-length coding of the Esoteric Twist tables (the RIA idea of
+ * Sect. 4.1 applied to them): node n continues the run of n-1 when its six
+ * locations are n-1's plus one and the masks are equal.  R (host) = number of
+ * runs; run_start (int32 [R+1]) the first node of each run and N; run_nb
+ * (int32 [6][R]) and run_mask (uint32 [R]) the entries of each run's first
+ * node.  Any pointer may be NULL (ask for R first). */
+LBM_API int lbm_export_et_runs(lbm_lattice* lat, int64_t* R, int32_t* run_start, int32_t* run_nb,
+                               uint32_t* run_mask);
+
 /* One Esoteric Twist step of the grid `pdf` ([19][Spad], layout ET_EVEN before
  * a parity-0 step, ET_ODD before a parity-1 one), in place.  Needs the
- * LBM_TABLES_ET tables uploaded.  s: Brinkman field or NULL. */
+ * LBM_TABLES_ET tables uploaded.  s: Brinkman field or NULL.  ria = 0 reads
+ * the plain tables (28 B per node and step); ria = 1 their run table (ET-R:
+ * about 28 r B, r = runs per node). */
 LBM_API int lbm_step_et(const lbm_lattice* lat, int prec, const lbm_params* params, void* pdf, int parity,
-                        const float* s, void* stream);
+                        const float* s, int ria, void* stream);
 
 /* `steps` consecutive Esoteric Twist steps starting with parity start_parity. */
 LBM_API int lbm_run_et(const lbm_lattice* lat, int prec, const lbm_params* params, void* pdf, int start_parity,
-                       int steps, const float* s, void* stream);
+                       int steps, const float* s, int ria, void* stream);
 
 /* ---- macroscopic quantities and reductions ------------------------------------- */
 

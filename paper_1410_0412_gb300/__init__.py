@@ -247,6 +247,18 @@ class Lattice:
             self._et = (S.value, Sp.value, ph)
         return self._et
 
+    def et_runs(self):
+        """Run-length coding of the Esoteric Twist tables: run_start [R+1], run_nb [6, R], run_mask [R]."""
+        R = ctypes.c_int64()
+        lib = _lib.load()
+        check(lib.lbm_export_et_runs(self._h, ctypes.byref(R), None, None, None), "lbm_export_et_runs")
+        rs = np.empty(R.value + 1, np.int32)
+        rnb = np.empty((6, R.value), np.int32)
+        rm = np.empty(R.value, np.uint32)
+        q = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        check(lib.lbm_export_et_runs(self._h, None, q(rs), q(rnb), q(rm)), "lbm_export_et_runs")
+        return rs, rnb, rm
+
     def et_tables(self):
         """Esoteric Twist tables on the host: nb [6, N] int32 and mask [N] uint32."""
         nb = np.empty((6, self.N), np.int32)
@@ -425,18 +437,19 @@ def lbm_run_aa(lat, prec, params, pdf, start_parity, steps, s=None, ria=False, s
           "lbm_run_aa")
 
 
-def lbm_step_et(lat, prec, params, pdf, parity, s=None, stream=None):
+def lbm_step_et(lat, prec, params, pdf, parity, s=None, ria=False, stream=None):
     prec = _prec(prec)
     _check_grid(lat, prec, pdf, "pdf", LBM_LAYOUT_ET_EVEN)
     check(_lib.load().lbm_step_et(lat.handle, prec, ctypes.byref(params.c()), _ptr(pdf), int(parity),
-                                  _ptr(_check_s(lat, s)), _stream(stream)), "lbm_step_et")
+                                  _ptr(_check_s(lat, s)), 1 if ria else 0, _stream(stream)), "lbm_step_et")
 
 
-def lbm_run_et(lat, prec, params, pdf, start_parity, steps, s=None, stream=None):
+def lbm_run_et(lat, prec, params, pdf, start_parity, steps, s=None, ria=False, stream=None):
     prec = _prec(prec)
     _check_grid(lat, prec, pdf, "pdf", LBM_LAYOUT_ET_EVEN)
     check(_lib.load().lbm_run_et(lat.handle, prec, ctypes.byref(params.c()), _ptr(pdf), int(start_parity),
-                                 int(steps), _ptr(_check_s(lat, s)), _stream(stream)), "lbm_run_et")
+                                 int(steps), _ptr(_check_s(lat, s)), 1 if ria else 0, _stream(stream)),
+          "lbm_run_et")
 
 
 def lbm_macroscopic(lat, prec, params, pdf, layout, s=None, fields=True, sums=True, workspace=None, stream=None):
@@ -689,7 +702,7 @@ class Solver:
                 self.grids.reverse()
                 self.t += 1
         elif self.form == "et":
-            lbm_run_et(self.lat, self.prec, self.params, self.grids[0], self.t % 2, n, self.s, stream)
+            lbm_run_et(self.lat, self.prec, self.params, self.grids[0], self.t % 2, n, self.s, self.ria, stream)
             self.t += n
         else:
             lbm_run_aa(self.lat, self.prec, self.params, self.grids[0], self.t % 2, n, self.s, self.ria, stream)
@@ -725,7 +738,7 @@ class Solver:
                     lbm_step_osnt(self.lat, self.prec, self.params, self.grids[0], self.grids[1], self.s, self.ria, st)
                     lbm_step_osnt(self.lat, self.prec, self.params, self.grids[1], self.grids[0], self.s, self.ria, st)
                 elif self.form == "et":
-                    lbm_run_et(self.lat, self.prec, self.params, self.grids[0], 0, 2, self.s, st)
+                    lbm_run_et(self.lat, self.prec, self.params, self.grids[0], 0, 2, self.s, self.ria, st)
                 else:
                     lbm_step_aa(self.lat, self.prec, self.params, self.grids[0], 0, self.s, self.ria, st)
                     lbm_step_aa(self.lat, self.prec, self.params, self.grids[0], 1, self.s, self.ria, st)

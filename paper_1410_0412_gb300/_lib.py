@@ -101,8 +101,9 @@ SIGNATURES = {
     "lbm_run_aa": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _I, _P, _I, _P],
     "lbm_et_info": [_P, _PI64, _PI64, _P],
     "lbm_export_et_tables": [_P, _P, _P],
-    "lbm_step_et": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _P, _P],
-    "lbm_run_et": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _I, _P, _P],
+    "lbm_step_et": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _P, _I, _P],
+    "lbm_run_et": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _I, _P, _I, _P],
+    "lbm_export_et_runs": [_P, _PI64, _P, _P, _P],
     "lbm_reduce_workspace_bytes": [_P, _PSZ],
     "lbm_macroscopic": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _P, _P, _P, _P, _P, _SZ, _P],
     "lbm_bandwidth_kernel": [_I, _P, _P, _I64, _I, _P],

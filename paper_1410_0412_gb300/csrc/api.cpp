@@ -57,7 +57,8 @@ namespace {
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct TableLayout {
-  size_t adj = 0, run_adj = 0, head_bits = 0, warp_run0 = 0, warp_head0 = 0, et_nb = 0, et_mask = 0, total = 0;
+  size_t adj = 0, run_adj = 0, head_bits = 0, warp_run0 = 0, warp_head0 = 0, et_nb = 0, et_mask = 0;
+  size_t et_run_nb = 0, et_run_mask = 0, et_head_bits = 0, et_warp_run0 = 0, et_warp_head0 = 0, total = 0;
 };
 
 TableLayout table_layout(const lbm_lattice* L, int which) {
@@ -82,6 +83,17 @@ TableLayout table_layout(const lbm_lattice* L, int which) {
     off = align256(off + size_t(6) * L->Npad * 4);
     t.et_mask = off;
     off = align256(off + size_t(L->Npad) * 4);
+    t.et_run_nb = off;
+    off = align256(off + size_t(6) * L->et_Rpad * 4);
+    t.et_run_mask = off;
+    off = align256(off + size_t(L->et_Rpad) * 4);
+    const size_t nw = size_t(std::max<int64_t>(int64_t(L->et_head_bits.size()), 1));
+    t.et_head_bits = off;
+    off = align256(off + nw * 4);
+    t.et_warp_run0 = off;
+    off = align256(off + nw * 4);
+    t.et_warp_head0 = off;
+    off = align256(off + nw * 4);
   }
   t.total = off;
   return t;
@@ -357,10 +369,31 @@ int lbm_lattice_upload(lbm_lattice* L, int which, void* dev, size_t bytes, void*
     e = cudaMemcpyAsync(base + t.et_nb, L->et_nb.data(), L->et_nb.size() * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(base + t.et_mask, L->et_mask.data(), L->et_mask.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(base + t.et_run_nb, L->et_run_nb.data(), L->et_run_nb.size() * 4, cudaMemcpyHostToDevice,
+                          st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(base + t.et_run_mask, L->et_run_mask.data(), L->et_run_mask.size() * 4,
+                          cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !L->et_head_bits.empty())
+      e = cudaMemcpyAsync(base + t.et_head_bits, L->et_head_bits.data(), L->et_head_bits.size() * 4,
+                          cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !L->et_warp_run0.empty())
+      e = cudaMemcpyAsync(base + t.et_warp_run0, L->et_warp_run0.data(), L->et_warp_run0.size() * 4,
+                          cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !L->et_warp_head0.empty())
+      e = cudaMemcpyAsync(base + t.et_warp_head0, L->et_warp_head0.data(), L->et_warp_head0.size() * 4,
+                          cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return set_error(LBM_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
     L->dev.et_nb = reinterpret_cast<const int32_t*>(base + t.et_nb);
     L->dev.et_mask = reinterpret_cast<const uint32_t*>(base + t.et_mask);
     L->dev.spad = uint32_t(L->et_Spad);
+    L->dev.et_run_nb = reinterpret_cast<const int32_t*>(base + t.et_run_nb);
+    L->dev.et_run_mask = reinterpret_cast<const uint32_t*>(base + t.et_run_mask);
+    L->dev.et_head_bits = reinterpret_cast<const uint32_t*>(base + t.et_head_bits);
+    L->dev.et_warp_run0 = reinterpret_cast<const int32_t*>(base + t.et_warp_run0);
+    L->dev.et_warp_head0 = reinterpret_cast<const int32_t*>(base + t.et_warp_head0);
+    L->dev.et_rpad = uint32_t(L->et_Rpad);
   }
   L->dev.Npad = L->Npad;
   L->dev.Rpad = L->Rpad;
@@ -482,7 +515,7 @@ int lbm_export_et_tables(lbm_lattice* L, int32_t* nb, uint32_t* mask) {
 }
 
 int lbm_run_et(const lbm_lattice* L, int prec, const lbm_params* params, void* pdf, int start_parity, int steps,
-               const float* s, void* stream) {
+               const float* s, int ria, void* stream) {
   if (int rc = check_lat(L)) return rc;
   KParams kp;
   if (int rc = make_kparams(params, prec, &kp)) return rc;
@@ -492,13 +525,25 @@ int lbm_run_et(const lbm_lattice* L, int prec, const lbm_params* params, void* p
   if (L->N == 0 || steps == 0) return LBM_OK;
   if (!(L->uploaded & LBM_TABLES_ET)) return set_error(LBM_ERR_ARG, "Esoteric Twist tables not uploaded to the device");
   for (int t = 0; t < steps; ++t)
-    if (int rc = LBM_DISPATCH_STEP(prec, launch_et_t, L, kp, pdf, (start_parity + t) & 1, s, stream)) return rc;
+    if (int rc = LBM_DISPATCH_STEP(prec, launch_et_t, L, kp, pdf, (start_parity + t) & 1, s, ria ? 1 : 0, stream))
+      return rc;
   return LBM_OK;
 }
 
 int lbm_step_et(const lbm_lattice* L, int prec, const lbm_params* params, void* pdf, int parity, const float* s,
-                void* stream) {
-  return lbm_run_et(L, prec, params, pdf, parity, 1, s, stream);
+                int ria, void* stream) {
+  return lbm_run_et(L, prec, params, pdf, parity, 1, s, ria, stream);
+}
+
+int lbm_export_et_runs(lbm_lattice* L, int64_t* R, int32_t* run_start, int32_t* run_nb, uint32_t* run_mask) {
+  if (int rc = check_lat(L)) return rc;
+  if (int rc = derive_et(L)) return rc;
+  if (R) *R = L->et_R;
+  if (run_start) std::memcpy(run_start, L->et_run_start.data(), size_t(L->et_R + 1) * 4);
+  if (run_nb)
+    for (int k = 0; k < 6; ++k) std::memcpy(run_nb + k * L->et_R, &L->et_run_nb[k * L->et_Rpad], size_t(L->et_R) * 4);
+  if (run_mask) std::memcpy(run_mask, L->et_run_mask.data(), size_t(L->et_R) * 4);
+  return LBM_OK;
 }
 
 int lbm_reduce_workspace_bytes(const lbm_lattice* L, size_t* bytes) {

@@ -42,6 +42,13 @@ struct DevTables {
   const int32_t* et_nb = nullptr;       // [6][Npad]   Esoteric Twist neighbour locations
   const uint32_t* et_mask = nullptr;    // [Npad]      Esoteric Twist link kinds
   uint32_t spad = 0;                    // Esoteric Twist grid stride (nodes + phantoms, padded)
+  // Esoteric Twist run table (the RIA coding of et_nb / et_mask), same warp-level index
+  const int32_t* et_run_nb = nullptr;   // [6][et_rpad] locations of each run's first node
+  const uint32_t* et_run_mask = nullptr;// [et_rpad]    its link mask
+  const uint32_t* et_head_bits = nullptr;
+  const int32_t* et_warp_run0 = nullptr;
+  const int32_t* et_warp_head0 = nullptr;
+  uint32_t et_rpad = 0;
 };
 
 // Ghost slots of a partition: local node index space [0, N_p) followed by the
@@ -89,6 +96,13 @@ struct lbm_lattice {
   std::vector<int32_t> et_nb;      // [6][Npad] storage index of n + (+x, +y, +z, +x+y, +x+z, +y+z)
   std::vector<uint32_t> et_mask;   // [Npad] bit i-1: pull i meets a marker; bits 18..27: pressure faces
   std::vector<int32_t> et_phantom; // [S-N][3] coordinates of the phantom locations
+  int64_t et_R = 0, et_Rpad = 0;   // runs of the ET tables (a run continues while all six locations advance by one
+  std::vector<int32_t> et_run_start;   // [et_R+1]             and the mask is unchanged)
+  std::vector<int32_t> et_run_nb;      // [6][et_Rpad]
+  std::vector<uint32_t> et_run_mask;   // [et_Rpad]
+  std::vector<uint32_t> et_head_bits;  // [nwarps]
+  std::vector<int32_t> et_warp_run0;   // [nwarps]
+  std::vector<int32_t> et_warp_head0;  // [nwarps]
   int uploaded = 0;                // LBM_TABLES_* bits present on the device
   int partition_local = 0;         // a partition's local lattice: entries >= N are ghost slots
   lbm::DevTables dev;
@@ -157,7 +171,8 @@ template <int PREC>
 int launch_aa_t(const lbm_lattice* L, const KParams& kp, void* pdf, int parity, const float* s, int ria,
                 void* stream);
 template <int PREC>
-int launch_et_t(const lbm_lattice* L, const KParams& kp, void* pdf, int parity, const float* s, void* stream);
+int launch_et_t(const lbm_lattice* L, const KParams& kp, void* pdf, int parity, const float* s, int ria,
+                void* stream);
 template <int PREC>
 int launch_init_eq_t(const lbm_lattice* L, const KParams& kp, void* pdf, int layout, double rho0, const double* u0,
                      void* stream);

@@ -123,16 +123,21 @@ struct RiaCursor {
   int off;   // node - first node of the run
 };
 
-__device__ __forceinline__ RiaCursor ria_locate(const DevTables& t, int n) {
+__device__ __forceinline__ RiaCursor ria_locate_in(const uint32_t* head_bits, const int32_t* warp_run0,
+                                                   const int32_t* warp_head0, int n) {
   const int w = n >> 5;
   const unsigned lane = unsigned(n) & 31u;
-  const unsigned bits = __ldg(t.head_bits + w);
+  const unsigned bits = __ldg(head_bits + w);
   const unsigned le = bits & (0xffffffffu >> (31u - lane));  // heads at lanes 0..lane
   RiaCursor c;
-  c.r = __ldg(t.warp_run0 + w) + __popc(le) - int(bits & 1u);
-  const int head = le ? (w << 5) + (31 - __clz(le)) : __ldg(t.warp_head0 + w);
+  c.r = __ldg(warp_run0 + w) + __popc(le) - int(bits & 1u);
+  const int head = le ? (w << 5) + (31 - __clz(le)) : __ldg(warp_head0 + w);
   c.off = n - head;
   return c;
+}
+
+__device__ __forceinline__ RiaCursor ria_locate(const DevTables& t, int n) {
+  return ria_locate_in(t.head_bits, t.warp_run0, t.warp_head0, n);
 }
 
 // One table entry read again after the collision (the volatile load is never
@@ -563,7 +568,24 @@ __device__ __forceinline__ void et_locations(const DevTables& t, int n, int (&lo
   for (int k = 0; k < 6; ++k) loc[k + 1] = __ldg(t.et_nb + at(k, t.npad, n));
 }
 
-template <int PREC, bool ODD, bool FORCE, bool DRAG, bool LP1 = false>
+// The node's locations and link mask, from the plain tables (28 B per node) or
+// from their run-length coding (RIA, Sect. 4.1: runs of nodes whose six
+// locations advance by one and whose masks agree; found with the same
+// warp-level run index as the adjacency runs).
+template <bool RIA>
+__device__ __forceinline__ unsigned et_locate(const DevTables& t, int n, int (&loc)[7]) {
+  if (!RIA) {
+    et_locations(t, n, loc);
+    return __ldg(t.et_mask + n);
+  }
+  const RiaCursor c = ria_locate_in(t.et_head_bits, t.et_warp_run0, t.et_warp_head0, n);
+  loc[0] = n;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) loc[k + 1] = __ldg(t.et_run_nb + at(k, t.et_rpad, c.r)) + c.off;
+  return __ldg(t.et_run_mask + c.r);
+}
+
+template <int PREC, bool RIA, bool ODD, bool FORCE, bool DRAG, bool LP1 = false>
 __global__ void __launch_bounds__(kBlock, MinCtasEt<PREC>::value) k_et(DevTables t, KParams kp,
                                                                           CollConst<typename St<PREC>::R> c,
                                                                           typename St<PREC>::T* __restrict__ A,
@@ -577,13 +599,12 @@ __global__ void __launch_bounds__(kBlock, MinCtasEt<PREC>::value) k_et(DevTables
   const int n = blockIdx.x * kBlock + threadIdx.x;
   if (n >= N) return;
   int loc[7];
-  et_locations(t, n, loc);
+  unsigned mask = et_locate<RIA>(t, n, loc);
   R d[kQ];
   d[0] = St<PREC>::ld(A + n, kp.inv_scale);
 #pragma unroll
   for (int i = 1; i < kQ; ++i)
     d[i] = St<PREC>::ld(A + at(ODD ? inv(i) : i, t.spad, loc[et_row(inv(i)) + 1]), kp.inv_scale);
-  unsigned mask = __ldg(t.et_mask + n);
   if (kStash) {
 #pragma unroll
     for (int k = 1; k < 7; ++k) s_loc[k - 1][threadIdx.x] = loc[k];
@@ -892,6 +913,7 @@ template <int PREC> inline bool use_lp1(const KParams& kp) { return kLp1Path<PRE
     dev::KERNEL<PREC, TARGS, false><<<g, dev::kBlock, 0, st>>> LAUNCH_ARGS;    \
   } while (0)
 #define LBM_TARGS3(A_, B_, C_) A_, B_, C_
+#define LBM_TARGS4(A_, B_, C_, D_) A_, B_, C_, D_
 #define LBM_TARGS2(A_, B_) A_, B_
 
 template <int PREC>
@@ -959,7 +981,8 @@ int launch_aa_t(const lbm_lattice* L, const KParams& kp, void* pdf, int parity, 
 }
 
 template <int PREC>
-int launch_et_t(const lbm_lattice* L, const KParams& kp, void* pdf, int parity, const float* s, void* stream) {
+int launch_et_t(const lbm_lattice* L, const KParams& kp, void* pdf, int parity, const float* s, int ria,
+                void* stream) {
   using T = typename dev::St<PREC>::T;
   auto st = static_cast<cudaStream_t>(stream);
   const unsigned g = grid_of(L->N);
@@ -968,14 +991,22 @@ int launch_et_t(const lbm_lattice* L, const KParams& kp, void* pdf, int parity, 
   const bool f = has_force(kp);
   const auto c = dev::make_coll<typename dev::St<PREC>::R>(kp);
   const bool lp1 = use_lp1<PREC>(kp);
-#define LBM_ET(O_, F_, D_) LBM_LAUNCH_LP1(k_et, LBM_TARGS3(O_, F_, D_), (L->dev, kp, c, A, s, N))
+#define LBM_ET(R_, O_, F_, D_) LBM_LAUNCH_LP1(k_et, LBM_TARGS4(R_, O_, F_, D_), (L->dev, kp, c, A, s, N))
+#define LBM_ET_R(O_, F_, D_) \
+  do {                       \
+    if (ria)                 \
+      LBM_ET(true, O_, F_, D_); \
+    else                     \
+      LBM_ET(false, O_, F_, D_); \
+  } while (0)
   if (s) {
-    if (parity) LBM_ET(true, true, true); else LBM_ET(false, true, true);
+    if (parity) LBM_ET_R(true, true, true); else LBM_ET_R(false, true, true);
   } else if (f) {
-    if (parity) LBM_ET(true, true, false); else LBM_ET(false, true, false);
+    if (parity) LBM_ET_R(true, true, false); else LBM_ET_R(false, true, false);
   } else {
-    if (parity) LBM_ET(true, false, false); else LBM_ET(false, false, false);
+    if (parity) LBM_ET_R(true, false, false); else LBM_ET_R(false, false, false);
   }
+#undef LBM_ET_R
 #undef LBM_ET
   return cuda_check("Esoteric Twist step launch");
 }
@@ -1062,12 +1093,12 @@ int launch_macroscopic_t(const lbm_lattice* L, const KParams& kp, const void* pd
 #define LBM_INSTANTIATE_STEP_LAUNCHERS(P)                                                                          \
   template int launch_osnt_t<P>(const lbm_lattice*, const KParams&, const void*, void*, const float*, int, void*); \
   template int launch_aa_t<P>(const lbm_lattice*, const KParams&, void*, int, const float*, int, void*);           \
-  template int launch_et_t<P>(const lbm_lattice*, const KParams&, void*, int, const float*, void*);
+  template int launch_et_t<P>(const lbm_lattice*, const KParams&, void*, int, const float*, int, void*);
 
 #define LBM_INSTANTIATE_LAUNCHERS(P)                                                                               \
   template int launch_osnt_t<P>(const lbm_lattice*, const KParams&, const void*, void*, const float*, int, void*); \
   template int launch_aa_t<P>(const lbm_lattice*, const KParams&, void*, int, const float*, int, void*);           \
-  template int launch_et_t<P>(const lbm_lattice*, const KParams&, void*, int, const float*, void*);                \
+  template int launch_et_t<P>(const lbm_lattice*, const KParams&, void*, int, const float*, int, void*);                \
   template int launch_init_eq_t<P>(const lbm_lattice*, const KParams&, void*, int, double, const double*, void*);  \
   template int launch_load_canonical_t<P>(const lbm_lattice*, const KParams&, const double*, void*, int, void*);   \
   template int launch_canonical_t<P>(const lbm_lattice*, const KParams&, const void*, int, double*, void*);        \

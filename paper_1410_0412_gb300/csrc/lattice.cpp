@@ -457,9 +457,45 @@ int derive_et(lbm_lattice* L) {
       if (m < 0) mask[n] |= 1u << (i - 1);
       if (kCX[i] != 0 && m <= LBM_MARK_INLET) mask[n] |= 1u << (i <= 2 ? 17 + i : 13 + i);
     }
+  // run-length coding (Sect. 4.1's idea on these tables): node n continues
+  // n-1's run when all six locations advance by one and the mask is equal
+  auto continues_et = [&](int64_t n) {
+    for (int k = 0; k < 6; ++k)
+      if (int64_t(nb[k * Np + n]) != int64_t(nb[k * Np + n - 1]) + 1) return false;
+    return mask[n] == mask[n - 1];
+  };
+  std::vector<int32_t> rs;
+  for (int64_t n = 0; n < N; ++n)
+    if (n == 0 || !continues_et(n)) rs.push_back(int32_t(n));
+  const int64_t R = int64_t(rs.size());
+  rs.push_back(int32_t(N));
+  const int64_t Rpad = round_up(std::max<int64_t>(R, 1), kPad);
+  std::vector<int32_t> rnb(size_t(6) * Rpad, -1);
+  std::vector<uint32_t> rmask(Rpad, 0u);
+  for (int64_t r = 0; r < R; ++r) {
+    for (int k = 0; k < 6; ++k) rnb[k * Rpad + r] = nb[k * Np + rs[r]];
+    rmask[r] = mask[rs[r]];
+  }
+  const int64_t nw = (N + kWarpNodes - 1) / kWarpNodes;
+  std::vector<uint32_t> hb(nw, 0u);
+  std::vector<int32_t> wr(nw, 0), wh(nw, 0);
+  for (int64_t r = 0; r < R; ++r) hb[rs[r] / kWarpNodes] |= 1u << (rs[r] % kWarpNodes);
+  for (int64_t w = 0, r = 0; w < nw; ++w) {
+    while (r + 1 < R && rs[r + 1] <= w * kWarpNodes) ++r;
+    wr[w] = int32_t(r);
+    wh[w] = rs[r];
+  }
   L->et_nb.swap(nb);
   L->et_mask.swap(mask);
   L->et_phantom.swap(ph);
+  L->et_run_start.swap(rs);
+  L->et_run_nb.swap(rnb);
+  L->et_run_mask.swap(rmask);
+  L->et_head_bits.swap(hb);
+  L->et_warp_run0.swap(wr);
+  L->et_warp_head0.swap(wh);
+  L->et_R = R;
+  L->et_Rpad = Rpad;
   L->et_S = N + M;
   L->et_Spad = round_up(std::max<int64_t>(N + M, 1), kPad);
   L->et_ready = 1;

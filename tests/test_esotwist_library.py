@@ -66,9 +66,9 @@ def test_et_refused_where_undefined():
     # stepping without the ET tables on the device is refused before any launch
     lib = lbm._lib.load()
     prm = lbm.Params().c()
-    assert lib.lbm_step_et(lat.handle, 0, ctypes.byref(prm), ctypes.c_void_p(256), 0, None, None) == \
+    assert lib.lbm_step_et(lat.handle, 0, ctypes.byref(prm), ctypes.c_void_p(256), 0, None, 0, None) == \
         lbm._lib.LBM_ERR_ARG
-    assert lib.lbm_step_et(lat.handle, 0, ctypes.byref(prm), ctypes.c_void_p(256), 2, None, None) == \
+    assert lib.lbm_step_et(lat.handle, 0, ctypes.byref(prm), ctypes.c_void_p(256), 2, None, 1, None) == \
         lbm._lib.LBM_ERR_ARG
 
 
@@ -76,3 +76,23 @@ def test_et_empty_lattice():
     lat = lbm.Lattice(np.ones((3, 3, 3), np.uint8))
     S, Spad, ph = lat.et_info()
     assert S == 0 and len(ph) == 0
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+@pytest.mark.parametrize("enum", [("lex", 1), ("hilbert", 1)])
+def test_et_runs_match_oracle(case, enum):
+    solid = geometry.random_voxels(13, 11, 9, 0.25, 180 + case)
+    lat = lbm.Lattice(solid, enum=enum[0], B=enum[1], **CASES[case])
+    T = tables.Tables(solid, enum=enum[0], B=enum[1], **CASES[case])
+    nb, mask, _ = et.tables(solid, T.node_xyz, T.adj, CASES[case]["periodic"])
+    rs, rnb, rmask = et.run_tables(nb, mask)
+    lrs, lrnb, lrmask = lat.et_runs()
+    assert np.array_equal(lrs, rs) and np.array_equal(lrnb, rnb) and np.array_equal(lrmask, rmask)
+
+
+def test_et_runs_paper_channel():
+    """The paper's channel cross-section rows: three ET runs per 98-node row, as for RIA."""
+    solid = geometry.square_channel(100, 100, 8)
+    lat = lbm.Lattice(solid, periodic=(0, 0, 1))
+    rs, _, _ = lat.et_runs()
+    assert len(rs) - 1 == 3 * 98 * 8

@@ -1,4 +1,5 @@
-"""GPU parity of the Esoteric Twist step (the single-grid form Sect. 1 and Sect. 4 name).
+"""GPU parity of the Esoteric Twist step (the single-grid form Sect. 1 and Sect. 4 name),
+with its plain tables and with their run-length coding (ET-R).
 
 The ET kernel runs through the C ABI on seeded synthetic lattices under every
 boundary kind and storage precision and is compared with the FP64 oracle's
@@ -58,7 +59,8 @@ def _relerr(a, b):
 
 @pytest.mark.parametrize("case", range(len(CASES)))
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f64df", 1e-12), ("f32", 2e-6), ("f16s", 5e-4)])
-def test_et_parity_with_oracle(case, prec, tol):
+@pytest.mark.parametrize("ria", [False, True])
+def test_et_parity_with_oracle(case, prec, tol, ria):
     kind, periodic, xp, enum, B, drag = CASES[case]
     solid = _geometry(kind, 140 + case)
     lat = lbm.Lattice(solid, periodic=periodic, x_pressure=xp, enum=enum, B=B).upload(ALL)
@@ -66,7 +68,7 @@ def test_et_parity_with_oracle(case, prec, tol):
     op, lp = _params(xp, prec in ("f32", "f16s"))
     s = torch.as_tensor(geometry.uniform_field(lat.N, 9 + case), dtype=torch.float64) * 0.5 if drag else None
     F0 = _state(lat.N, case)
-    sv = lbm.Solver(lat, prec, lp, form="et", s=None if s is None else s.to(torch.float32).cuda())
+    sv = lbm.Solver(lat, prec, lp, form="et", ria=ria, s=None if s is None else s.to(torch.float32).cuda())
     sv.load(F0.cuda())
     G = olbm.from_canonical(F0, 0, T["adj"], op)
     sref = None if s is None else s.to(torch.float32).to(torch.float64)
@@ -81,7 +83,8 @@ def test_et_parity_with_oracle(case, prec, tol):
 
 @pytest.mark.parametrize("case", range(len(CASES)))
 @pytest.mark.parametrize("prec", ["f64", "f32", "f16s"])
-def test_et_equals_aa_bitwise(case, prec):
+@pytest.mark.parametrize("ria", [False, True])
+def test_et_equals_aa_bitwise(case, prec, ria):
     kind, periodic, xp, enum, B, drag = CASES[case]
     solid = _geometry(kind, 150 + case)
     lat = lbm.Lattice(solid, periodic=periodic, x_pressure=xp, enum=enum, B=B).upload(ALL)
@@ -89,7 +92,7 @@ def test_et_equals_aa_bitwise(case, prec):
     s = (torch.as_tensor(geometry.uniform_field(lat.N, 2), dtype=torch.float32) * 0.5).cuda() if drag else None
     F0 = _state(lat.N, 7).cuda()
     a = lbm.Solver(lat, prec, lp, form="aa", ria=True, s=s)
-    e = lbm.Solver(lat, prec, lp, form="et", s=s)
+    e = lbm.Solver(lat, prec, lp, form="et", ria=ria, s=s)
     a.load(F0)
     e.load(F0)
     for n in (1, 1, 3, 5):
@@ -113,7 +116,7 @@ def test_et_matches_oracle_grid():
     nb, mask, ph = oet.tables(solid, T.node_xyz, T.adj, periodic)
     S, Spad, _ = lat.et_info()
     F0 = _state(lat.N, 3)
-    sv = lbm.Solver(lat, "f64", lp, form="et")
+    sv = lbm.Solver(lat, "f64", lp, form="et", ria=False)
     sv.load(F0.cuda())
     A = oet.from_canonical(F0, 0, nb, S)
     for k in range(5):
@@ -136,7 +139,7 @@ def test_et_macroscopic_and_init():
     solid = geometry.sphere_box_64x32x32(0)
     lat = lbm.Lattice(solid, periodic=(1, 0, 0)).upload(ALL)
     lp = lbm.Params(omega_plus=1.0, magic=3 / 16, g=(1e-5, 0, 0))
-    e = lbm.Solver(lat, "f64", lp, form="et")
+    e = lbm.Solver(lat, "f64", lp, form="et", ria=True)
     a = lbm.Solver(lat, "f64", lp, form="aa", ria=True)
     for sv in (e, a):
         sv.init_equilibrium(1.0, (0.01, 0.0, 0.0))
@@ -153,8 +156,8 @@ def test_et_graph_replay():
     solid = geometry.sphere_box_64x32x32(0)
     lat = lbm.Lattice(solid, periodic=(1, 0, 0)).upload(ALL)
     lp = lbm.Params(omega_plus=1.0, magic=3 / 16, g=(1e-5, 0, 0), shifted=True)
-    a = lbm.Solver(lat, "f32", lp, form="et")
-    b = lbm.Solver(lat, "f32", lp, form="et")
+    a = lbm.Solver(lat, "f32", lp, form="et", ria=True)
+    b = lbm.Solver(lat, "f32", lp, form="et", ria=True)
     a.init_equilibrium(1.0)
     b.init_equilibrium(1.0)
     a.step(40)
@@ -166,9 +169,10 @@ def test_et_graph_replay():
 
 def test_et_empty_and_errors():
     empty = lbm.Lattice(np.ones((3, 3, 3), np.uint8)).upload(ALL)
-    sv = lbm.Solver(empty, "f64", lbm.Params(), form="et")
-    sv.init_equilibrium(1.0)
-    sv.step(3)
+    for ria in (False, True):
+        sv = lbm.Solver(empty, "f64", lbm.Params(), form="et", ria=ria)
+        sv.init_equilibrium(1.0)
+        sv.step(3)
     lat = lbm.Lattice(geometry.random_voxels(9, 8, 7, 0.25, 5), periodic=(1, 0, 0)).upload()
     with pytest.raises(ValueError):
         lbm.Solver(lat, "f64", lbm.Params(), form="et")
