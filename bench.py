@@ -751,13 +751,13 @@ def main():
         torch.cuda.empty_cache()
 
     # ---- end to end through host buffers: H2D state, one pair, D2H state -------------------------------
-    # Two independent states are in flight, each on its own stream: a step of a
-    # state copies it in from pinned host memory, runs the AA pair on it and
-    # copies it back out.  One state's copies overlap the other's pair, and the
+    # Three independent states are in flight, each on its own stream: a step of
+    # a state copies it in from pinned host memory, runs the AA pair on it and
+    # copies it back out.  One state's copies overlap the others' pairs, and the
     # two copy directions run at the same time.
     e2e = None
     if rank == 0 or world > 1:
-        nstate = 2
+        nstate = 3
         hosts = [torch.empty((19, lat.Npad), dtype=solver.pdf.dtype, pin_memory=True) for _ in range(nstate)]
         devs = [solver.pdf] + [torch.empty_like(solver.pdf) for _ in range(nstate - 1)]
         for h in hosts:
@@ -785,7 +785,7 @@ def main():
         e2e = {"value": world * 2 * N * Ke / (ems / 1e3) / 1e9, "unit": "GFLUP/s", "h2d_bytes_per_step": nb,
                "d2h_bytes_per_step": nb,
                "what": "per step: pinned-host -> device copy of an FP64 state, AA even+odd, device -> "
-                       "pinned-host copy of the state; two independent states in flight on two streams"}
+                       "pinned-host copy of the state; three independent states in flight on three streams"}
         del hosts, devs
 
     # ---- per-variant numbers ------------------------------------------------------------------------
