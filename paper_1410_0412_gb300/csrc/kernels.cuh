@@ -443,8 +443,8 @@ __global__ void __launch_bounds__(kBlock, MinCtasEven<PREC>::value) k_aa_even(De
 // AA even step for shifted FP16 storage, two consecutive nodes per thread: one
 // 4-byte half2 access per direction and thread keeps twice the bytes in flight
 // of the one-node form (Npad is a multiple of 128, so every pair is aligned;
-// a pair's second node may be padding, which is computed and stored but never
-// read as a node).
+// a pair's second node may lie past N: it is loaded and computed but not
+// stored).
 template <bool FORCE, bool DRAG>
 __global__ void __launch_bounds__(kBlock) k_aa_even_h2(DevTables t, KParams kp, CollConst<float> c,
                                                        __half* __restrict__ A, const float* __restrict__ s,
