@@ -538,6 +538,37 @@ def suite_exchange(args, lbm, torch):
     return out
 
 
+def suite_bed40(args, lbm, torch):
+    """The porosity-0.4 bed (about 6.7 M nodes) that random sequential addition cannot reach:
+    radius-12 spheres on a jittered, randomly rotated FCC lattice in the same 256^3 box, every
+    storage form and precision, with the loop balance of each."""
+    solid = geometry.packed_bed_fcc_256(1)
+    w = WORKLOAD
+    hbm, kind = peaks()
+    lat = lbm.Lattice(solid, periodic=w["periodic"], enum="lex", B=1).upload(
+        lbm.LBM_TABLES_ADJ | lbm.LBM_TABLES_RIA | lbm.LBM_TABLES_ET)
+    N = lat.N
+    r = lat.R / N
+    r_et = (len(lat.et_runs()[0]) - 1) / N
+    out = {"suite": "bed40", "fluid_nodes": N, "porosity": geometry.porosity(solid), "runs": lat.R, "r": r,
+           "r_et": r_et, "phantoms": lat.et_info()[0] - N, "pairs": args.steps, "variants": {}}
+    for prec, pb in (("f64", 8), ("f64df", 8), ("f32", 4), ("f16s", 2)):
+        params = lbm.Params(omega_plus=w["omega_plus"], magic=w["magic"], g=w["g"],
+                            shifted=prec in ("f32", "f16s"))
+        for form, ria in (("osnt", False), ("osnt", True), ("aa", False), ("aa", True), ("et", False),
+                          ("et", True)):
+            name = f"{form}{'_r' if ria else ''}"
+            sv, g = _time_variant(lbm, torch, lat, prec, params, form, ria, args.steps)
+            bl = loop_balance(name, pb, r_et if name == "et_r" else r)
+            out["variants"][f"{name}_{prec}"] = {"GFLUPs": g, "B_l": bl, "frac_hbm": g * bl / hbm}
+            del sv
+            torch.cuda.empty_cache()
+    dp = COLL_DP_INSTR_UNIT_OMEGA if w["omega_plus"] == 1.0 else COLL_DP_INSTR_GENERAL
+    out["aa_r_f64_fp64_pipe_frac"] = out["variants"]["aa_r_f64"]["GFLUPs"] * dp / FP64_PEAK_GINSTR
+    out["hbm_peak_GBs"] = hbm
+    return out
+
+
 def suite_graph(args, lbm, torch):
     """Launch overhead on the small sphere box (64x32x32, ~46k nodes): direct launches vs CUDA graph replay."""
     solid = geometry.sphere_box_64x32x32(0)
@@ -565,7 +596,7 @@ def suite_graph(args, lbm, torch):
     return out
 
 
-SUITES = {"bandwidth": suite_bandwidth, "partition": suite_partition, "exchange": suite_exchange,
+SUITES = {"bandwidth": suite_bandwidth, "partition": suite_partition, "exchange": suite_exchange, "bed40": suite_bed40,
           "graph": suite_graph, "channel": suite_channel, "sweep": suite_sweep, "foam": suite_foam, "adjoint": suite_adjoint,
           "large": suite_large}
 
@@ -610,7 +641,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--box", type=int, default=None, help="smaller cubic bed (profiling only)")
-    ap.add_argument("--suite", default=None, choices=sorted(["bandwidth", "channel", "sweep", "foam", "adjoint", "exchange",
+    ap.add_argument("--suite", default=None, choices=sorted(["bandwidth", "channel", "sweep", "foam", "adjoint", "exchange", "bed40",
                                                              "large", "partition", "graph"]),
                     help="measure another configuration instead of the headline (one JSON line)")
     ap.add_argument("--radius", type=float, default=None, help="foam strut radius (suites foam/large)")
