@@ -96,3 +96,18 @@ def test_et_runs_paper_channel():
     lat = lbm.Lattice(solid, periodic=(0, 0, 1))
     rs, _, _ = lat.et_runs()
     assert len(rs) - 1 == 3 * 98 * 8
+
+
+@pytest.mark.parametrize("dims,periodic", [((1, 8, 1), (1, 0, 1)), ((3, 1, 4), (1, 1, 0)), ((2, 2, 2), (1, 1, 1)),
+                                           ((5, 4, 1), (0, 0, 1))])
+def test_et_tables_degenerate_boxes(dims, periodic):
+    solid = geometry.empty_box(*dims)
+    lat = lbm.Lattice(solid, periodic=periodic)
+    T = tables.Tables(solid, periodic=periodic)
+    nb, mask, ph = et.tables(solid, T.node_xyz, T.adj, periodic)
+    lnb, lmask = lat.et_tables()
+    assert np.array_equal(lnb, nb) and np.array_equal(lmask, mask)
+    assert np.array_equal(lat.et_info()[2], ph)
+    rs, rnb, rm = et.run_tables(nb, mask)
+    lrs, lrnb, lrm = lat.et_runs()
+    assert np.array_equal(lrs, rs) and np.array_equal(lrnb, rnb) and np.array_equal(lrm, rm)

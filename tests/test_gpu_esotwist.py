@@ -179,3 +179,26 @@ def test_et_empty_and_errors():
     grid = lat.new_grid("f64", et=True)
     with pytest.raises(lbm.LbmError):
         lbm.lbm_step_et(lat, "f64", lbm.Params(), grid, 0)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f64df"])
+@pytest.mark.parametrize("ria", [False, True])
+def test_et_plane_poiseuille(prec, ria):
+    """1 x 8 x 1, periodic x and z (links joining a node to itself): the ET kernels reach the
+    exact TRT Poiseuille profile (magic 3/16) and match the oracle's OS-NT state."""
+    H = 8
+    solid = geometry.empty_box(1, H, 1)
+    lat = lbm.Lattice(solid, periodic=(1, 0, 1)).upload(ALL)
+    T = otables.Tables(solid, periodic=(1, 0, 1))
+    op = olbm.Params(omega_plus=1.0, magic=3 / 16, g=(1e-4, 0, 0))
+    lp = lbm.Params(omega_plus=1.0, magic=3 / 16, g=(1e-4, 0, 0))
+    sv = lbm.Solver(lat, prec, lp, form="et", ria=ria)
+    sv.init_equilibrium(1.0)
+    sv.step(20)
+    G = olbm.run_osnt(olbm.from_canonical(olbm.uniform_state(T.N, op), 0, T.adj, op), T.adj, op, 20)
+    assert _relerr(sv.canonical().cpu(), olbm.canonical(G, 0, T.adj, op)) <= 1e-12
+    sv.step(5000)
+    _, u, _ = sv.macroscopic(sums=False)
+    y = torch.as_tensor(T.node_xyz[:, 1], dtype=torch.float64) + 0.5
+    exact = op.g[0] / (2 * op.nu) * y * (H - y)
+    assert float((u[0].cpu() - exact).abs().max() / exact.max()) <= 1e-10

@@ -201,3 +201,25 @@ def test_et_runs_on_the_paper_channel_rows():
     rs, _, _ = et.run_tables(nb, mask)
     # each row: the first node, the 36 interior ones, the last node
     assert len(rs) - 1 == 3 * 5 * 6
+
+
+def test_esotwist_one_voxel_periodic_axes():
+    """Plane Poiseuille geometry (1 x 8 x 1, periodic x and z): links in x and z join a node to
+    itself, and the ET form still equals OS-NT and reaches the exact parabolic profile."""
+    H = 8
+    solid = geometry.empty_box(1, H, 1)
+    T = tables.Tables(solid, periodic=(1, 0, 1))
+    nb, mask, ph = et.tables(solid, T.node_xyz, T.adj, (1, 0, 1))
+    p = lbm.Params(omega_plus=1.0, magic=3 / 16, g=(1e-4, 0, 0))
+    F0 = lbm.uniform_state(T.N, p)
+    A = et.from_canonical(F0, 0, nb, T.N + len(ph))
+    G = lbm.from_canonical(F0, 0, T.adj, p)
+    for k in range(6):
+        A = et.step(A, k % 2, nb, T.adj, p)
+        G = lbm.osnt_step(G, T.adj, p)
+        assert torch.max(torch.abs(et.canonical(A, (k + 1) % 2, nb) - lbm.canonical(G, 0, T.adj, p))) <= 1e-16
+    A = et.run(A, nb, T.adj, p, 3000, start_parity=0)
+    rho, u, _ = lbm.macroscopic(et.canonical(A, 0, nb), p)
+    y = torch.as_tensor(T.node_xyz[:, 1], dtype=torch.float64) + 0.5
+    exact = p.g[0] / (2 * p.nu) * y * (H - y)
+    assert torch.max(torch.abs(u[0] - exact)) / exact.max() <= 1e-10
