@@ -166,3 +166,20 @@ def test_packed_bed_crop_partitioned_hilbert_renumbered():
         chunks.step(4)
         torch.cuda.synchronize()
         assert torch.equal(chunks.to_global(), whole.pdf[:, :lat.N])
+
+
+@pytest.mark.parametrize("form", ["osnt", "aa"])
+def test_one_node_per_chunk(form):
+    """P = N: every fluid pull crosses a chunk border; the result still equals the whole lattice."""
+    solid = geometry.random_voxels(7, 6, 5, 0.25, 90)
+    lat = lbm.Lattice(solid, periodic=(1, 0, 1)).upload()
+    part = lbm.Partitioning(lat, lat.N).upload()
+    lp = _params("f64", False)
+    whole = lbm.Solver(lat, "f64", lp, form=form, ria=True)
+    whole.load(_state(lat.N, 4).cuda())
+    chunks = lbm.PartitionedSolver(part, "f64", lp, form=form, ria=True)
+    chunks.load_global(whole.pdf)
+    whole.step(6)
+    chunks.step(6)
+    torch.cuda.synchronize()
+    assert torch.equal(chunks.to_global(), whole.pdf[:, :lat.N])

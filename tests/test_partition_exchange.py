@@ -163,3 +163,16 @@ def test_empty_lattice_partition():
     part = lbm.Partitioning(lat, 1)
     assert part.sizes == [0] and part.ghost_pdfs == [0]
     part.validate(lat)
+
+
+def test_one_node_per_chunk():
+    """P = N: every pull from a fluid neighbour is a ghost; tables still match the oracle."""
+    solid = geometry.random_voxels(5, 4, 3, 0.2, 1)
+    lat = lbm.Lattice(solid, periodic=(1, 1, 0))
+    T = tables.Tables(solid, periodic=(1, 1, 0))
+    part = lbm.Partitioning(lat, lat.N)
+    part.validate(lat)
+    ref = tables.partition_local_tables(T.adj, lat.N)
+    for k, r in enumerate(ref):
+        assert np.array_equal(part.parts[k].tables()["adj"], r["adj"])
+    assert sum(part.ghost_pdfs) == int((T.adj >= 0).sum())
