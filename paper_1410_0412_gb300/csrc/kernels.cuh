@@ -49,10 +49,10 @@ template <int PREC, bool RIA> struct MinCtasOdd { static constexpr int value = R
 template <bool RIA> struct MinCtasOdd<LBM_F64, RIA> { static constexpr int value = 5; };
 template <bool RIA> struct MinCtasOdd<LBM_F64_DF, RIA> { static constexpr int value = 8; };
 // The Esoteric Twist step: every step is indirect, and a sweep of 6/8/10/12
-// on GB300 put FP32 and FP16 at 10 CTAs (<= 51 registers; +3-5 % over 8).
-// Double-float keeps 6 (its collision needs the registers), native FP64 5.
+// on GB300 put FP32 and FP16 at 10 CTAs (<= 51 registers; +3-5 % over 8),
+// double-float at 8 (+3 % over 6), native FP64 at 5.
 template <int PREC> struct MinCtasEt { static constexpr int value = 10; };
-template <> struct MinCtasEt<LBM_F64_DF> { static constexpr int value = 6; };
+template <> struct MinCtasEt<LBM_F64_DF> { static constexpr int value = 8; };
 template <> struct MinCtasEt<LBM_F64> { static constexpr int value = 5; };
 static_assert(kBlock % kWarpNodes == 0, "a warp must cover one run-index group");
 
