@@ -9,8 +9,11 @@
  * enumeration function (Sect. 1, Sect. 5.6); an adjacency list gives the 18
  * neighbours of every node (Sect. 4, "Loop Balance"); reduced indirect
  * addressing (RIA) replaces it by a run-length table where consecutive nodes
- * share a shifted access pattern (Sect. 4.1).  Two storage forms are offered:
- * the two-grid one-step form OS-NT and the single-grid AA pattern (Sect. 4).
+ * share a shifted access pattern (Sect. 4.1).  Three storage forms are
+ * offered: the two-grid one-step form OS-NT and the single-grid AA pattern
+ * (Sect. 4), and the single-grid Esoteric Twist the paper names (Sect. 1,
+ * Sect. 4).  A lattice can also be cut into chunks that step separately with a
+ * ghost-PDF exchange, the distributed form of Sect. 6.
  *
  * Conventions that hold for every call below:
  *  - Every function returns an int status (LBM_OK = 0 on success).  Errors
@@ -18,6 +21,10 @@
  *    thread's most recent failure.
  *  - Device memory is always owned by the caller and passed as a raw device
  *    pointer.  Host-side tables are owned by the opaque lbm_lattice handle.
+ *  - Threads: calls on different handles are independent.  Calls that change
+ *    a handle (uploads, and the first Esoteric Twist query, which derives its
+ *    tables) must not run concurrently with other calls on the same handle;
+ *    stepping calls only read the handle and may overlap.
  *  - Device work is enqueued on `stream` (a cudaStream_t passed as void*;
  *    NULL selects the legacy default stream) and is asynchronous: a call
  *    returns once the kernels are queued.  Launch errors are reported as
