@@ -880,6 +880,12 @@ def main():
             _t.set_num_threads(len(os.sched_getaffinity(0)))
             cpu = cpu_oracle_sample(solid, 3, zslab=64)
             cpu.pop("seconds", None)
+            # the same oracle on one host thread, one pair on a thin slab
+            _t.set_num_threads(1)
+            one = cpu_oracle_sample(solid, 1, zslab=8)
+            one.pop("seconds", None)
+            cpu["one_thread"] = one
+            _t.set_num_threads(len(os.sched_getaffinity(0)))
         except Exception as e:  # the baseline must never hide the GPU number
             cpu = {"error": str(e)}
 
