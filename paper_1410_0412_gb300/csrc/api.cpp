@@ -229,7 +229,11 @@ int lbm_renumber_partitions(const lbm_lattice* L, int P, int32_t* node_xyz_out) 
   if (P < 1 || P > L->N) return set_error(LBM_ERR_ARG, "P must be in [1, N]");
   if (!node_xyz_out) return set_error(LBM_ERR_ARG, "node_xyz_out is NULL");
   if (int64_t(L->node_xyz.size()) != 3 * L->N) return set_error(LBM_ERR_ARG, "lattice has no node coordinates");
-  return renumber_partitions(L, P, node_xyz_out);
+  try {
+    return renumber_partitions(L, P, node_xyz_out);
+  } catch (const std::bad_alloc&) {
+    return set_error(LBM_ERR_ALLOC, "out of host memory while renumbering");
+  }
 }
 
 int lbm_partition_ghosts(const lbm_lattice* L, int P, int64_t* ghost_pdfs) {
@@ -318,7 +322,11 @@ int lbm_check_finite(const double* values, int64_t count, void* stream) {
 
 int lbm_validate_tables(const lbm_lattice* L) {
   if (int rc = check_lat(L)) return rc;
-  return validate(L);
+  try {
+    return validate(L);
+  } catch (const std::bad_alloc&) {
+    return set_error(LBM_ERR_ALLOC, "out of host memory while validating");
+  }
 }
 
 int lbm_device_table_bytes(const lbm_lattice* L, int which, size_t* bytes) {

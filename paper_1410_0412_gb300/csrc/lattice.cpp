@@ -15,6 +15,7 @@
 #include <atomic>
 #include <cstring>
 #include <functional>
+#include <new>
 #include <thread>
 
 #include "internal.h"
@@ -408,8 +409,18 @@ int partition_ghosts(const lbm_lattice* L, int P, int64_t* ghosts) {
 // non-negative adjacency entry already names the fluid node there; every
 // other location gets a phantom storage index N + rank, ranks in
 // lexicographic order of the (wrapped) coordinates, x fastest.
+int derive_et_tables(lbm_lattice* L);
+
 int derive_et(lbm_lattice* L) {
   if (L->et_ready) return LBM_OK;
+  try {
+    return derive_et_tables(L);
+  } catch (const std::bad_alloc&) {
+    return set_error(LBM_ERR_ALLOC, "out of host memory for the Esoteric Twist tables");
+  }
+}
+
+int derive_et_tables(lbm_lattice* L) {
   if (L->partition_local)
     return set_error(LBM_ERR_UNSUPPORTED, "Esoteric Twist tables need a whole lattice, not a partition's local one");
   static const int kSrcDir[6] = {2, 4, 6, 8, 12, 16};

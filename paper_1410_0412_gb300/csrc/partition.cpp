@@ -120,6 +120,9 @@ int build_partitioning(const lbm_lattice* G, int P, lbm_partitioning* out) {
     } catch (const std::bad_alloc&) {
       status[p] = LBM_ERR_ALLOC;
       msg[p] = "out of host memory while building partition " + std::to_string(p);
+    } catch (...) {
+      status[p] = LBM_ERR_ALLOC;
+      msg[p] = "host tables of partition " + std::to_string(p) + " exceed the vector size limit";
     }
   });
   for (int p = 0; p < P; ++p)
@@ -368,7 +371,11 @@ int lbm_partition_export_ghosts(const lbm_partitioning* part, int p, int32_t* sr
 
 int lbm_partition_validate(const lbm_partitioning* part, const lbm_lattice* lat) {
   if (!part || !lat) return set_error(LBM_ERR_ARG, "partitioning or lattice handle is NULL");
-  return validate_partitioning(part, lat);
+  try {
+    return validate_partitioning(part, lat);
+  } catch (const std::bad_alloc&) {
+    return set_error(LBM_ERR_ALLOC, "out of host memory while validating the partitioning");
+  }
 }
 
 int lbm_halo_table_bytes(const lbm_partitioning* part, size_t* bytes) {
