@@ -7,6 +7,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "internal.h"
 
@@ -309,7 +310,12 @@ int lbm_export_adjacency_rows(const lbm_lattice* L, const int64_t* nodes, int64_
 int lbm_check_finite(const double* values, int64_t count, void* stream) {
   if (count < 0 || (count > 0 && !values)) return set_error(LBM_ERR_ARG, "values is NULL");
   if (count == 0) return LBM_OK;
-  std::vector<double> h(size_t(count), 0.0);
+  std::vector<double> h;
+  try {
+    h.assign(size_t(count), 0.0);
+  } catch (const std::bad_alloc&) {
+    return set_error(LBM_ERR_ALLOC, "out of host memory for the check");
+  }
   auto st = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemcpyAsync(h.data(), values, size_t(count) * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
