@@ -617,7 +617,13 @@ def lbm_flux_backward(lat, prec, params, s, T, K, ws, ria=False, lambda_0=None, 
     return grad
 
 
+_FLUX = None
+
+
 def _flux_function():
+    global _FLUX
+    if _FLUX is not None:
+        return _FLUX
     torch = _torch()
 
     class FluxObjective(torch.autograd.Function):
@@ -644,7 +650,16 @@ def _flux_function():
             grad = lbm_flux_backward(lat, prec, params, sf, T, K, ws, ria)
             return (grad * gJ).to(ctx.s_dtype), None, None, None, None, None, None, None
 
+    _FLUX = FluxObjective
     return FluxObjective
+
+
+def __getattr__(name):
+    # torch is imported on first use only; FluxObjective is the autograd Function
+    # class (FluxObjective.apply(s, lat, prec, params, G0, T, K, ria)).
+    if name == "FluxObjective":
+        return _flux_function()
+    raise AttributeError(name)
 
 
 def flux_objective(s, lat, prec, params, G0, T, K, ria=False):
@@ -766,7 +781,12 @@ __all__ = [
     "PartitionedSolver", "lbm_halo_exchange", "lbm_partition_run_aa", "lbm_partition_run_osnt",
     "lbm_objective_flux", "lbm_adjoint_step", "lbm_ckpt_workspace_bytes", "lbm_flux_forward", "lbm_flux_backward",
     "flux_objective", "new_adjoint", "lbm_macroscopic_noalloc", "lbm_check_finite", "lbm_bandwidth_kernel",
+    "State", "FluxObjective",
 ]
+
+
+# The simulation state object (grids, parity, grid swap) under its other name.
+State = Solver
 
 
 class PartitionedSolver:
