@@ -187,6 +187,7 @@ template <class R> struct CollConst {
   R gs[10], go[10];  // per pair k (first direction a = 2k-1): w_a-class S+ / S- scales times c_a . g
   R rho_s;
   R abb_in[2], abb_out[2];  // 2 w (rho_bc - rho_s) for w = 1/18 and 1/36
+  R inv_s;                  // 1 / storage scale of the scaled collision (see make_coll_step)
 };
 
 template <class R> inline CollConst<R> make_coll(const KParams& kp) {
@@ -215,12 +216,70 @@ template <class R> inline CollConst<R> make_coll(const KParams& kp) {
   }
   c.gs[0] = c.go[0] = R(0.0);
   c.rho_s = R(kp.rho_s);
+  c.inv_s = R(1.0f);
   for (int k = 0; k < 2; ++k) {
     const double w = k == 0 ? 1.0 / 18.0 : 1.0 / 36.0;
     c.abb_in[k] = R(2.0 * w * (kp.rho_in - kp.rho_s));
     c.abb_out[k] = R(2.0 * w * (kp.rho_out - kp.rho_s));
   }
   return c;
+}
+
+// The step kernels of LBM_F16S work in storage units, s (f - w rho_s) with s
+// the storage scale: every constant of the collision that its output is
+// linear in is multiplied by s (make_coll_step), and only rho and j are taken
+// back to physical units (four multiplies by 1/s), which saves a multiply per
+// PDF load and per PDF store.  With a power-of-two scale (the default 2^10)
+// every intermediate is exactly s times the unscaled one, so the stored
+// values are the same bits.
+template <int PREC> constexpr bool kScaled = PREC == LBM_F16S;
+
+template <int PREC> inline CollConst<typename St<PREC>::R> make_coll_step(const KParams& kp) {
+  using R = typename St<PREC>::R;
+  CollConst<R> c = make_coll<R>(kp);
+  if (kScaled<PREC>) {
+    const R sc = R(kp.scale);
+    c.k0a = c.k0a * sc;
+    c.k0b = c.k0b * sc;
+    c.k1 = c.k1 * sc;
+    c.k2 = c.k2 * sc;
+    c.fs = c.fs * sc;
+    c.fo = c.fo * sc;
+    for (int k = 0; k < 10; ++k) {
+      c.gs[k] = c.gs[k] * sc;
+      c.go[k] = c.go[k] * sc;
+    }
+    for (int k = 0; k < 2; ++k) {
+      c.abb_in[k] = c.abb_in[k] * sc;
+      c.abb_out[k] = c.abb_out[k] * sc;
+    }
+    c.inv_s = R(kp.inv_scale);
+  }
+  return c;
+}
+
+// PDF loads and stores of the step kernels: storage units for LBM_F16S
+// (no scale), the storage traits otherwise.
+template <int PREC>
+__device__ __forceinline__ typename St<PREC>::R ld_step(const typename St<PREC>::T* p, float inv_scale) {
+  if constexpr (kScaled<PREC>)
+    return __half2float(__ldg(p));
+  else
+    return St<PREC>::ld(p, inv_scale);
+}
+template <int PREC>
+__device__ __forceinline__ void st_step(typename St<PREC>::T* p, typename St<PREC>::R v, float scale) {
+  if constexpr (kScaled<PREC>)
+    *p = __float2half_rn(v);
+  else
+    St<PREC>::st(p, v, scale);
+}
+template <int PREC>
+__device__ __forceinline__ void st_stream_step(typename St<PREC>::T* p, typename St<PREC>::R v, float scale) {
+  if constexpr (kScaled<PREC>)
+    __stcs(p, __float2half_rn(v));
+  else
+    St<PREC>::st_stream(p, v, scale);
 }
 
 // c . v for a lattice direction with components in {-1, 0, 1}; folds at compile time.
@@ -279,7 +338,7 @@ __device__ __forceinline__ void coll_pair_f(R (&d)[kQ], const R sa, const R da, 
 // l+ = 1, so (1 - l+)/2 = 0 and 1 - l+ = 0: the even parts relax fully to
 // equilibrium, and the ten products with those zeros are skipped
 // (fma(0, x, e) = e, so the values are unchanged).
-template <class R, bool FORCE, bool DRAG, bool LP1 = false>
+template <class R, bool FORCE, bool DRAG, bool LP1 = false, bool SC = false>
 __device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const R s) {
   using ::fma;
   R sa[10], da[10];
@@ -293,9 +352,15 @@ __device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const
   for (int k = 1; k <= 9; ++k) drho += sa[k];
   // first moment: pairs k = 1..9 have directions (1,0,0) (0,1,0) (0,0,1) (1,1,0)
   // (1,-1,0) (1,0,1) (1,0,-1) (0,1,1) (0,1,-1)
-  const R jx = da[1] + da[4] + da[5] + da[6] + da[7];
-  const R jy = da[2] + da[4] - da[5] + da[8] + da[9];
-  const R jz = da[3] + da[6] - da[7] + da[8] - da[9];
+  R jx = da[1] + da[4] + da[5] + da[6] + da[7];
+  R jy = da[2] + da[4] - da[5] + da[8] + da[9];
+  R jz = da[3] + da[6] - da[7] + da[8] - da[9];
+  if (SC) {  // storage units -> physical units for the moments
+    drho = drho * c.inv_s;
+    jx = jx * c.inv_s;
+    jy = jy * c.inv_s;
+    jz = jz * c.inv_s;
+  }
   const R rho = c.rho_s + drho;
   const R irho = recip(rho);
   R ux = fma(jx, irho, c.hg[0]);
@@ -374,17 +439,17 @@ __device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const
 //   AA grid after an odd count:      A[inv i][m]  | marker: A[i][n]
 // a pressure marker (-2 / -3) turns the bounce-back value v into
 // 2 w_i (rho_bc - rho_s) - v (anti-bounce-back, in deviation form).
-template <int PREC, bool AA_ODD>
+template <int PREC, bool AA_ODD, bool SC = false>
 __device__ __forceinline__ void gather(const typename St<PREC>::T* g, uint32_t npad, int n, const int (&m)[18],
                                        typename St<PREC>::R (&d)[kQ], float inv_scale,
                                        const CollConst<typename St<PREC>::R>& c, int pressure) {
-  d[0] = St<PREC>::ld(g + n, inv_scale);
+  d[0] = SC ? ld_step<PREC>(g + n, inv_scale) : St<PREC>::ld(g + n, inv_scale);
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
     const int mi = m[i - 1];
     const int dir = (mi >= 0) == AA_ODD ? inv(i) : i;
     const int node = mi >= 0 ? mi : n;
-    d[i] = St<PREC>::ld(g + at(dir, npad, node), inv_scale);
+    d[i] = SC ? ld_step<PREC>(g + at(dir, npad, node), inv_scale) : St<PREC>::ld(g + at(dir, npad, node), inv_scale);
   }
   if (pressure) {  // uniform: only lattices with pressure faces pay for the check
 #pragma unroll
@@ -415,11 +480,11 @@ __global__ void __launch_bounds__(kBlock, MinCtasOsnt<PREC, RIA>::value) k_osnt(
     nbr_adj(t, n, m);
   }
   R d[kQ];
-  gather<PREC, false>(src, t.npad, n, m, d, kp.inv_scale, c, t.pressure);
+  gather<PREC, false, kScaled<PREC>>(src, t.npad, n, m, d, kp.inv_scale, c, t.pressure);
   const R sn = DRAG ? R(__ldg(s + n)) : R(0);
-  collide<R, FORCE, DRAG, LP1>(d, c, sn);
+  collide<R, FORCE, DRAG, LP1, kScaled<PREC>>(d, c, sn);
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) St<PREC>::st_stream(dst + at(i, t.npad, n), d[i], kp.scale);
+  for (int i = 0; i < kQ; ++i) st_stream_step<PREC>(dst + at(i, t.npad, n), d[i], kp.scale);
 }
 
 // AA even step: direct read of the 19 local PDFs, collide, write to the
@@ -433,11 +498,11 @@ __global__ void __launch_bounds__(kBlock, MinCtasEven<PREC>::value) k_aa_even(De
   if (n >= N) return;
   R d[kQ];
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) d[i] = St<PREC>::ld(A + at(i, t.npad, n), kp.inv_scale);
+  for (int i = 0; i < kQ; ++i) d[i] = ld_step<PREC>(A + at(i, t.npad, n), kp.inv_scale);
   const R sn = DRAG ? R(__ldg(s + n)) : R(0);
-  collide<R, FORCE, DRAG, LP1>(d, c, sn);
+  collide<R, FORCE, DRAG, LP1, kScaled<PREC>>(d, c, sn);
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) St<PREC>::st(A + at(inv(i), t.npad, n), d[i], kp.scale);
+  for (int i = 0; i < kQ; ++i) st_step<PREC>(A + at(inv(i), t.npad, n), d[i], kp.scale);
 }
 
 // AA even step for shifted FP16 storage, two consecutive nodes per thread: one
@@ -455,23 +520,22 @@ __global__ void __launch_bounds__(kBlock) k_aa_even_h2(DevTables t, KParams kp, 
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     const float2 v = __half22float2(__ldg(reinterpret_cast<const __half2*>(A + at(i, t.npad, n))));
-    d0[i] = v.x * kp.inv_scale;
-    d1[i] = v.y * kp.inv_scale;
+    d0[i] = v.x;  // storage units: the scale is folded into c (make_coll_step)
+    d1[i] = v.y;
   }
   const float s0 = DRAG ? __ldg(s + n) : 0.0f;
   const float s1 = DRAG ? (n + 1 < N ? __ldg(s + n + 1) : 0.0f) : 0.0f;
-  collide<float, FORCE, DRAG>(d0, c, s0);
-  collide<float, FORCE, DRAG>(d1, c, s1);
+  collide<float, FORCE, DRAG, false, true>(d0, c, s0);
+  collide<float, FORCE, DRAG, false, true>(d1, c, s1);
   // the pair's second node may lie past N (odd N): write node slots only, as
   // the slot after the last node can be a partition's ghost slot
   if (n + 1 < N) {
 #pragma unroll
     for (int i = 0; i < kQ; ++i)
-      *reinterpret_cast<__half2*>(A + at(inv(i), t.npad, n)) =
-          __floats2half2_rn(d0[i] * kp.scale, d1[i] * kp.scale);
+      *reinterpret_cast<__half2*>(A + at(inv(i), t.npad, n)) = __floats2half2_rn(d0[i], d1[i]);
   } else {
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) A[at(inv(i), t.npad, n)] = __float2half_rn(d0[i] * kp.scale);
+    for (int i = 0; i < kQ; ++i) A[at(inv(i), t.npad, n)] = __float2half_rn(d0[i]);
   }
 }
 
@@ -505,11 +569,11 @@ __global__ void __launch_bounds__(kBlock, MinCtasOdd<PREC, RIA>::value) k_aa_odd
 #pragma unroll
       for (int j = 0; j < 18; ++j) s_m[j][threadIdx.x] = m[j];
     }
-    gather<PREC, true>(A, t.npad, n, m, d, kp.inv_scale, c, t.pressure);
+    gather<PREC, true, kScaled<PREC>>(A, t.npad, n, m, d, kp.inv_scale, c, t.pressure);
   }
   const R sn = DRAG ? R(__ldg(s + n)) : R(0);
-  collide<R, FORCE, DRAG, LP1>(d, c, sn);
-  St<PREC>::st(A + n, d[0], kp.scale);
+  collide<R, FORCE, DRAG, LP1, kScaled<PREC>>(d, c, sn);
+  st_step<PREC>(A + n, d[0], kp.scale);
   // p_i goes to the slot node m_{inv i} pulls it from next (or, through a
   // marker, to this node's own opposite slot); re-reads are issued first
   int mo_[18];
@@ -523,7 +587,7 @@ __global__ void __launch_bounds__(kBlock, MinCtasOdd<PREC, RIA>::value) k_aa_odd
       if (mo < -1) v = (mo == LBM_MARK_INLET ? c.abb_in[wclass(i) - 1] : c.abb_out[wclass(i) - 1]) - v;
       const int dir = mo >= 0 ? i : inv(i);
       const int node = mo >= 0 ? mo : n;
-      St<PREC>::st(A + at(dir, t.npad, node), v, kp.scale);
+      st_step<PREC>(A + at(dir, t.npad, node), v, kp.scale);
     }
   } else {
 #pragma unroll
@@ -531,7 +595,7 @@ __global__ void __launch_bounds__(kBlock, MinCtasOdd<PREC, RIA>::value) k_aa_odd
       const int mo = mo_[inv(i) - 1];
       const int dir = mo >= 0 ? i : inv(i);
       const int node = mo >= 0 ? mo : n;
-      St<PREC>::st(A + at(dir, t.npad, node), d[i], kp.scale);
+      st_step<PREC>(A + at(dir, t.npad, node), d[i], kp.scale);
     }
   }
 }
@@ -601,18 +665,18 @@ __global__ void __launch_bounds__(kBlock, MinCtasEt<PREC>::value) k_et(DevTables
   int loc[7];
   unsigned mask = et_locate<RIA>(t, n, loc);
   R d[kQ];
-  d[0] = St<PREC>::ld(A + n, kp.inv_scale);
+  d[0] = ld_step<PREC>(A + n, kp.inv_scale);
 #pragma unroll
   for (int i = 1; i < kQ; ++i)
-    d[i] = St<PREC>::ld(A + at(ODD ? inv(i) : i, t.spad, loc[et_row(inv(i)) + 1]), kp.inv_scale);
+    d[i] = ld_step<PREC>(A + at(ODD ? inv(i) : i, t.spad, loc[et_row(inv(i)) + 1]), kp.inv_scale);
   if (kStash) {
 #pragma unroll
     for (int k = 1; k < 7; ++k) s_loc[k - 1][threadIdx.x] = loc[k];
     s_loc[6][threadIdx.x] = int(mask);
   }
   const R sn = DRAG ? R(__ldg(s + n)) : R(0);
-  collide<R, FORCE, DRAG, LP1>(d, c, sn);
-  St<PREC>::st(A + n, d[0], kp.scale);
+  collide<R, FORCE, DRAG, LP1, kScaled<PREC>>(d, c, sn);
+  st_step<PREC>(A + n, d[0], kp.scale);
   if (kStash) {
 #pragma unroll
     for (int k = 1; k < 7; ++k) loc[k] = s_loc[k - 1][threadIdx.x];
@@ -627,7 +691,7 @@ __global__ void __launch_bounds__(kBlock, MinCtasEt<PREC>::value) k_et(DevTables
       if (t.pressure && ((mask >> et_xbit(jj)) & 1u))
         v = (cx(jj) > 0 ? c.abb_in[wclass(j) - 1] : c.abb_out[wclass(j) - 1]) - v;
     }
-    St<PREC>::st(A + at(link != ODD ? jj : j, t.spad, loc[et_row(j) + 1]), v, kp.scale);
+    st_step<PREC>(A + at(link != ODD ? jj : j, t.spad, loc[et_row(j) + 1]), v, kp.scale);
   }
 }
 
@@ -926,7 +990,7 @@ int launch_osnt_t(const lbm_lattice* L, const KParams& kp, const void* src, void
   T* b = static_cast<T*>(dst);
   const int N = int(L->N);
   const bool f = has_force(kp);
-  const auto c = dev::make_coll<typename dev::St<PREC>::R>(kp);
+  const auto c = dev::make_coll_step<PREC>(kp);
   const bool lp1 = use_lp1<PREC>(kp);
 #define LBM_OSNT(R_, F_, D_) LBM_LAUNCH_LP1(k_osnt, LBM_TARGS3(R_, F_, D_), (L->dev, kp, c, a, b, s, N))
   if (s) {
@@ -950,12 +1014,12 @@ int launch_aa_t(const lbm_lattice* L, const KParams& kp, void* pdf, int parity, 
   const int N = int(L->N);
   const bool f = has_force(kp);
   const bool lp1 = use_lp1<PREC>(kp);
-  const auto c = dev::make_coll<typename dev::St<PREC>::R>(kp);
+  const auto c = dev::make_coll_step<PREC>(kp);
   if constexpr (PREC == LBM_F16S) {
     if (parity == 0) {
     const unsigned g2 = unsigned((L->N + 2 * dev::kBlock - 1) / (2 * dev::kBlock));
     __half* H = reinterpret_cast<__half*>(pdf);
-    const auto cf = dev::make_coll<float>(kp);
+    const auto cf = dev::make_coll_step<LBM_F16S>(kp);
     if (s) dev::k_aa_even_h2<true, true><<<g2, dev::kBlock, 0, st>>>(L->dev, kp, cf, H, s, N);
     else if (f) dev::k_aa_even_h2<true, false><<<g2, dev::kBlock, 0, st>>>(L->dev, kp, cf, H, s, N);
     else dev::k_aa_even_h2<false, false><<<g2, dev::kBlock, 0, st>>>(L->dev, kp, cf, H, s, N);
@@ -989,7 +1053,7 @@ int launch_et_t(const lbm_lattice* L, const KParams& kp, void* pdf, int parity, 
   T* A = static_cast<T*>(pdf);
   const int N = int(L->N);
   const bool f = has_force(kp);
-  const auto c = dev::make_coll<typename dev::St<PREC>::R>(kp);
+  const auto c = dev::make_coll_step<PREC>(kp);
   const bool lp1 = use_lp1<PREC>(kp);
 #define LBM_ET(R_, O_, F_, D_) LBM_LAUNCH_LP1(k_et, LBM_TARGS4(R_, O_, F_, D_), (L->dev, kp, c, A, s, N))
 #define LBM_ET_R(O_, F_, D_) \
