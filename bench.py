@@ -38,20 +38,19 @@ FALLBACK_HBM_GBS = 6800.0
 # FP64 pipe of GB300: 152 SMs x 2 DP lanes/clk x 2.07 GHz (measured 0.60 T DFMA/s burst)
 FP64_PEAK_GINSTR = 152 * 2 * 2.07e9 / 1e9
 # FP64-pipe instructions per node of the AA steps with a uniform body force
-# (adds, multiplies, FMAs and the reciprocal's Newton steps each take one FP64
-# slot), counted by ncu (smsp__sass_thread_inst_executed_op_{dadd,dfma,dmul}
-# _pred_on.sum over the nodes), the same for the even and odd step: 152 in
-# general (64 DADD, 59 DFMA, 29 DMUL); 142 when omega_plus = 1, where the
-# kernels skip the ten products with (1 - l+)/2 = 0 and 1 - l+ = 0
-# (64 DADD, 49 DFMA, 29 DMUL).
-COLL_DP_INSTR_GENERAL = 152
-COLL_DP_INSTR_UNIT_OMEGA = 142
+# along x (adds, multiplies, FMAs and the reciprocal's Newton steps each take
+# one FP64 slot; the moments and the halvings run on the integer pipe), counted
+# by ncu (smsp__sass_thread_inst_executed_op_{dadd,dfma,dmul}_pred_on.sum over
+# the nodes), the same for the even and odd step: 91 in general (37 DADD,
+# 41 DFMA, 13 DMUL); 81 when omega_plus = 1, where the kernels skip the ten
+# products with (1 - l+)/2 = 0 and 1 - l+ = 0 (37 DADD, 31 DFMA, 13 DMUL).
+COLL_DP_INSTR_GENERAL = 91
+COLL_DP_INSTR_UNIT_OMEGA = 81
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
 # dominant kernel, the FP64 AA odd step with RIA (l+ = 1 collision), on the
-# 10,896,954-node bed: 1,823,091,408 + 1,594,950,800, the mean over 16
-# launches of one ncu capture of this kernel version (313.7 B/node against the
-# model's 319.7).
-TRAFFIC_AA_ODD_RIA_F64 = 1823091408 + 1594950800
+# 10,896,954-node bed: 1,823,148,032 + 1,595,339,520 from one ncu capture of
+# this kernel version (313.7 B/node against the model's 319.7).
+TRAFFIC_AA_ODD_RIA_F64 = 1823148032 + 1595339520
 
 WORKLOAD = dict(name="packed_bed_256_rsa_r12", X=256, Y=256, Z=256, radius=12.0, seed=1, rejections=20000,
                 periodic=(1, 0, 0), g=(1e-6, 0.0, 0.0), omega_plus=1.0, magic=3.0 / 16.0)

@@ -77,7 +77,9 @@ extern "C" {
 #define LBM_ENUM_LEX 0       /* lexicographic order with blocking factor B (Sect. 5.6) */
 #define LBM_ENUM_HILBERT 1   /* Hilbert space-filling curve (Sect. 5.6)                */
 
-#define LBM_F64 0            /* double storage, double collision                     */
+#define LBM_F64 0            /* double storage, double collision; the step kernels
+                                take the moments as exact integer sums rounded once
+                                to double (lbm_exact_moments_host)                */
 #define LBM_F32 1            /* float storage, float collision                       */
 #define LBM_F16S 2           /* half storage of (f - w rho0) * f16_scale, float math */
 #define LBM_F64_DF 3         /* double storage (same grids as LBM_F64); the step's
@@ -308,6 +310,20 @@ LBM_API int lbm_export_adjacency_rows(const lbm_lattice* lat, const int64_t* nod
  * lbm_macroscopic) are all finite, LBM_ERR_NONFINITE otherwise.  Synchronises
  * `stream` to read them; a guard between steps, not for the timed loop. */
 LBM_API int lbm_check_finite(const double* values, int64_t count, void* stream);
+
+/* Host image of the FP64 step's moment arithmetic, so that it can be tested
+ * without a GPU.  The LBM_F64 step kernels form a node's moments -- the
+ * density deviation sum_i d_i, the momentum sum_i c_i d_i, and the pair sums
+ * and differences d_a +- d_inv(a) that the TRT collision (Sect. 2) splits
+ * into even and odd parts -- as exact fixed-point sums on the integer pipe,
+ * each rounded once to the nearest double; this runs the same routine on the
+ * host.  d: host double [n][19] (node-major, direction order as above);
+ * out: host double [n][22]: drho, jx, jy, jz, sa_1..sa_9, da_1..da_9, pair k
+ * holding directions 2k-1 and 2k.  A PDF more than 5 binades below the node's
+ * largest loses the bits below 2^-57 of that largest (truncated).  A node
+ * with an Inf or NaN PDF, or one of magnitude >= 2^1017, gets drho = NaN.
+ * LBM_ERR_ARG for NULL pointers or n < 0. */
+LBM_API int lbm_exact_moments_host(const double* d, int64_t n, double* out);
 
 /* Check the host tables: entries in range, adjacency reciprocity
  * (adj[i][n] = m >= 0  <=>  adj[inv i][m] = n), run table decoding back to the

@@ -536,6 +536,22 @@ def lbm_check_finite(values, stream=None):
     check(_lib.load().lbm_check_finite(_ptr(values), values.numel(), _stream(stream)), "lbm_check_finite")
 
 
+def lbm_exact_moments_host(d):
+    """Moments of nodes by the FP64 step's integer arithmetic, run on the host.
+
+    d: float64 array [n, 19] (numpy or CPU tensor), direction order of the
+    lattice.  Returns a numpy float64 array [n, 22]: drho, jx, jy, jz,
+    sa_1..sa_9, da_1..da_9 (pair k holds directions 2k-1 and 2k).
+    """
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(d, dtype=np.float64))
+    if a.ndim != 2 or a.shape[1] != 19:
+        raise ValueError("d must have shape [n, 19]")
+    out = np.empty((a.shape[0], 22), dtype=np.float64)
+    check(_lib.load().lbm_exact_moments_host(a.ctypes.data, a.shape[0], out.ctypes.data), "lbm_exact_moments_host")
+    return out
+
+
 def lbm_bandwidth_kernel(kind, dst, src=None, arrays=1, stream=None):
     """One launch of the CNT-kA (kind 0, copy src -> dst with streaming stores) or
     U-kA (kind 1, update dst in place) bandwidth kernel over ``arrays`` equal
@@ -781,6 +797,7 @@ __all__ = [
     "PartitionedSolver", "lbm_halo_exchange", "lbm_partition_run_aa", "lbm_partition_run_osnt",
     "lbm_objective_flux", "lbm_adjoint_step", "lbm_ckpt_workspace_bytes", "lbm_flux_forward", "lbm_flux_backward",
     "flux_objective", "new_adjoint", "lbm_macroscopic_noalloc", "lbm_check_finite", "lbm_bandwidth_kernel",
+    "lbm_exact_moments_host",
     "State", "FluxObjective",
 ]
 

@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include "exact64.cuh"
 #include "internal.h"
 
 namespace lbm {
@@ -323,6 +324,25 @@ int lbm_check_finite(const double* values, int64_t count, void* stream) {
   for (int64_t k = 0; k < count; ++k)
     if (!std::isfinite(h[size_t(k)]))
       return set_error(LBM_ERR_NONFINITE, "non-finite value at index " + std::to_string(k));
+  return LBM_OK;
+}
+
+int lbm_exact_moments_host(const double* d, int64_t n, double* out) {
+  if (n < 0 || (n > 0 && (!d || !out))) return set_error(LBM_ERR_ARG, "d or out is NULL, or n < 0");
+  for (int64_t k = 0; k < n; ++k) {
+    double f[19], sa[10], da[10], drho, jx, jy, jz;
+    std::memcpy(f, d + 19 * k, sizeof f);
+    dev::exact_moments<true>(f, sa, da, drho, jx, jy, jz);
+    double* o = out + 22 * k;
+    o[0] = drho;
+    o[1] = jx;
+    o[2] = jy;
+    o[3] = jz;
+    for (int p = 1; p <= 9; ++p) {
+      o[3 + p] = sa[p];
+      o[12 + p] = da[p];
+    }
+  }
   return LBM_OK;
 }
 

@@ -7,7 +7,10 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "df32.cuh"
+#include "exact64.cuh"
 #include "internal.h"
 
 namespace lbm {
@@ -179,15 +182,17 @@ template <class R> struct CollConst {
   R hg[3];    // g / 2
   R g[3];
   R k0a, k0b; // l+/18, 3 a+/18 (K0 of the axis class: k0a*base - k0b*uF)
+  R k0a15;    // 3/2 k0a
   R k1;       // 4.5 l+ / 18 = l+/4 (K1 of the axis class, times rho)
   R k2;       // 3 l- / 18 = l-/6   (K2 of the axis class, times rho)
   R fs;       // 9 a+ / 18 = a+/2   (axis-class scale of F in S+)
   R fo;       // 3 a- / 18 = a-/6   (axis-class scale of F in S-)
   R omlp;     // 1 - l+
-  R gs[10], go[10];  // per pair k (first direction a = 2k-1): w_a-class S+ / S- scales times c_a . g
+  R gsv[3], gov[3];  // axis-class S+ / S- force scales times g: fs g, fo g
   R rho_s;
   R abb_in[2], abb_out[2];  // 2 w (rho_bc - rho_s) for w = 1/18 and 1/36
   R inv_s;                  // 1 / storage scale of the scaled collision (see make_coll_step)
+  bool gx;                  // the body force points along x (g_y = g_z = 0)
 };
 
 template <class R> inline CollConst<R> make_coll(const KParams& kp) {
@@ -207,16 +212,14 @@ template <class R> inline CollConst<R> make_coll(const KParams& kp) {
   c.fs = R(ap / 2.0);
   c.fo = R(am / 6.0);
   c.omlp = R(1.0 - kp.lp);
-  for (int k = 1; k <= 9; ++k) {
-    const int a = 2 * k - 1;
-    const double cg = kCX[a] * kp.g[0] + kCY[a] * kp.g[1] + kCZ[a] * kp.g[2];
-    const double wscale = a <= 6 ? 1.0 : 0.5;  // diagonal class: half of the axis-class scale
-    c.gs[k] = R(wscale * (ap / 2.0) * cg);
-    c.go[k] = R(wscale * (am / 6.0) * cg);
+  c.k0a15 = R(1.5 * kp.lp / 18.0);
+  for (int a = 0; a < 3; ++a) {
+    c.gsv[a] = R((ap / 2.0) * kp.g[a]);
+    c.gov[a] = R((am / 6.0) * kp.g[a]);
   }
-  c.gs[0] = c.go[0] = R(0.0);
   c.rho_s = R(kp.rho_s);
   c.inv_s = R(1.0f);
+  c.gx = kp.g[1] == 0.0 && kp.g[2] == 0.0;
   for (int k = 0; k < 2; ++k) {
     const double w = k == 0 ? 1.0 / 18.0 : 1.0 / 36.0;
     c.abb_in[k] = R(2.0 * w * (kp.rho_in - kp.rho_s));
@@ -241,13 +244,14 @@ template <int PREC> inline CollConst<typename St<PREC>::R> make_coll_step(const 
     const R sc = R(kp.scale);
     c.k0a = c.k0a * sc;
     c.k0b = c.k0b * sc;
+    c.k0a15 = c.k0a15 * sc;
     c.k1 = c.k1 * sc;
     c.k2 = c.k2 * sc;
     c.fs = c.fs * sc;
     c.fo = c.fo * sc;
-    for (int k = 0; k < 10; ++k) {
-      c.gs[k] = c.gs[k] * sc;
-      c.go[k] = c.go[k] * sc;
+    for (int a = 0; a < 3; ++a) {
+      c.gsv[a] = c.gsv[a] * sc;
+      c.gov[a] = c.gov[a] * sc;
     }
     for (int k = 0; k < 2; ++k) {
       c.abb_in[k] = c.abb_in[k] * sc;
@@ -292,69 +296,63 @@ template <class R, int X, int Y, int Z> __device__ __forceinline__ R cdot(R vx, 
   return acc;
 }
 
-template <class R, bool FORCE, int K, bool LP1>
+// Pair k (first direction a = 2k-1, b = inv a) from its class's vectors
+// T = K1 u + F+ and O = K2 u + F- (F+- the class's scaled forces): the even
+// part is e = K0 + (c_a.u)(c_a.T), the odd part o = c_a.O.  The diagonal class
+// passes K0, T and O halved.
+template <class R, int K, bool LP1>
 __device__ __forceinline__ void coll_pair(R (&d)[kQ], const R sa, const R da, const R ux, const R uy, const R uz,
-                                          const R K0, const R K1, const R K2, const R Fsx, const R Fsy,
-                                          const R Fsz, const R Fox, const R Foy, const R Foz, const R qp,
-                                          const R qm) {
+                                          const R K0, const R Tx, const R Ty, const R Tz, const R Ox, const R Oy,
+                                          const R Oz, const R qp, const R qm) {
   using ::fma;
   constexpr int a = 2 * K - 1, b = 2 * K;
   const R cu = cdot<R, cx(a), cy(a), cz(a)>(ux, uy, uz);
-  R t, o;
-  if (FORCE) {
-    const R cFs = cdot<R, cx(a), cy(a), cz(a)>(Fsx, Fsy, Fsz);
-    const R cFo = cdot<R, cx(a), cy(a), cz(a)>(Fox, Foy, Foz);
-    t = fma(K1, cu, cFs);
-    o = fma(K2, cu, cFo);
-  } else {
-    t = K1 * cu;
-    o = K2 * cu;
-  }
-  const R e = fma(cu, t, K0);
+  const R ct = cdot<R, cx(a), cy(a), cz(a)>(Tx, Ty, Tz);
+  const R co = cdot<R, cx(a), cy(a), cz(a)>(Ox, Oy, Oz);
+  const R e = fma(cu, ct, K0);
   const R Ep = LP1 ? e : fma(qp, sa, e);
-  const R Op = fma(qm, da, o);
+  const R Op = fma(qm, da, co);
   d[a] = Ep + Op;
   d[b] = Ep - Op;
 }
 
-// Same pair update with the force projections c.F (already scaled) given.
-template <class R, int K, bool LP1>
-__device__ __forceinline__ void coll_pair_f(R (&d)[kQ], const R sa, const R da, const R ux, const R uy, const R uz,
-                                            const R K0, const R K1, const R K2, const R cFs, const R cFo,
-                                            const R qp, const R qm) {
-  using ::fma;
-  constexpr int a = 2 * K - 1, b = 2 * K;
-  const R cu = cdot<R, cx(a), cy(a), cz(a)>(ux, uy, uz);
-  const R t = fma(K1, cu, cFs);
-  const R o = fma(K2, cu, cFo);
-  const R e = fma(cu, t, K0);
-  const R Ep = LP1 ? e : fma(qp, sa, e);
-  const R Op = fma(qm, da, o);
-  d[a] = Ep + Op;
-  d[b] = Ep - Op;
+// Pair sums sa_k = d_a + d_b and differences da_k = d_a - d_b, the density
+// deviation and the momentum.  FP64 takes them exactly on the integer pipe
+// (exact64.cuh), with sa converted only when the caller needs it (l+ != 1).
+template <class R, bool NEED_SA>
+__device__ __forceinline__ void moments(const R (&d)[kQ], R (&sa)[10], R (&da)[10], R& drho, R& jx, R& jy, R& jz) {
+  if constexpr (std::is_same<R, double>::value) {
+    exact_moments<NEED_SA>(d, sa, da, drho, jx, jy, jz);
+  } else {
+#pragma unroll
+    for (int k = 1; k <= 9; ++k) {
+      sa[k] = d[2 * k - 1] + d[2 * k];
+      da[k] = d[2 * k - 1] - d[2 * k];
+    }
+    drho = d[0];
+#pragma unroll
+    for (int k = 1; k <= 9; ++k) drho += sa[k];
+    jx = da[1] + da[4] + da[5] + da[6] + da[7];
+    jy = da[2] + da[4] - da[5] + da[8] + da[9];
+    jz = da[3] + da[6] - da[7] + da[8] - da[9];
+  }
 }
+
+// Halving: an exponent decrement for FP64 (exact64.cuh), a multiply otherwise.
+__device__ __forceinline__ double halve(double x) { return halve_exact(x); }
+__device__ __forceinline__ float halve(float x) { return half(x); }
+__device__ __forceinline__ df halve(df x) { return half(x); }
 
 // s: Brinkman solid fraction of the node (DRAG only).  LP1: the caller knows
 // l+ = 1, so (1 - l+)/2 = 0 and 1 - l+ = 0: the even parts relax fully to
 // equilibrium, and the ten products with those zeros are skipped
 // (fma(0, x, e) = e, so the values are unchanged).
+// SC: the PDFs are in storage units (make_coll_step); rho and j are scaled back.
 template <class R, bool FORCE, bool DRAG, bool LP1 = false, bool SC = false>
 __device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const R s) {
   using ::fma;
-  R sa[10], da[10];
-#pragma unroll
-  for (int k = 1; k <= 9; ++k) {
-    sa[k] = d[2 * k - 1] + d[2 * k];
-    da[k] = d[2 * k - 1] - d[2 * k];
-  }
-  R drho = d[0];
-#pragma unroll
-  for (int k = 1; k <= 9; ++k) drho += sa[k];
-  // first moment: pairs k = 1..9 have directions (1,0,0) (0,1,0) (0,0,1) (1,1,0)
-  // (1,-1,0) (1,0,1) (1,0,-1) (0,1,1) (0,1,-1)
-  R jx = da[1] + da[4] + da[5] + da[6] + da[7];
-  R jy = da[2] + da[4] - da[5] + da[8] + da[9];
-  R jz = da[3] + da[6] - da[7] + da[8] - da[9];
+  R sa[10], da[10], drho, jx, jy, jz;
+  moments<R, !LP1>(d, sa, da, drho, jx, jy, jz);
   if (SC) {  // storage units -> physical units for the moments
     drho = drho * c.inv_s;
     jx = jx * c.inv_s;
@@ -366,69 +364,77 @@ __device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const
   R ux = fma(jx, irho, c.hg[0]);
   R uy = fma(jy, irho, c.hg[1]);
   R uz = fma(jz, irho, c.hg[2]);
-  const R uu = fma(ux, ux, fma(uy, uy, uz * uz));  // (the drag path recomputes it after scaling u)
-  if (FORCE && !DRAG) {
-    // uniform body force F = rho g: its projections are rho times per-pair constants
-    const R base = fma(-1.5f * rho, uu, drho);  // drho - 3/2 rho u.u
-    const R uF = rho * fma(ux, c.g[0], fma(uy, c.g[1], uz * c.g[2]));
-    const R K0a = fma(c.k0a, base, -c.k0b * uF);
-    const R K1a = c.k1 * rho, K2a = c.k2 * rho;
-    const R K0b = half(K0a), K1b = half(K1a), K2b = half(K2a);
-    coll_pair_f<R, 1, LP1>(d, sa[1], da[1], ux, uy, uz, K0a, K1a, K2a, rho * c.gs[1], rho * c.go[1], c.qp, c.qm);
-    coll_pair_f<R, 2, LP1>(d, sa[2], da[2], ux, uy, uz, K0a, K1a, K2a, rho * c.gs[2], rho * c.go[2], c.qp, c.qm);
-    coll_pair_f<R, 3, LP1>(d, sa[3], da[3], ux, uy, uz, K0a, K1a, K2a, rho * c.gs[3], rho * c.go[3], c.qp, c.qm);
-    coll_pair_f<R, 4, LP1>(d, sa[4], da[4], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[4], rho * c.go[4], c.qp, c.qm);
-    coll_pair_f<R, 5, LP1>(d, sa[5], da[5], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[5], rho * c.go[5], c.qp, c.qm);
-    coll_pair_f<R, 6, LP1>(d, sa[6], da[6], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[6], rho * c.go[6], c.qp, c.qm);
-    coll_pair_f<R, 7, LP1>(d, sa[7], da[7], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[7], rho * c.go[7], c.qp, c.qm);
-    coll_pair_f<R, 8, LP1>(d, sa[8], da[8], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[8], rho * c.go[8], c.qp, c.qm);
-    coll_pair_f<R, 9, LP1>(d, sa[9], da[9], ux, uy, uz, K0b, K1b, K2b, rho * c.gs[9], rho * c.go[9], c.qp, c.qm);
-    d[0] = LP1 ? 6.0f * K0a : fma(c.omlp, d[0], 6.0f * K0a);
-    return;
-  }
-  R Fx = R(0), Fy = R(0), Fz = R(0);
+  // axis-class K0 = w (l+ (drho - 3/2 rho u.u) - 3 a+ u.F) and the vectors
+  // T = K1 u + a+/2 F, O = K2 u + a-/6 F (K1 = l+ rho / 4, K2 = l- rho / 6)
+  R K0a, Tx, Ty, Tz, Ox, Oy, Oz;
   if (DRAG) {
-    const R kd = recip(R(1) + half(s));
+    const R kd = recip(R(1) + halve(s));
     ux *= kd;
     uy *= kd;
     uz *= kd;
     const R rs = rho * s;
-    Fx = fma(-rs, ux, rho * c.g[0]);
-    Fy = fma(-rs, uy, rho * c.g[1]);
-    Fz = fma(-rs, uz, rho * c.g[2]);
-  }
-  const R uuv = DRAG ? fma(ux, ux, fma(uy, uy, uz * uz)) : uu;
-  const R base = fma(-1.5f * rho, uuv, drho);  // drho - 3/2 rho u.u
-  R K0a;                                      // axis-class K0 = w (l+ base - 3 a+ u.F)
-  R Fsx = R(0), Fsy = R(0), Fsz = R(0), Fox = R(0), Foy = R(0), Foz = R(0);
-  if (DRAG) {
+    const R Fx = fma(-rs, ux, rho * c.g[0]);
+    const R Fy = fma(-rs, uy, rho * c.g[1]);
+    const R Fz = fma(-rs, uz, rho * c.g[2]);
+    const R uu = fma(ux, ux, fma(uy, uy, uz * uz));
     const R uF = fma(ux, Fx, fma(uy, Fy, uz * Fz));
-    K0a = fma(c.k0a, base, -c.k0b * uF);
-    Fsx = c.fs * Fx;
-    Fsy = c.fs * Fy;
-    Fsz = c.fs * Fz;
-    Fox = c.fo * Fx;
-    Foy = c.fo * Fy;
-    Foz = c.fo * Fz;
+    K0a = fma(-rho, c.k0a15 * uu, fma(c.k0a, drho, -c.k0b * uF));
+    const R K1a = c.k1 * rho, K2a = c.k2 * rho;
+    Tx = fma(K1a, ux, c.fs * Fx);
+    Ty = fma(K1a, uy, c.fs * Fy);
+    Tz = fma(K1a, uz, c.fs * Fz);
+    Ox = fma(K2a, ux, c.fo * Fx);
+    Oy = fma(K2a, uy, c.fo * Fy);
+    Oz = fma(K2a, uz, c.fo * Fz);
+  } else if (FORCE) {
+    // uniform body force F = rho g
+    const R uu = fma(ux, ux, fma(uy, uy, uz * uz));
+    if (std::is_same<R, double>::value && c.gx) {
+      // the usual case of a force along the flow axis x: four FP64
+      // instructions fewer (uniform branch, taken by every thread or none)
+      K0a = fma(-rho, fma(c.k0a15, uu, c.k0b * (ux * c.g[0])), c.k0a * drho);
+      const R K1a = c.k1 * rho, K2a = c.k2 * rho;
+      Tx = rho * fma(c.k1, ux, c.gsv[0]);
+      Ty = K1a * uy;
+      Tz = K1a * uz;
+      Ox = rho * fma(c.k2, ux, c.gov[0]);
+      Oy = K2a * uy;
+      Oz = K2a * uz;
+    } else {
+      const R ug = fma(ux, c.g[0], fma(uy, c.g[1], uz * c.g[2]));
+      K0a = fma(-rho, fma(c.k0a15, uu, c.k0b * ug), c.k0a * drho);
+      Tx = rho * fma(c.k1, ux, c.gsv[0]);
+      Ty = rho * fma(c.k1, uy, c.gsv[1]);
+      Tz = rho * fma(c.k1, uz, c.gsv[2]);
+      Ox = rho * fma(c.k2, ux, c.gov[0]);
+      Oy = rho * fma(c.k2, uy, c.gov[1]);
+      Oz = rho * fma(c.k2, uz, c.gov[2]);
+    }
   } else {
-    K0a = c.k0a * base;
+    const R uu = fma(ux, ux, fma(uy, uy, uz * uz));
+    K0a = fma(-rho * c.k0a15, uu, c.k0a * drho);
+    const R K1a = c.k1 * rho, K2a = c.k2 * rho;
+    Tx = K1a * ux;
+    Ty = K1a * uy;
+    Tz = K1a * uz;
+    Ox = K2a * ux;
+    Oy = K2a * uy;
+    Oz = K2a * uz;
   }
-  const R K1a = c.k1 * rho, K2a = c.k2 * rho;
-  const R K0b = half(K0a), K1b = half(K1a), K2b = half(K2a);
-  constexpr bool F = DRAG;
   // axis pairs (weight 1/18)
-  coll_pair<R, F, 1, LP1>(d, sa[1], da[1], ux, uy, uz, K0a, K1a, K2a, Fsx, Fsy, Fsz, Fox, Foy, Foz, c.qp, c.qm);
-  coll_pair<R, F, 2, LP1>(d, sa[2], da[2], ux, uy, uz, K0a, K1a, K2a, Fsx, Fsy, Fsz, Fox, Foy, Foz, c.qp, c.qm);
-  coll_pair<R, F, 3, LP1>(d, sa[3], da[3], ux, uy, uz, K0a, K1a, K2a, Fsx, Fsy, Fsz, Fox, Foy, Foz, c.qp, c.qm);
+  coll_pair<R, 1, LP1>(d, sa[1], da[1], ux, uy, uz, K0a, Tx, Ty, Tz, Ox, Oy, Oz, c.qp, c.qm);
+  coll_pair<R, 2, LP1>(d, sa[2], da[2], ux, uy, uz, K0a, Tx, Ty, Tz, Ox, Oy, Oz, c.qp, c.qm);
+  coll_pair<R, 3, LP1>(d, sa[3], da[3], ux, uy, uz, K0a, Tx, Ty, Tz, Ox, Oy, Oz, c.qp, c.qm);
   // diagonal pairs (weight 1/36): every class constant halves
-  const R hFsx = half(Fsx), hFsy = half(Fsy), hFsz = half(Fsz);
-  const R hFox = half(Fox), hFoy = half(Foy), hFoz = half(Foz);
-  coll_pair<R, F, 4, LP1>(d, sa[4], da[4], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
-  coll_pair<R, F, 5, LP1>(d, sa[5], da[5], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
-  coll_pair<R, F, 6, LP1>(d, sa[6], da[6], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
-  coll_pair<R, F, 7, LP1>(d, sa[7], da[7], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
-  coll_pair<R, F, 8, LP1>(d, sa[8], da[8], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
-  coll_pair<R, F, 9, LP1>(d, sa[9], da[9], ux, uy, uz, K0b, K1b, K2b, hFsx, hFsy, hFsz, hFox, hFoy, hFoz, c.qp, c.qm);
+  const R K0b = halve(K0a);
+  const R hTx = halve(Tx), hTy = halve(Ty), hTz = halve(Tz);
+  const R hOx = halve(Ox), hOy = halve(Oy), hOz = halve(Oz);
+  coll_pair<R, 4, LP1>(d, sa[4], da[4], ux, uy, uz, K0b, hTx, hTy, hTz, hOx, hOy, hOz, c.qp, c.qm);
+  coll_pair<R, 5, LP1>(d, sa[5], da[5], ux, uy, uz, K0b, hTx, hTy, hTz, hOx, hOy, hOz, c.qp, c.qm);
+  coll_pair<R, 6, LP1>(d, sa[6], da[6], ux, uy, uz, K0b, hTx, hTy, hTz, hOx, hOy, hOz, c.qp, c.qm);
+  coll_pair<R, 7, LP1>(d, sa[7], da[7], ux, uy, uz, K0b, hTx, hTy, hTz, hOx, hOy, hOz, c.qp, c.qm);
+  coll_pair<R, 8, LP1>(d, sa[8], da[8], ux, uy, uz, K0b, hTx, hTy, hTz, hOx, hOy, hOz, c.qp, c.qm);
+  coll_pair<R, 9, LP1>(d, sa[9], da[9], ux, uy, uz, K0b, hTx, hTy, hTz, hOx, hOy, hOz, c.qp, c.qm);
   // rest PDF: p0 = (1 - l+) d0 + w0 (l+ base - 3 a+ u.F), w0 = 6 w_axis
   d[0] = LP1 ? 6.0f * K0a : fma(c.omlp, d[0], 6.0f * K0a);
 }

@@ -172,16 +172,18 @@ def test_config1_200_steps_parity():
 @pytest.mark.parametrize("case", range(4))
 @pytest.mark.parametrize("prec", ["f64", "f64df"])
 @pytest.mark.parametrize("form,ria", [("osnt", True), ("aa", False), ("aa", True), ("et", False)])
-def test_unit_omega_fast_path(case, prec, form, ria):
+@pytest.mark.parametrize("g", [(1e-4, 2e-5, -3e-5), (1e-4, 0.0, 0.0)])
+def test_unit_omega_fast_path(case, prec, form, ria, g):
     """omega+ = 1 selects the l+ = 1 collision of the FP64-storage kernels (the even-part
     products with (1 - l+)/2 = 0 are skipped): parity 1e-12 with every boundary kind, with
-    and without drag, and a perturbed (non-equilibrium) state."""
+    and without drag, and a perturbed (non-equilibrium) state.  A force along x alone takes
+    the FP64 collision's shorter branch."""
     kind, periodic, xp, enum, B, drag = CASES[case]
     solid = _geometry(kind, 300 + case)
     T = otables.Tables(solid, periodic=periodic, x_pressure=xp, enum=enum, B=B)
     lat = lbm.Lattice(solid, periodic=periodic, x_pressure=xp, enum=enum, B=B).upload(
         lbm.LBM_TABLES_ADJ | lbm.LBM_TABLES_RIA | lbm.LBM_TABLES_ET)
-    op, lp = _params(omega=1.0, rho_in=1.002 if xp else 1.0, rho_out=0.998 if xp else 1.0)
+    op, lp = _params(g=g, omega=1.0, rho_in=1.002 if xp else 1.0, rho_out=0.998 if xp else 1.0)
     s = torch.as_tensor(geometry.uniform_field(T.N, 40 + case), dtype=torch.float64) * 0.5 if drag else None
     F0 = _state(T.N, 50 + case)
     ref = _run_oracle(T, F0, op, 12, None if s is None else s.to(torch.float32).to(torch.float64), "osnt")
