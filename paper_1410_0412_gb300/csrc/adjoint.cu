@@ -29,6 +29,13 @@ template <class R> struct AdjConst {
   R rho_s;
   R w[3];            // D3Q19 weights 1/3, 1/18, 1/36
   R omlp;            // 1 - l+
+  // integer multiples of the rates, folded once on the host
+  R k45lp, k9lp, nk3lp;     // 9/2 l+, 9 l+, -3 l+
+  R k3lm;                   // 3 l-
+  R k9ap, nk3ap, nk9ap;     // 9 a+, -3 a+, -9 a+
+  R nk18ap, k6ap;           // -18 a+, 6 a+
+  R k3am, nk3am;            // 3 a-, -3 a-
+  bool gx;                  // the body force points along x (g_y = g_z = 0)
 };
 
 // Storage of the adjoint arrays: IEEE double for both FP64 paths (the
@@ -69,12 +76,90 @@ template <class R> AdjConst<R> make_adj(const KParams& kp) {
     c.hg[a] = R(kp.g[a] / 2);
   }
   c.rho_s = R(kp.rho_s);
+  const double ap = 1.0 - kp.lp / 2, am = 1.0 - kp.lm / 2;
+  c.k45lp = R(4.5 * kp.lp);
+  c.k9lp = R(9.0 * kp.lp);
+  c.nk3lp = R(-3.0 * kp.lp);
+  c.k3lm = R(3.0 * kp.lm);
+  c.k9ap = R(9.0 * ap);
+  c.nk3ap = R(-3.0 * ap);
+  c.nk9ap = R(-9.0 * ap);
+  c.nk18ap = R(-18.0 * ap);
+  c.k6ap = R(6.0 * ap);
+  c.k3am = R(3.0 * am);
+  c.nk3am = R(-3.0 * am);
+  c.gx = kp.g[1] == 0.0 && kp.g[2] == 0.0;
   return c;
+}
+
+// Pair sums P_k = mu_a + mu_b and differences D_k = mu_a - mu_b of the adjoint
+// vector and its weighted moments M0 = sum w mu, M1 = sum w c mu and
+// M2 = sum w c c^T mu.  The diagonal weight w2 = 1/36 is half the axis weight,
+// so each moment is w2 times an integer-coefficient sum of P_k or D_k (plus
+// w0 mu_0 for M0).  FP64 forms those sums exactly in fixed point on the
+// integer pipe (exact64.cuh) and rounds each once; P_k is converted only when
+// the caller needs it (l+ != 1).
+template <class R, bool NEED_P>
+__device__ __forceinline__ void adj_moments(const R (&mu)[kQ], const AdjConst<R>& c, R (&P)[10], R (&D)[10], R& M0,
+                                            R& M1x, R& M1y, R& M1z, R& Mxx, R& Myy, R& Mzz, R& Mxy, R& Mxz,
+                                            R& Myz) {
+  using ::fma;
+  const R w2 = c.w[2];
+  if constexpr (std::is_same<R, double>::value) {
+    uint64_t b[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) b[i] = dbits(mu[i]);
+    const int emax = fx_scale(b);
+    int64_t f[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) f[i] = fx_of(b[i], emax);
+    int64_t Pi[10], Di[10];
+#pragma unroll
+    for (int k = 1; k <= 9; ++k) {
+      Pi[k] = f[2 * k - 1] + f[2 * k];
+      Di[k] = f[2 * k - 1] - f[2 * k];
+      if (NEED_P) P[k] = fx_to_double(Pi[k], emax);
+      D[k] = fx_to_double(Di[k], emax);
+    }
+    // every integer sum below has at most 24 terms of magnitude < 2^58
+    const int64_t A1 = Pi[1] + Pi[2] + Pi[3];
+    const int64_t A2 = Pi[4] + Pi[5] + Pi[6] + Pi[7] + Pi[8] + Pi[9];
+    M0 = fma(c.w[0], mu[0], w2 * fx_to_double(2 * A1 + A2, emax));
+    if (emax >= kFxMaxExp) M0 = dfrom(0x7ff8000000000000ull);
+    M1x = w2 * fx_to_double(2 * Di[1] + Di[4] + Di[5] + Di[6] + Di[7], emax);
+    M1y = w2 * fx_to_double(2 * Di[2] + Di[4] - Di[5] + Di[8] + Di[9], emax);
+    M1z = w2 * fx_to_double(2 * Di[3] + Di[6] - Di[7] + Di[8] - Di[9], emax);
+    Mxx = w2 * fx_to_double(2 * Pi[1] + Pi[4] + Pi[5] + Pi[6] + Pi[7], emax);
+    Myy = w2 * fx_to_double(2 * Pi[2] + Pi[4] + Pi[5] + Pi[8] + Pi[9], emax);
+    Mzz = w2 * fx_to_double(2 * Pi[3] + Pi[6] + Pi[7] + Pi[8] + Pi[9], emax);
+    Mxy = w2 * fx_to_double(Pi[4] - Pi[5], emax);
+    Mxz = w2 * fx_to_double(Pi[6] - Pi[7], emax);
+    Myz = w2 * fx_to_double(Pi[8] - Pi[9], emax);
+  } else {
+#pragma unroll
+    for (int k = 1; k <= 9; ++k) {
+      P[k] = mu[2 * k - 1] + mu[2 * k];
+      D[k] = mu[2 * k - 1] - mu[2 * k];
+    }
+    const R A1 = P[1] + P[2] + P[3];
+    const R A2 = (P[4] + P[5]) + (P[6] + P[7]) + (P[8] + P[9]);
+    M0 = fma(c.w[0], mu[0], w2 * (A1 + A1 + A2));
+    M1x = w2 * ((D[1] + D[1]) + ((D[4] + D[5]) + (D[6] + D[7])));
+    M1y = w2 * ((D[2] + D[2]) + ((D[4] - D[5]) + (D[8] + D[9])));
+    M1z = w2 * ((D[3] + D[3]) + ((D[6] - D[7]) + (D[8] - D[9])));
+    Mxx = w2 * ((P[1] + P[1]) + ((P[4] + P[5]) + (P[6] + P[7])));
+    Myy = w2 * ((P[2] + P[2]) + ((P[4] + P[5]) + (P[8] + P[9])));
+    Mzz = w2 * ((P[3] + P[3]) + ((P[6] + P[7]) + (P[8] + P[9])));
+    Mxy = w2 * (P[4] - P[5]);
+    Mxz = w2 * (P[6] - P[7]);
+    Myz = w2 * (P[8] - P[9]);
+  }
 }
 
 // One adjoint step.  G: OS-NT grid at step n (its pull gather is F_n).
 // lam_next / lam: adjoint of the canonical states F_{n+1} / F_n, layout [19][Npad].
-template <int PREC, bool RIA, bool DRAG>
+// LP1: l+ = 1 (FP64-storage paths), where (1 - l+)/2 = 1 - l+ = 0.
+template <int PREC, bool RIA, bool DRAG, bool LP1 = false>
 __global__ void __launch_bounds__(kBlock) k_adjoint(DevTables t, KParams kp, CollConst<typename St<PREC>::R> cc,
                                                     AdjConst<typename St<PREC>::R> c,
                                                     const typename St<PREC>::T* __restrict__ G,
@@ -95,19 +180,18 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(DevTables t, KParams kp, Col
   // forward quantities of F_n
   R d[kQ];
   gather<PREC, false>(G, t.npad, n, m, d, kp.inv_scale, cc, t.pressure);
-  R drho = d[0], jx = R(0), jy = R(0), jz = R(0);
-#pragma unroll
-  for (int i = 1; i < kQ; ++i) {
-    drho += d[i];
-    if (cx(i)) jx += cx(i) > 0 ? d[i] : -d[i];
-    if (cy(i)) jy += cy(i) > 0 ? d[i] : -d[i];
-    if (cz(i)) jz += cz(i) > 0 ? d[i] : -d[i];
-  }
+  R sa[10], da[10], drho, jx, jy, jz;
+  moments<R, false>(d, sa, da, drho, jx, jy, jz);
   const R rho = c.rho_s + drho;
   const R irho = recip(rho);
   const R sn = DRAG ? R(__ldg(s + n)) : R(0);
-  const R kd = DRAG ? recip(R(1) + half(sn)) : R(1);
-  const R ux = fma(jx, irho, c.hg[0]) * kd, uy = fma(jy, irho, c.hg[1]) * kd, uz = fma(jz, irho, c.hg[2]) * kd;
+  const R kd = DRAG ? recip(R(1) + halve(sn)) : R(1);
+  R ux = fma(jx, irho, c.hg[0]), uy = fma(jy, irho, c.hg[1]), uz = fma(jz, irho, c.hg[2]);
+  if (DRAG) {
+    ux *= kd;
+    uy *= kd;
+    uz *= kd;
+  }
   // mu = S^T lambda_{n+1}: slot (j, n) of the post-collision state is pulled by
   // node m_{inv j} (fluid) or, through a marker, by this node's inv j slot
   // (sign -1 for anti-bounce-back).
@@ -121,71 +205,69 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(DevTables t, KParams kp, Col
     const R v = L::ld(lam_next + at(dir, t.npad, node));
     mu[j] = mp < -1 ? -v : v;
   }
-  // weighted moments of mu (pairs: even part for M0/M2, odd part for M1)
-  R M0 = c.w[0] * mu[0];
-  R M1x = R(0), M1y = R(0), M1z = R(0);
-  R Mxx = R(0), Myy = R(0), Mzz = R(0), Mxy = R(0), Mxz = R(0), Myz = R(0);
-#pragma unroll
-  for (int k = 1; k <= 9; ++k) {
-    const int a = 2 * k - 1;
-    const R w = c.w[wclass(a)];
-    const R sp = w * (mu[a] + mu[a + 1]);
-    const R sm = w * (mu[a] - mu[a + 1]);
-    M0 += sp;
-    if (cx(a)) M1x += cx(a) > 0 ? sm : -sm;
-    if (cy(a)) M1y += cy(a) > 0 ? sm : -sm;
-    if (cz(a)) M1z += cz(a) > 0 ? sm : -sm;
-    if (cx(a)) Mxx += sp;
-    if (cy(a)) Myy += sp;
-    if (cz(a)) Mzz += sp;
-    if (cx(a) && cy(a)) Mxy += cx(a) * cy(a) > 0 ? sp : -sp;
-    if (cx(a) && cz(a)) Mxz += cx(a) * cz(a) > 0 ? sp : -sp;
-    if (cy(a) && cz(a)) Myz += cy(a) * cz(a) > 0 ? sp : -sp;
-  }
+  R P[10], D[10], M0, M1x, M1y, M1z, Mxx, Myy, Mzz, Mxy, Mxz, Myz;
+  adj_moments<R, !LP1>(mu, c, P, D, M0, M1x, M1y, M1z, Mxx, Myy, Mzz, Mxy, Mxz, Myz);
   const R M2ux = fma(Mxx, ux, fma(Mxy, uy, Mxz * uz));
   const R M2uy = fma(Mxy, ux, fma(Myy, uy, Myz * uz));
   const R M2uz = fma(Mxz, ux, fma(Myz, uy, Mzz * uz));
-  const R M2gx = fma(Mxx, c.g[0], fma(Mxy, c.g[1], Mxz * c.g[2]));
-  const R M2gy = fma(Mxy, c.g[0], fma(Myy, c.g[1], Myz * c.g[2]));
-  const R M2gz = fma(Mxz, c.g[0], fma(Myz, c.g[1], Mzz * c.g[2]));
   const R uu = fma(ux, ux, fma(uy, uy, uz * uz));
   const R q = fma(ux, M2ux, fma(uy, M2uy, uz * M2uz));
   const R av = fma(M1x, ux, fma(M1y, uy, M1z * uz));
-  const R ug = fma(ux, c.g[0], fma(uy, c.g[1], uz * c.g[2]));
-  const R uM2g = fma(ux, M2gx, fma(uy, M2gy, uz * M2gz));
-  const R M1g = fma(M1x, c.g[0], fma(M1y, c.g[1], M1z * c.g[2]));
-  const R lp = c.lp, lm = c.lm, ap = c.ap, am = c.am;
-  const R lpM0 = lp * M0, apM0 = ap * M0;
-  // Psi and dPsi/du (see the header comment)
-  R Psi = lpM0 * fma(-1.5f * uu, R(1), R(1)) + 4.5f * (lp * q) + 3.0f * (lm * av) + 9.0f * (ap * uM2g) -
-          3.0f * (apM0 * ug) + 3.0f * (am * M1g);
-  R Px = -3.0f * (lpM0 * ux) + 9.0f * (lp * M2ux) + 3.0f * (lm * M1x) + 9.0f * (ap * M2gx) - 3.0f * (apM0 * c.g[0]);
-  R Py = -3.0f * (lpM0 * uy) + 9.0f * (lp * M2uy) + 3.0f * (lm * M1y) + 9.0f * (ap * M2gy) - 3.0f * (apM0 * c.g[1]);
-  R Pz = -3.0f * (lpM0 * uz) + 9.0f * (lp * M2uz) + 3.0f * (lm * M1z) + 9.0f * (ap * M2gz) - 3.0f * (apM0 * c.g[2]);
-  const R dPsi_ds = -9.0f * (ap * q) + 3.0f * (apM0 * uu) - 3.0f * (am * av);
-  if (DRAG) {
-    Psi += sn * dPsi_ds;
-    Px += sn * (-18.0f * (ap * M2ux) + 6.0f * (apM0 * ux) - 3.0f * (am * M1x));
-    Py += sn * (-18.0f * (ap * M2uy) + 6.0f * (apM0 * uy) - 3.0f * (am * M1y));
-    Pz += sn * (-18.0f * (ap * M2uz) + 6.0f * (apM0 * uz) - 3.0f * (am * M1z));
+  const R apM0 = c.ap * M0;
+  const R nk3lpM0 = c.nk3lp * M0, nk3apM0 = c.nk3ap * M0;  // -3 l+ M0, -3 a+ M0
+  // the force terms: M2 g, u.g, u.M2 g, M1.g and -3 a+ M0 g
+  R M2gx, M2gy, M2gz, ug, M1g, Gx, Gy, Gz;
+  if (std::is_same<R, double>::value && c.gx) {  // uniform: a force along x alone
+    M2gx = Mxx * c.g[0];
+    M2gy = Mxy * c.g[0];
+    M2gz = Mxz * c.g[0];
+    ug = ux * c.g[0];
+    M1g = M1x * c.g[0];
+    Gx = nk3apM0 * c.g[0];
+    Gy = R(0);
+    Gz = R(0);
+  } else {
+    M2gx = fma(Mxx, c.g[0], fma(Mxy, c.g[1], Mxz * c.g[2]));
+    M2gy = fma(Mxy, c.g[0], fma(Myy, c.g[1], Myz * c.g[2]));
+    M2gz = fma(Mxz, c.g[0], fma(Myz, c.g[1], Mzz * c.g[2]));
+    ug = fma(ux, c.g[0], fma(uy, c.g[1], uz * c.g[2]));
+    M1g = fma(M1x, c.g[0], fma(M1y, c.g[1], M1z * c.g[2]));
+    Gx = nk3apM0 * c.g[0];
+    Gy = nk3apM0 * c.g[1];
+    Gz = nk3apM0 * c.g[2];
   }
-  const R A = Psi - (Px * (ux - kd * c.hg[0]) + Py * (uy - kd * c.hg[1]) + Pz * (uz - kd * c.hg[2]));
+  const R uM2g = fma(ux, M2gx, fma(uy, M2gy, uz * M2gz));
+  // Psi and dPsi/du (see the header comment)
+  R Psi = fma(c.lp * M0, fma(R(-1.5f), uu, R(1)),
+              fma(c.k45lp, q, fma(c.k3lm, av, fma(c.k9ap, uM2g, fma(c.k3am, M1g, nk3apM0 * ug)))));
+  R Px = fma(nk3lpM0, ux, fma(c.k9lp, M2ux, fma(c.k3lm, M1x, fma(c.k9ap, M2gx, Gx))));
+  R Py = fma(nk3lpM0, uy, fma(c.k9lp, M2uy, fma(c.k3lm, M1y, fma(c.k9ap, M2gy, Gy))));
+  R Pz = fma(nk3lpM0, uz, fma(c.k9lp, M2uz, fma(c.k3lm, M1z, fma(c.k9ap, M2gz, Gz))));
+  const R dPsi_ds = fma(c.nk9ap, q, fma(R(3), apM0 * uu, c.nk3am * av));
+  if (DRAG) {
+    Psi = fma(sn, dPsi_ds, Psi);
+    const R k6apM0 = c.k6ap * M0;
+    Px = fma(sn, fma(c.nk18ap, M2ux, fma(k6apM0, ux, c.nk3am * M1x)), Px);
+    Py = fma(sn, fma(c.nk18ap, M2uy, fma(k6apM0, uy, c.nk3am * M1y)), Py);
+    Pz = fma(sn, fma(c.nk18ap, M2uz, fma(k6apM0, uz, c.nk3am * M1z)), Pz);
+  }
+  // A = Psi - P.(u - kd g/2)
+  const R A = fma(-Px, fma(-kd, c.hg[0], ux), fma(-Py, fma(-kd, c.hg[1], uy), fma(-Pz, fma(-kd, c.hg[2], uz), Psi)));
   const R Bx = kd * Px, By = kd * Py, Bz = kd * Pz;
   if (grad_s) {
-    const R gs = rho * (dPsi_ds - half(kd) * (Px * ux + Py * uy + Pz * uz));
+    const R Pu = fma(Px, ux, fma(Py, uy, Pz * uz));
+    const R gs = rho * fma(-halve(kd), Pu, dPsi_ds);
     grad_s[n] += L::to_double(gs);
   }
-  L::st(lam + n, fma(c.omlp, mu[0], A));
+  L::st(lam + n, LP1 ? A : fma(c.omlp, mu[0], A));
 #pragma unroll
   for (int k = 1; k <= 9; ++k) {
     const int a = 2 * k - 1;
-    const R sp = mu[a] + mu[a + 1], sm = mu[a] - mu[a + 1];
-    R Bc = R(0);
-    if (cx(a)) Bc += cx(a) > 0 ? Bx : -Bx;
-    if (cy(a)) Bc += cy(a) > 0 ? By : -By;
-    if (cz(a)) Bc += cz(a) > 0 ? Bz : -Bz;
-    const R e = fma(c.qp, sp, A);
-    const R o = fma(c.qm, sm, Bc);
+    // c_a . B for the pair's first direction (the loop is unrolled: k is a constant)
+    const R Bc = k == 1 ? Bx : k == 2 ? By : k == 3 ? Bz : k == 4 ? Bx + By : k == 5 ? Bx - By
+               : k == 6 ? Bx + Bz : k == 7 ? Bx - Bz : k == 8 ? By + Bz : By - Bz;
+    const R e = LP1 ? A : fma(c.qp, P[k], A);
+    const R o = fma(c.qm, D[k], Bc);
     L::st(lam + at(a, t.npad, n), e + o);
     L::st(lam + at(a + 1, t.npad, n), e - o);
   }
@@ -295,7 +377,8 @@ int launch_adjoint_t(const lbm_lattice* L, const KParams& kp, const void* G, con
   const LT* ln = static_cast<const LT*>(lam_next);
   LT* lo = static_cast<LT*>(lam);
   const int N = int(L->N);
-#define LBM_ADJ(R_, D_) dev::k_adjoint<PREC, R_, D_><<<g, dev::kBlock, 0, st>>>(L->dev, kp, cc, ac, Gp, ln, lo, s, grad_s, N)
+  const bool lp1 = use_lp1<PREC>(kp);
+#define LBM_ADJ(R_, D_) LBM_LAUNCH_LP1(k_adjoint, LBM_TARGS2(R_, D_), (L->dev, kp, cc, ac, Gp, ln, lo, s, grad_s, N))
   if (s) {
     if (ria) LBM_ADJ(true, true); else LBM_ADJ(false, true);
   } else {

@@ -439,6 +439,12 @@ __device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const
   d[0] = LP1 ? 6.0f * K0a : fma(c.omlp, d[0], 6.0f * K0a);
 }
 
+// True for every thread of the warp when any active thread has `flag`: the
+// anti-bounce-back work of pressure faces becomes a warp-uniform branch that
+// warps away from the faces skip, instead of predicated arithmetic that every
+// node would issue.
+__device__ __forceinline__ bool warp_any(bool flag) { return __any_sync(__activemask(), flag); }
+
 // ---- PDF gathers of the storage layouts ----------------------------------------------
 // Pull of f_i at node n with adjacency entry m:
 //   OS-NT grid (post-collision P):   P[i][m]      | marker: P[inv i][n]
@@ -458,10 +464,15 @@ __device__ __forceinline__ void gather(const typename St<PREC>::T* g, uint32_t n
     d[i] = SC ? ld_step<PREC>(g + at(dir, npad, node), inv_scale) : St<PREC>::ld(g + at(dir, npad, node), inv_scale);
   }
   if (pressure) {  // uniform: only lattices with pressure faces pay for the check
+    bool face = false;
 #pragma unroll
-    for (int i = 1; i < kQ; ++i) {
-      const int mi = m[i - 1];
-      if (mi < -1) d[i] = (mi == LBM_MARK_INLET ? c.abb_in[wclass(i) - 1] : c.abb_out[wclass(i) - 1]) - d[i];
+    for (int i = 1; i < kQ; ++i) face |= m[i - 1] < -1;
+    if (warp_any(face)) {
+#pragma unroll
+      for (int i = 1; i < kQ; ++i) {
+        const int mi = m[i - 1];
+        if (mi < -1) d[i] = (mi == LBM_MARK_INLET ? c.abb_in[wclass(i) - 1] : c.abb_out[wclass(i) - 1]) - d[i];
+      }
     }
   }
 }
@@ -585,7 +596,12 @@ __global__ void __launch_bounds__(kBlock, MinCtasOdd<PREC, RIA>::value) k_aa_odd
   int mo_[18];
 #pragma unroll
   for (int j = 0; j < 18; ++j) mo_[j] = kStash ? s_m[j][threadIdx.x] : nbr_again<RIA>(t, cur, n, j);
+  bool face = false;
   if (t.pressure) {
+#pragma unroll
+    for (int j = 0; j < 18; ++j) face |= mo_[j] < -1;
+  }
+  if (t.pressure && warp_any(face)) {
 #pragma unroll
     for (int i = 1; i < kQ; ++i) {
       const int mo = mo_[inv(i) - 1];
@@ -688,13 +704,19 @@ __global__ void __launch_bounds__(kBlock, MinCtasEt<PREC>::value) k_et(DevTables
     for (int k = 1; k < 7; ++k) loc[k] = s_loc[k - 1][threadIdx.x];
     mask = unsigned(s_loc[6][threadIdx.x]);
   }
+  // bits 18..27 of the mask: pull directions that meet a pressure face.  The
+  // FP64 path branches per warp around the anti-bounce-back arithmetic; the
+  // others keep one predicated loop (fewer registers, cheap arithmetic).
+  constexpr bool kF64 = std::is_same<R, double>::value;
+  bool face = false;
+  if constexpr (kF64) face = t.pressure && warp_any((mask >> 18) != 0u);
 #pragma unroll
   for (int j = 1; j < kQ; ++j) {
     const int jj = inv(j);
     const bool link = !((mask >> (jj - 1)) & 1u);
     R v = d[j];
     if (cx(jj) != 0) {
-      if (t.pressure && ((mask >> et_xbit(jj)) & 1u))
+      if ((kF64 ? face : t.pressure != 0) && ((mask >> et_xbit(jj)) & 1u))
         v = (cx(jj) > 0 ? c.abb_in[wclass(j) - 1] : c.abb_out[wclass(j) - 1]) - v;
     }
     st_step<PREC>(A + at(link != ODD ? jj : j, t.spad, loc[et_row(j) + 1]), v, kp.scale);
