@@ -143,23 +143,6 @@ __device__ __forceinline__ RiaCursor ria_locate(const DevTables& t, int n) {
   return ria_locate_in(t.head_bits, t.warp_run0, t.warp_head0, n);
 }
 
-// One table entry read again after the collision (the volatile load is never
-// merged with the first read; it hits L1).
-__device__ __forceinline__ int ld_index_again(const int32_t* p) {
-  int v;
-  asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(p));
-  return v;
-}
-
-template <bool RIA>
-__device__ __forceinline__ int nbr_again(const DevTables& t, RiaCursor c, int n, int i) {
-  if (RIA) {
-    const int a = ld_index_again(t.run_adj + at(i, t.rpad, c.r));
-    return a >= 0 ? a + c.off : a;
-  }
-  return ld_index_again(t.adj + at(i, t.npad, n));
-}
-
 __device__ __forceinline__ void nbr_ria(const DevTables& t, RiaCursor c, int (&m)[18]) {
 #pragma unroll
   for (int i = 0; i < 18; ++i) {
@@ -564,38 +547,33 @@ __global__ void __launch_bounds__(kBlock, MinCtasOdd<PREC, RIA>::value) k_aa_odd
                                                                               typename St<PREC>::T* __restrict__ A,
                                                                               const float* __restrict__ s, int N) {
   using R = typename St<PREC>::R;
-  // The 18 resolved entries must survive the collision.  FP32 and the FP64
-  // paths park them in shared memory ([18][kBlock], lane-consecutive,
-  // conflict-free); the FP16 path, short of registers already, reads them
-  // again from L1 after the collision (measured faster for each on GB300).
-  constexpr bool kStash = PREC != LBM_F16S;
-  __shared__ int s_m[kStash ? 18 : 1][kBlock];
+  // The 18 resolved entries must survive the collision: they are parked in
+  // shared memory ([18][kBlock], lane-consecutive, conflict-free) rather than
+  // held in registers across it or read again from L1 after it (measured
+  // faster for every precision on GB300).
+  __shared__ int s_m[18][kBlock];
   const int n = blockIdx.x * kBlock + threadIdx.x;
   if (n >= N) return;
   R d[kQ];
-  RiaCursor cur{0, 0};
   {
     int m[18];
     if (RIA) {
-      cur = ria_locate(t, n);
-      nbr_ria(t, cur, m);
+      nbr_ria(t, ria_locate(t, n), m);
     } else {
       nbr_adj(t, n, m);
     }
-    if (kStash) {
 #pragma unroll
-      for (int j = 0; j < 18; ++j) s_m[j][threadIdx.x] = m[j];
-    }
+    for (int j = 0; j < 18; ++j) s_m[j][threadIdx.x] = m[j];
     gather<PREC, true, kScaled<PREC>>(A, t.npad, n, m, d, kp.inv_scale, c, t.pressure);
   }
   const R sn = DRAG ? R(__ldg(s + n)) : R(0);
   collide<R, FORCE, DRAG, LP1, kScaled<PREC>>(d, c, sn);
   st_step<PREC>(A + n, d[0], kp.scale);
   // p_i goes to the slot node m_{inv i} pulls it from next (or, through a
-  // marker, to this node's own opposite slot); re-reads are issued first
+  // marker, to this node's own opposite slot)
   int mo_[18];
 #pragma unroll
-  for (int j = 0; j < 18; ++j) mo_[j] = kStash ? s_m[j][threadIdx.x] : nbr_again<RIA>(t, cur, n, j);
+  for (int j = 0; j < 18; ++j) mo_[j] = s_m[j][threadIdx.x];
   bool face = false;
   if (t.pressure) {
 #pragma unroll
