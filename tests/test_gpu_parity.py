@@ -255,17 +255,20 @@ def test_missing_tables_and_bad_arguments():
         lbm.lbm_step_aa(lat, "f16s", lbm.Params(shifted=False), lat.new_grid("f16s"), 0)
 
 
-def test_nonfinite_state_is_reported():
-    """A NaN planted in one PDF surfaces as LBM_ERR_NONFINITE from the FP64 sums guard."""
+@pytest.mark.parametrize("omega", [1.1, 1.0])
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+def test_nonfinite_state_is_reported(omega, bad):
+    """A NaN or Inf planted in one PDF surfaces as LBM_ERR_NONFINITE from the FP64 sums guard,
+    through the integer-pipe moments of the general and the l+ = 1 collision."""
     solid = geometry.random_voxels(12, 10, 8, 0.2, 3)
     lat = lbm.Lattice(solid, periodic=(1, 1, 1)).upload()
-    _, lp = _params()
+    _, lp = _params(omega=omega)
     solver = lbm.Solver(lat, "f64", lp, form="aa", ria=True)
     solver.init_equilibrium(1.0)
     solver.step(2)
     _, _, sums = solver.macroscopic(fields=False)
     lbm.lbm_check_finite(sums)
-    solver.pdf[7, lat.N // 2] = float("nan")
+    solver.pdf[7, lat.N // 2] = bad
     solver.step(2)
     _, _, sums = solver.macroscopic(fields=False)
     with pytest.raises(lbm.LbmError) as e:
