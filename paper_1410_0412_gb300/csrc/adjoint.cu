@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(DevTables t, KParams kp, Col
   }
   // forward quantities of F_n
   R d[kQ];
-  gather<PREC, false>(G, t.npad, n, m, d, kp.inv_scale, cc, t.pressure);
+  gather<PREC, false>(G, t.npad, n, m, d, kp.inv_scale, cc.abb_in, cc.abb_out, t.pressure);
   R sa[10], da[10], drho, jx, jy, jz;
   moments<R, false>(d, sa, da, drho, jx, jy, jz);
   const R rho = c.rho_s + drho;

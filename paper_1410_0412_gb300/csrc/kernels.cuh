@@ -174,6 +174,7 @@ template <class R> struct CollConst {
   R gsv[3], gov[3];  // axis-class S+ / S- force scales times g: fs g, fo g
   R rho_s;
   R abb_in[2], abb_out[2];  // 2 w (rho_bc - rho_s) for w = 1/18 and 1/36
+  double abb64_in[2], abb64_out[2];  // the same in double (the double-float odd step's FP64 gather)
   R inv_s;                  // 1 / storage scale of the scaled collision (see make_coll_step)
   bool gx;                  // the body force points along x (g_y = g_z = 0)
 };
@@ -207,6 +208,8 @@ template <class R> inline CollConst<R> make_coll(const KParams& kp) {
     const double w = k == 0 ? 1.0 / 18.0 : 1.0 / 36.0;
     c.abb_in[k] = R(2.0 * w * (kp.rho_in - kp.rho_s));
     c.abb_out[k] = R(2.0 * w * (kp.rho_out - kp.rho_s));
+    c.abb64_in[k] = 2.0 * w * (kp.rho_in - kp.rho_s);
+    c.abb64_out[k] = 2.0 * w * (kp.rho_out - kp.rho_s);
   }
   return c;
 }
@@ -302,9 +305,9 @@ __device__ __forceinline__ void coll_pair(R (&d)[kQ], const R sa, const R da, co
 // Pair sums sa_k = d_a + d_b and differences da_k = d_a - d_b, the density
 // deviation and the momentum.  FP64 takes them exactly on the integer pipe
 // (exact64.cuh), with sa converted only when the caller needs it (l+ != 1).
-template <class R, bool NEED_SA>
+template <class R, bool NEED_SA, bool IEEE = false>
 __device__ __forceinline__ void moments(const R (&d)[kQ], R (&sa)[10], R (&da)[10], R& drho, R& jx, R& jy, R& jz) {
-  if constexpr (std::is_same<R, double>::value) {
+  if constexpr (std::is_same<R, double>::value && !IEEE) {
     exact_moments<NEED_SA>(d, sa, da, drho, jx, jy, jz);
   } else {
 #pragma unroll
@@ -331,17 +334,12 @@ __device__ __forceinline__ df halve(df x) { return half(x); }
 // equilibrium, and the ten products with those zeros are skipped
 // (fma(0, x, e) = e, so the values are unchanged).
 // SC: the PDFs are in storage units (make_coll_step); rho and j are scaled back.
-template <class R, bool FORCE, bool DRAG, bool LP1 = false, bool SC = false>
-__device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const R s) {
+// collide_m: the collision from given moments (sa only read when !LP1; d[0]
+// only read when !LP1).
+template <class R, bool FORCE, bool DRAG, bool LP1 = false>
+__device__ __forceinline__ void collide_m(R (&d)[kQ], const CollConst<R>& c, const R s, const R (&sa)[10],
+                                          const R (&da)[10], const R drho, const R jx, const R jy, const R jz) {
   using ::fma;
-  R sa[10], da[10], drho, jx, jy, jz;
-  moments<R, !LP1>(d, sa, da, drho, jx, jy, jz);
-  if (SC) {  // storage units -> physical units for the moments
-    drho = drho * c.inv_s;
-    jx = jx * c.inv_s;
-    jy = jy * c.inv_s;
-    jz = jz * c.inv_s;
-  }
   const R rho = c.rho_s + drho;
   const R irho = recip(rho);
   R ux = fma(jx, irho, c.hg[0]);
@@ -422,6 +420,19 @@ __device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const
   d[0] = LP1 ? 6.0f * K0a : fma(c.omlp, d[0], 6.0f * K0a);
 }
 
+template <class R, bool FORCE, bool DRAG, bool LP1 = false, bool SC = false>
+__device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const R s) {
+  R sa[10], da[10], drho, jx, jy, jz;
+  moments<R, !LP1>(d, sa, da, drho, jx, jy, jz);
+  if (SC) {  // storage units -> physical units for the moments
+    drho = drho * c.inv_s;
+    jx = jx * c.inv_s;
+    jy = jy * c.inv_s;
+    jz = jz * c.inv_s;
+  }
+  collide_m<R, FORCE, DRAG, LP1>(d, c, s, sa, da, drho, jx, jy, jz);
+}
+
 // True for every thread of the warp when any active thread has `flag`: the
 // anti-bounce-back work of pressure faces becomes a warp-uniform branch that
 // warps away from the faces skip, instead of predicated arithmetic that every
@@ -437,7 +448,8 @@ __device__ __forceinline__ bool warp_any(bool flag) { return __any_sync(__active
 template <int PREC, bool AA_ODD, bool SC = false>
 __device__ __forceinline__ void gather(const typename St<PREC>::T* g, uint32_t npad, int n, const int (&m)[18],
                                        typename St<PREC>::R (&d)[kQ], float inv_scale,
-                                       const CollConst<typename St<PREC>::R>& c, int pressure) {
+                                       const typename St<PREC>::R (&abb_in)[2],
+                                       const typename St<PREC>::R (&abb_out)[2], int pressure) {
   d[0] = SC ? ld_step<PREC>(g + n, inv_scale) : St<PREC>::ld(g + n, inv_scale);
 #pragma unroll
   for (int i = 1; i < kQ; ++i) {
@@ -454,7 +466,7 @@ __device__ __forceinline__ void gather(const typename St<PREC>::T* g, uint32_t n
 #pragma unroll
       for (int i = 1; i < kQ; ++i) {
         const int mi = m[i - 1];
-        if (mi < -1) d[i] = (mi == LBM_MARK_INLET ? c.abb_in[wclass(i) - 1] : c.abb_out[wclass(i) - 1]) - d[i];
+        if (mi < -1) d[i] = (mi == LBM_MARK_INLET ? abb_in[wclass(i) - 1] : abb_out[wclass(i) - 1]) - d[i];
       }
     }
   }
@@ -480,7 +492,7 @@ __global__ void __launch_bounds__(kBlock, MinCtasOsnt<PREC, RIA>::value) k_osnt(
     nbr_adj(t, n, m);
   }
   R d[kQ];
-  gather<PREC, false, kScaled<PREC>>(src, t.npad, n, m, d, kp.inv_scale, c, t.pressure);
+  gather<PREC, false, kScaled<PREC>>(src, t.npad, n, m, d, kp.inv_scale, c.abb_in, c.abb_out, t.pressure);
   const R sn = DRAG ? R(__ldg(s + n)) : R(0);
   collide<R, FORCE, DRAG, LP1, kScaled<PREC>>(d, c, sn);
 #pragma unroll
@@ -564,10 +576,33 @@ __global__ void __launch_bounds__(kBlock, MinCtasOdd<PREC, RIA>::value) k_aa_odd
     }
 #pragma unroll
     for (int j = 0; j < 18; ++j) s_m[j][threadIdx.x] = m[j];
-    gather<PREC, true, kScaled<PREC>>(A, t.npad, n, m, d, kp.inv_scale, c, t.pressure);
+    if constexpr (PREC == LBM_F64_DF) {
+      // The double-float odd step leaves its FP64 pipe mostly idle: it takes
+      // the moments there, in IEEE double from the loaded doubles, and
+      // converts only those 13 (or 23) values to double-float.
+      double g64[kQ];
+      gather<LBM_F64, true>(reinterpret_cast<const double*>(A), t.npad, n, m, g64, kp.inv_scale, c.abb64_in,
+                            c.abb64_out, t.pressure);
+      double sa64[10], da64[10], drho64, jx64, jy64, jz64;
+      moments<double, !LP1, true>(g64, sa64, da64, drho64, jx64, jy64, jz64);
+      R sa[10], da[10];
+#pragma unroll
+      for (int k = 1; k <= 9; ++k) {
+        if (!LP1) sa[k] = df_from_double(sa64[k]);
+        da[k] = df_from_double(da64[k]);
+      }
+      if (!LP1) d[0] = df_from_double(g64[0]);
+      const R sn = DRAG ? R(__ldg(s + n)) : R(0);
+      collide_m<R, FORCE, DRAG, LP1>(d, c, sn, sa, da, df_from_double(drho64), df_from_double(jx64),
+                                     df_from_double(jy64), df_from_double(jz64));
+    } else {
+      gather<PREC, true, kScaled<PREC>>(A, t.npad, n, m, d, kp.inv_scale, c.abb_in, c.abb_out, t.pressure);
+    }
   }
-  const R sn = DRAG ? R(__ldg(s + n)) : R(0);
-  collide<R, FORCE, DRAG, LP1, kScaled<PREC>>(d, c, sn);
+  if constexpr (PREC != LBM_F64_DF) {
+    const R sn = DRAG ? R(__ldg(s + n)) : R(0);
+    collide<R, FORCE, DRAG, LP1, kScaled<PREC>>(d, c, sn);
+  }
   st_step<PREC>(A + n, d[0], kp.scale);
   // p_i goes to the slot node m_{inv i} pulls it from next (or, through a
   // marker, to this node's own opposite slot)
@@ -851,9 +886,9 @@ __device__ __forceinline__ bool node_canonical(const DevTables& t, const KParams
 #pragma unroll
     for (int i = 0; i < kQ; ++i) d[i] = St<PREC>::ld(pdf + at(i, t.npad, n), kp.inv_scale);
   } else if (layout == LBM_LAYOUT_OSNT) {
-    gather<PREC, false>(pdf, t.npad, n, m, d, kp.inv_scale, c, t.pressure);
+    gather<PREC, false>(pdf, t.npad, n, m, d, kp.inv_scale, c.abb_in, c.abb_out, t.pressure);
   } else {
-    gather<PREC, true>(pdf, t.npad, n, m, d, kp.inv_scale, c, t.pressure);
+    gather<PREC, true>(pdf, t.npad, n, m, d, kp.inv_scale, c.abb_in, c.abb_out, t.pressure);
   }
 #pragma unroll
   for (int i = 0; i < kQ; ++i) F[i] = double(d[i]) + wgt(i) * kp.rho_s;
