@@ -11,13 +11,14 @@
 //    exponent among them, with 5 bits of headroom), summed exactly, and each
 //    sum is rounded once to the nearest double.  A PDF at most 5 binades below
 //    the node's largest converts exactly; smaller ones lose bits below 2^-57
-//    of the largest, below the rounding of an IEEE double sum of that size.
-//    Every moment is therefore at least as accurate as the IEEE FP64 sum;
+//    of the largest.  A moment's error is at most 19 * 2^-57 * max|f_i| plus
+//    half an ulp of the result, below the error bound (n - 1) * 2^-53 * sum|f_i|
+//    of the IEEE double sum of n terms that it replaces;
 //  * halving: an exponent decrement, identical to 0.5 * x for every x whose
 //    half is a normal number, Inf or NaN.
 //
-// All functions are __host__ __device__ so that host tests can check them bit
-// for bit against long-double references.
+// All functions are __host__ __device__ so that a host test can check the
+// moments bit for bit against exact rational arithmetic.
 #pragma once
 
 #include <cstdint>
