@@ -718,21 +718,41 @@ __global__ void __launch_bounds__(kBlock, MinCtasEt<PREC>::value) k_et(DevTables
     mask = unsigned(s_loc[6][threadIdx.x]);
   }
   // bits 18..27 of the mask: pull directions that meet a pressure face.  The
-  // FP64 path branches per warp around the anti-bounce-back arithmetic; the
-  // others keep one predicated loop (fewer registers, cheap arithmetic).
-  constexpr bool kF64 = std::is_same<R, double>::value;
-  bool face = false;
-  if constexpr (kF64) face = t.pressure && warp_any((mask >> 18) != 0u);
+  // FP64 path branches per warp around the anti-bounce-back arithmetic (a
+  // predicated subtraction would be issued for all ten x-directions of every
+  // node); the others keep one predicated loop (fewer registers, cheap
+  // arithmetic).
+  if constexpr (std::is_same<R, double>::value) {
+    if (t.pressure && warp_any((mask >> 18) != 0u)) {
 #pragma unroll
-  for (int j = 1; j < kQ; ++j) {
-    const int jj = inv(j);
-    const bool link = !((mask >> (jj - 1)) & 1u);
-    R v = d[j];
-    if (cx(jj) != 0) {
-      if ((kF64 ? face : t.pressure != 0) && ((mask >> et_xbit(jj)) & 1u))
-        v = (cx(jj) > 0 ? c.abb_in[wclass(j) - 1] : c.abb_out[wclass(j) - 1]) - v;
+      for (int j = 1; j < kQ; ++j) {
+        const int jj = inv(j);
+        const bool link = !((mask >> (jj - 1)) & 1u);
+        R v = d[j];
+        if (cx(jj) != 0 && ((mask >> et_xbit(jj)) & 1u))
+          v = (cx(jj) > 0 ? c.abb_in[wclass(j) - 1] : c.abb_out[wclass(j) - 1]) - v;
+        st_step<PREC>(A + at(link != ODD ? jj : j, t.spad, loc[et_row(j) + 1]), v, kp.scale);
+      }
+    } else {
+#pragma unroll
+      for (int j = 1; j < kQ; ++j) {
+        const int jj = inv(j);
+        const bool link = !((mask >> (jj - 1)) & 1u);
+        st_step<PREC>(A + at(link != ODD ? jj : j, t.spad, loc[et_row(j) + 1]), d[j], kp.scale);
+      }
     }
-    st_step<PREC>(A + at(link != ODD ? jj : j, t.spad, loc[et_row(j) + 1]), v, kp.scale);
+  } else {
+#pragma unroll
+    for (int j = 1; j < kQ; ++j) {
+      const int jj = inv(j);
+      const bool link = !((mask >> (jj - 1)) & 1u);
+      R v = d[j];
+      if (cx(jj) != 0) {
+        if (t.pressure && ((mask >> et_xbit(jj)) & 1u))
+          v = (cx(jj) > 0 ? c.abb_in[wclass(j) - 1] : c.abb_out[wclass(j) - 1]) - v;
+      }
+      st_step<PREC>(A + at(link != ODD ? jj : j, t.spad, loc[et_row(j) + 1]), v, kp.scale);
+    }
   }
 }
 
