@@ -94,3 +94,30 @@ def test_nonfinite_or_huge_pdf_marks_the_node(bad):
 def test_rejects_bad_shapes():
     with pytest.raises(ValueError):
         lbm.lbm_exact_moments_host(np.zeros((4, 18)))
+
+
+def test_property_exact_or_within_bound():
+    """Property test over arbitrary finite PDFs (hypothesis, where installed): every output is
+    within 19 truncations of 2^(emax-1080) plus one rounding of the exact rational sum, and
+    exactly the rounded sum when no PDF lies more than 5 binades below the largest."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    @hyp.settings(max_examples=300, deadline=None)
+    @hyp.given(st.lists(st.floats(min_value=-1e6, max_value=1e6, allow_nan=False, allow_infinity=False,
+                                  allow_subnormal=False), min_size=19, max_size=19))
+    def check(vals):
+        d = np.asarray(vals, dtype=np.float64)[None, :]
+        got = lbm.lbm_exact_moments_host(d)[0]
+        e = biased_exponents(d[0])
+        emax = max(int(e.max()), 64)
+        exact = exact_moments(d[0])
+        within5 = bool(np.all((e == 0) | (e >= emax - 5)))
+        lsb = Fraction(2) ** (emax - 1080)
+        for out, x in zip(got, exact):
+            if within5:
+                assert out == float(x)
+            else:
+                assert abs(Fraction(out) - x) <= 19 * lsb + Fraction(abs(out)) * Fraction(2) ** -53
+
+    check()
