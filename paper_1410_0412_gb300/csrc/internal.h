@@ -5,8 +5,12 @@
 #include <algorithm>
 #include <cstddef>
 #include <cstdint>
+#include <memory>
+#include <type_traits>
 #include <mutex>
+#include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/lbm.h"
@@ -28,6 +32,22 @@ constexpr int64_t kPad = 128;
 constexpr int kWarpNodes = 32;
 
 inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// Allocator whose value-less construct() leaves the element uninitialized, so
+// that resize() of a large table costs no serial fill: the builders then
+// write every element, in parallel.
+template <class T> struct NoInitAlloc : std::allocator<T> {
+  template <class U> struct rebind { using other = NoInitAlloc<U>; };
+  NoInitAlloc() = default;
+  template <class U> NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+  template <class U> void construct(U* p) noexcept(std::is_nothrow_default_constructible<U>::value) {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <class U, class... A> void construct(U* p, A&&... a) {
+    ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+  }
+};
+using TableVec = std::vector<int32_t, NoInitAlloc<int32_t>>;
 
 // Device addresses of the uploaded tables (all inside one caller buffer).
 struct DevTables {
@@ -83,9 +103,9 @@ struct lbm_lattice {
   int enumeration = 0, block_B = 1;
   int64_t N = 0, Npad = 0, R = 0, Rpad = 0, nwarps = 0;
   std::vector<int32_t> node_xyz;   // [N][3]
-  std::vector<int32_t> adj;        // [18][Npad], padding = -1
+  lbm::TableVec adj;               // [18][Npad], padding = -1
   std::vector<int32_t> run_start;  // [R+1]
-  std::vector<int32_t> run_adj;    // [18][Rpad], padding = -1
+  lbm::TableVec run_adj;           // [18][Rpad], padding = -1
   std::vector<uint32_t> head_bits; // [nwarps]  run heads, one bit per node
   std::vector<int32_t> warp_run0;  // [nwarps]  run holding node 32w
   std::vector<int32_t> warp_head0; // [nwarps]  first node of that run

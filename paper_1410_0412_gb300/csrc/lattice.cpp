@@ -29,9 +29,11 @@ int n_threads() {
 }
 
 // Run body(begin, end) over [0, n) split into contiguous chunks, one per thread.
-void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& body) {
+// Fewer than min_items items run on the calling thread: per-node loops keep
+// the default, loops over coarse items (slabs, chunks, partitions) pass 2.
+void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& body, int64_t min_items = 4096) {
   int T = n_threads();
-  if (n < 4096 || T == 1) {
+  if (n < min_items || T == 1) {
     if (n > 0) body(0, n);
     return;
   }
@@ -91,7 +93,7 @@ int enumerate_lex(lbm_lattice* L, const uint8_t* solid, int B) {
       }
       cnt[u] = c;
     }
-  });
+  }, 2);
   int64_t N = exclusive_scan(cnt);
   if (N > INT32_MAX) return set_error(LBM_ERR_ARG, "more than 2^31-1 fluid nodes");
   L->N = N;
@@ -112,41 +114,59 @@ int enumerate_lex(lbm_lattice* L, const uint8_t* solid, int B) {
           }
       }
     }
-  });
+  }, 2);
   return LBM_OK;
 }
 
 // ---- Hilbert curve ----------------------------------------------------------------
+// Bit i of v moved to bit 3i (v < 2^21).
+inline uint64_t spread3(uint32_t v) {
+  uint64_t x = v & 0x1fffffu;
+  x = (x | (x << 32)) & 0x1f00000000ffffull;
+  x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+  x = (x | (x << 8)) & 0x100f00f00f00f00full;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+
 // Index of (x, y, z) on the Hilbert curve of the 2^bits cube, after J. Skilling,
 // "Programming the Hilbert curve" (AIP Conf. Proc. 707, 2004): undo the
 // per-level rotations/reflections from the top bit down, Gray-code across the
 // three axes, then read the transposed bits out level by level (x first).
+// Branch-free: each level's "bit set" choice is a mask, so the per-voxel
+// loop does not mispredict on the coordinates' bits.
 uint64_t hilbert_index(uint32_t x, uint32_t y, uint32_t z, int bits) {
   if (bits == 0) return 0;
-  uint32_t a[3] = {x, y, z};
-  const uint32_t top = 1u << (bits - 1);
-  for (uint32_t q = top; q > 1; q >>= 1) {
-    const uint32_t low = q - 1;
-    for (int k = 0; k < 3; ++k) {
-      if (a[k] & q) {
-        a[0] ^= low;
-      } else {
-        uint32_t t = (a[0] ^ a[k]) & low;
-        a[0] ^= t;
-        a[k] ^= t;
-      }
+  uint32_t a0 = x, a1 = y, a2 = z;
+  for (int l = bits - 1; l >= 1; --l) {
+    const uint32_t low = (1u << l) - 1u;
+    // axis 0: bit set -> invert its low bits (the exchange with itself is a no-op)
+    a0 ^= low & (0u - ((a0 >> l) & 1u));
+    // axes 1, 2: bit set -> invert axis 0's low bits, else exchange them with axis 0's
+    {
+      const uint32_t m = 0u - ((a1 >> l) & 1u);
+      const uint32_t t = (a0 ^ a1) & low & ~m;
+      a0 ^= (low & m) | t;
+      a1 ^= t;
+    }
+    {
+      const uint32_t m = 0u - ((a2 >> l) & 1u);
+      const uint32_t t = (a0 ^ a2) & low & ~m;
+      a0 ^= (low & m) | t;
+      a2 ^= t;
     }
   }
-  a[1] ^= a[0];
-  a[2] ^= a[1];
+  a1 ^= a0;  // Gray code across the axes
+  a2 ^= a1;
   uint32_t fix = 0;
-  for (uint32_t q = top; q > 1; q >>= 1)
-    if (a[2] & q) fix ^= q - 1;
-  for (int k = 0; k < 3; ++k) a[k] ^= fix;
-  uint64_t key = 0;
-  for (int lvl = bits - 1; lvl >= 0; --lvl)
-    for (int k = 0; k < 3; ++k) key = (key << 1) | ((a[k] >> lvl) & 1u);
-  return key;
+  for (int l = bits - 1; l >= 1; --l) fix ^= ((1u << l) - 1u) & (0u - ((a2 >> l) & 1u));
+  a0 ^= fix;
+  a1 ^= fix;
+  a2 ^= fix;
+  // read the transposed bits out level by level, axis 0 first
+  const uint32_t mask = (1u << bits) - 1u;
+  return (spread3(a0 & mask) << 2) | (spread3(a1 & mask) << 1) | spread3(a2 & mask);
 }
 
 int enumerate_hilbert(lbm_lattice* L, const uint8_t* solid) {
@@ -164,19 +184,22 @@ int enumerate_hilbert(lbm_lattice* L, const uint8_t* solid) {
       for (int64_t k = 0; k < X * Y; ++k) c += sl[k] == 0;
       cnt[z] = c;
     }
-  });
+  }, 2);
   const int64_t N = exclusive_scan(cnt);
   if (N > INT32_MAX) return set_error(LBM_ERR_ARG, "more than 2^31-1 fluid nodes");
-  // Keys are unique in [0, 8^bits): place every fluid voxel in its key slot,
-  // then scan the slots in order.
-  const int64_t slots = int64_t(1) << (3 * bits);
-  std::vector<int32_t> slot;
+  // Sort keys: the voxel's Hilbert index above its raster rank (31 bits).  The
+  // indices are unique, so sorting the keys sorts the voxels along the curve;
+  // the cost follows N, not the 8^bits cells of the enclosing cube.
+  using KeyVec = std::vector<uint64_t, NoInitAlloc<uint64_t>>;
+  KeyVec kv, tmp;
+  std::vector<int32_t, NoInitAlloc<int32_t>> raster;
   try {
-    slot.assign(slots, -1);
+    kv.resize(N);
+    tmp.resize(N);
+    raster.resize(3 * N);
   } catch (...) {
-    return set_error(LBM_ERR_ALLOC, "out of host memory for the Hilbert slot table");
+    return set_error(LBM_ERR_ALLOC, "out of host memory for the Hilbert sort");
   }
-  std::vector<int32_t> raster(3 * N);
   parallel_for(Z, [&](int64_t zb, int64_t ze) {
     for (int64_t z = zb; z < ze; ++z) {
       int64_t n = cnt[z];
@@ -186,34 +209,46 @@ int enumerate_hilbert(lbm_lattice* L, const uint8_t* solid) {
             raster[3 * n] = int32_t(x);
             raster[3 * n + 1] = int32_t(y);
             raster[3 * n + 2] = int32_t(z);
-            slot[hilbert_index(uint32_t(x), uint32_t(y), uint32_t(z), bits)] = int32_t(n);
+            kv[n] = (hilbert_index(uint32_t(x), uint32_t(y), uint32_t(z), bits) << 31) | uint64_t(n);
             ++n;
           }
     }
-  });
-  // Compact the occupied slots in key order.
+  }, 2);
+  // One most-significant-digit pass on the top SB key bits (per-thread
+  // histograms, scatter), then each bucket sorted on its own.
+  const int kb = 3 * bits + 31;  // significant key bits
+  const int SB = std::min(16, kb);
+  const int shift = kb - SB;
+  const int64_t NB = int64_t(1) << SB;
   const int T = n_threads();
-  const int64_t chunk = (slots + T - 1) / T;
-  std::vector<int64_t> part(T, 0);
+  const int64_t chunk = std::max<int64_t>(1, (N + T - 1) / T);
+  std::vector<int64_t> hist(size_t(T) * NB, 0), start(NB + 1, 0);
   parallel_for(T, [&](int64_t tb, int64_t te) {
-    for (int64_t t = tb; t < te; ++t) {
-      int64_t c = 0;
-      for (int64_t k = t * chunk; k < std::min(slots, (t + 1) * chunk); ++k) c += slot[k] >= 0;
-      part[t] = c;
+    for (int64_t t = tb; t < te; ++t)
+      for (int64_t k = t * chunk; k < std::min(N, (t + 1) * chunk); ++k) ++hist[t * NB + int64_t(kv[k] >> shift)];
+  }, 2);
+  int64_t acc = 0;
+  for (int64_t b = 0; b < NB; ++b) {
+    start[b] = acc;
+    for (int t = 0; t < T; ++t) {
+      const int64_t c = hist[t * NB + b];
+      hist[t * NB + b] = acc;
+      acc += c;
     }
-  });
-  exclusive_scan(part);
+  }
+  start[NB] = acc;
+  parallel_for(T, [&](int64_t tb, int64_t te) {
+    for (int64_t t = tb; t < te; ++t)
+      for (int64_t k = t * chunk; k < std::min(N, (t + 1) * chunk); ++k) tmp[hist[t * NB + int64_t(kv[k] >> shift)]++] = kv[k];
+  }, 2);
+  parallel_for(NB, [&](int64_t bb, int64_t be) {
+    for (int64_t b = bb; b < be; ++b) std::sort(tmp.begin() + start[b], tmp.begin() + start[b + 1]);
+  }, 2);
   L->N = N;
-  L->node_xyz.assign(3 * N, 0);
-  parallel_for(T, [&](int64_t tb, int64_t te) {
-    for (int64_t t = tb; t < te; ++t) {
-      int64_t n = part[t];
-      for (int64_t k = t * chunk; k < std::min(slots, (t + 1) * chunk); ++k)
-        if (slot[k] >= 0) {
-          std::memcpy(&L->node_xyz[3 * n], &raster[3 * int64_t(slot[k])], 3 * sizeof(int32_t));
-          ++n;
-        }
-    }
+  L->node_xyz.resize(3 * N);
+  parallel_for(N, [&](int64_t b, int64_t e) {
+    for (int64_t k = b; k < e; ++k)
+      std::memcpy(&L->node_xyz[3 * k], &raster[3 * int64_t(tmp[k] & 0x7fffffffu)], 3 * sizeof(int32_t));
   });
   return LBM_OK;
 }
@@ -221,13 +256,17 @@ int enumerate_hilbert(lbm_lattice* L, const uint8_t* solid) {
 // ---- adjacency list -------------------------------------------------------------------
 int fill_adjacency(lbm_lattice* L) {
   const int64_t X = L->X, Y = L->Y, Z = L->Z, N = L->N, Np = L->Npad;
-  std::vector<int32_t> v2n;
+  TableVec v2n;
   try {
-    v2n.assign(X * Y * Z, -1);
-    L->adj.assign(18 * Np, LBM_MARK_WALL);
+    v2n.resize(X * Y * Z);  // uninitialized: filled below
+    L->adj.resize(18 * Np);
   } catch (...) {
     return set_error(LBM_ERR_ALLOC, "out of host memory for the adjacency list");
   }
+  parallel_for(Z, [&](int64_t zb, int64_t ze) {
+    std::fill(v2n.begin() + zb * X * Y, v2n.begin() + ze * X * Y, -1);
+  }, 2);
+  for (int i = 0; i < 18; ++i) std::fill(L->adj.begin() + i * Np + N, L->adj.begin() + (i + 1) * Np, LBM_MARK_WALL);
   parallel_for(N, [&](int64_t b, int64_t e) {
     for (int64_t n = b; n < e; ++n) {
       const int32_t* p = &L->node_xyz[3 * n];
@@ -295,16 +334,18 @@ int derive_ria(lbm_lattice* L) {
         h += (n == 0 || !continues(L->adj.data(), Np, n));
       heads[c] = h;
     }
-  });
+  }, 2);
   const int64_t R = exclusive_scan(heads);
   L->R = R;
   L->Rpad = round_up(std::max<int64_t>(R, 1), kPad);
   try {
     L->run_start.assign(R + 1, 0);
-    L->run_adj.assign(18 * L->Rpad, LBM_MARK_WALL);
+    L->run_adj.resize(18 * L->Rpad);  // rows [0, R) are filled below
   } catch (...) {
     return set_error(LBM_ERR_ALLOC, "out of host memory for the RIA table");
   }
+  for (int i = 0; i < 18; ++i)
+    std::fill(L->run_adj.begin() + i * L->Rpad + R, L->run_adj.begin() + (i + 1) * L->Rpad, LBM_MARK_WALL);
   parallel_for(nchunks, [&](int64_t cb, int64_t ce) {
     for (int64_t c = cb; c < ce; ++c) {
       int64_t r = heads[c];
@@ -315,7 +356,7 @@ int derive_ria(lbm_lattice* L) {
           ++r;
         }
     }
-  });
+  }, 2);
   L->run_start[R] = int32_t(N);
   // Warp-level run index: a head bit per node, and for every 32-node group the
   // run holding its first node and that run's first node.
@@ -382,7 +423,7 @@ int renumber_partitions(const lbm_lattice* L, int P, int32_t* out) {
       const int64_t a = N * p / P, b = N * (p + 1) / P;
       std::sort(idx.begin() + a, idx.begin() + b, [&](int64_t u, int64_t v) { return key(u) < key(v); });
     }
-  });
+  }, 2);
   for (int64_t n = 0; n < N; ++n) std::memcpy(out + 3 * n, &L->node_xyz[3 * idx[n]], 3 * sizeof(int32_t));
   return LBM_OK;
 }
@@ -400,7 +441,7 @@ int partition_ghosts(const lbm_lattice* L, int P, int64_t* ghosts) {
         }
       ghosts[p] = g;
     }
-  });
+  }, 2);
   return LBM_OK;
 }
 

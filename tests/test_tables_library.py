@@ -111,3 +111,12 @@ def test_adjacency_rows_export():
     assert np.array_equal(lat.adjacency_rows(nodes), full[:, nodes])
     with pytest.raises(lbm.LbmError):
         lat.adjacency_rows(np.array([lat.N]))
+
+
+@pytest.mark.parametrize("dims", [(2048, 2, 2), (3, 1025, 2), (2, 3, 700), (130, 33, 65)])
+def test_hilbert_deep_curves(dims):
+    # long thin boxes reach the deepest curve levels the builder supports (2^11
+    # per axis) at a few thousand voxels, so every level of the index is checked
+    X, Y, Z = dims
+    solid = geometry.random_voxels(X, Y, Z, 0.2, X + Y + Z)
+    _compare(solid, (0, 0, 0), False, "hilbert", 1)
