@@ -469,46 +469,79 @@ int derive_et_tables(lbm_lattice* L) {
   const int64_t N = L->N, Np = L->Npad;
   const bool have_xyz = int64_t(L->node_xyz.size()) == 3 * N;
   const int64_t X = L->X, Y = L->Y;
+  const int64_t dim[3] = {L->X, L->Y, L->Z};
   std::vector<int32_t> nb(size_t(6) * Np, -1);
   std::vector<uint32_t> mask(Np, 0u);
-  std::vector<std::pair<uint64_t, int64_t>> cand;  // (location key, k * Np + n)
-  for (int k = 0; k < 6; ++k)
-    for (int64_t n = 0; n < N; ++n) {
-      const int32_t m = L->adj[(kSrcDir[k] - 1) * Np + n];
-      if (m >= 0) {
-        nb[k * Np + n] = m;
-        continue;
-      }
-      if (!have_xyz)
-        return set_error(LBM_ERR_UNSUPPORTED, "Esoteric Twist phantom locations need node coordinates");
-      int64_t p[3];
-      const int64_t dim[3] = {L->X, L->Y, L->Z};
-      for (int a = 0; a < 3; ++a) {
-        p[a] = L->node_xyz[3 * n + a] + kOff[k][a];
-        if (L->bc.periodic[a] && p[a] == dim[a]) p[a] = 0;
-      }
-      cand.emplace_back(uint64_t((p[2] * (Y + 1) + p[1]) * (X + 1) + p[0]), k * Np + n);
+  // Locations that are no fluid node's: candidates (location key, k * Np + n),
+  // counted per chunk of nodes, then filled in chunk order.
+  const int T = n_threads();
+  const int64_t chunk = std::max<int64_t>(1, (N + T - 1) / T);
+  const int64_t nchunks = N == 0 ? 0 : (N + chunk - 1) / chunk;
+  std::vector<int64_t> ccount(nchunks, 0);
+  parallel_for(nchunks, [&](int64_t cb, int64_t ce) {
+    for (int64_t c = cb; c < ce; ++c) {
+      int64_t cnt = 0;
+      for (int k = 0; k < 6; ++k)
+        for (int64_t n = c * chunk; n < std::min(N, (c + 1) * chunk); ++n) {
+          const int32_t m = L->adj[(kSrcDir[k] - 1) * Np + n];
+          if (m >= 0)
+            nb[k * Np + n] = m;
+          else
+            ++cnt;
+        }
+      ccount[c] = cnt;
     }
-  std::vector<uint64_t> keys(cand.size());
-  for (size_t c = 0; c < cand.size(); ++c) keys[c] = cand[c].first;
+  }, 2);
+  const int64_t ncand = exclusive_scan(ccount);
+  if (ncand > 0 && !have_xyz)
+    return set_error(LBM_ERR_UNSUPPORTED, "Esoteric Twist phantom locations need node coordinates");
+  std::vector<uint64_t> ckey(ncand);
+  std::vector<int64_t> cslot(ncand);
+  parallel_for(nchunks, [&](int64_t cb, int64_t ce) {
+    for (int64_t c = cb; c < ce; ++c) {
+      int64_t w = ccount[c];
+      for (int k = 0; k < 6; ++k)
+        for (int64_t n = c * chunk; n < std::min(N, (c + 1) * chunk); ++n) {
+          if (L->adj[(kSrcDir[k] - 1) * Np + n] >= 0) continue;
+          int64_t p[3];
+          for (int a = 0; a < 3; ++a) {
+            p[a] = L->node_xyz[3 * n + a] + kOff[k][a];
+            if (L->bc.periodic[a] && p[a] == dim[a]) p[a] = 0;
+          }
+          ckey[w] = uint64_t((p[2] * (Y + 1) + p[1]) * (X + 1) + p[0]);
+          cslot[w] = k * Np + n;
+          ++w;
+        }
+    }
+  }, 2);
+  std::vector<uint64_t> keys(ckey);
   std::sort(keys.begin(), keys.end());
   keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
   const int64_t M = int64_t(keys.size());
   if (N + M > INT32_MAX) return set_error(LBM_ERR_UNSUPPORTED, "too many Esoteric Twist storage locations");
-  for (const auto& c : cand)
-    nb[c.second] = int32_t(N + (std::lower_bound(keys.begin(), keys.end(), c.first) - keys.begin()));
+  parallel_for(ncand, [&](int64_t b, int64_t e) {
+    for (int64_t c = b; c < e; ++c)
+      nb[cslot[c]] = int32_t(N + (std::lower_bound(keys.begin(), keys.end(), ckey[c]) - keys.begin()));
+  });
   std::vector<int32_t> ph(size_t(3) * M);
-  for (int64_t r = 0; r < M; ++r) {
-    ph[3 * r] = int32_t(keys[r] % uint64_t(X + 1));
-    ph[3 * r + 1] = int32_t((keys[r] / uint64_t(X + 1)) % uint64_t(Y + 1));
-    ph[3 * r + 2] = int32_t(keys[r] / uint64_t((X + 1) * (Y + 1)));
-  }
-  for (int i = 1; i < kQ; ++i)
-    for (int64_t n = 0; n < N; ++n) {
-      const int32_t m = L->adj[(i - 1) * Np + n];
-      if (m < 0) mask[n] |= 1u << (i - 1);
-      if (kCX[i] != 0 && m <= LBM_MARK_INLET) mask[n] |= 1u << (i <= 2 ? 17 + i : 13 + i);
+  parallel_for(M, [&](int64_t b, int64_t e) {
+    for (int64_t r = b; r < e; ++r) {
+      ph[3 * r] = int32_t(keys[r] % uint64_t(X + 1));
+      ph[3 * r + 1] = int32_t((keys[r] / uint64_t(X + 1)) % uint64_t(Y + 1));
+      ph[3 * r + 2] = int32_t(keys[r] / uint64_t((X + 1) * (Y + 1)));
     }
+  });
+  parallel_for(N, [&](int64_t b, int64_t e) {
+    for (int64_t n = b; n < e; ++n) {
+      uint32_t mk = 0u;
+      for (int i = 1; i < kQ; ++i) {
+        const int32_t m = L->adj[(i - 1) * Np + n];
+        if (m < 0) mk |= 1u << (i - 1);
+        if (kCX[i] != 0 && m <= LBM_MARK_INLET) mk |= 1u << (i <= 2 ? 17 + i : 13 + i);
+      }
+      mask[n] = mk;
+    }
+  });
   // run-length coding (Sect. 4.1's idea on these tables): node n continues
   // n-1's run when all six locations advance by one and the mask is equal
   auto continues_et = [&](int64_t n) {
@@ -516,18 +549,33 @@ int derive_et_tables(lbm_lattice* L) {
       if (int64_t(nb[k * Np + n]) != int64_t(nb[k * Np + n - 1]) + 1) return false;
     return mask[n] == mask[n - 1];
   };
-  std::vector<int32_t> rs;
-  for (int64_t n = 0; n < N; ++n)
-    if (n == 0 || !continues_et(n)) rs.push_back(int32_t(n));
-  const int64_t R = int64_t(rs.size());
-  rs.push_back(int32_t(N));
+  std::vector<int64_t> hcount(nchunks, 0);
+  parallel_for(nchunks, [&](int64_t cb, int64_t ce) {
+    for (int64_t c = cb; c < ce; ++c) {
+      int64_t h = 0;
+      for (int64_t n = c * chunk; n < std::min(N, (c + 1) * chunk); ++n) h += (n == 0 || !continues_et(n));
+      hcount[c] = h;
+    }
+  }, 2);
+  const int64_t R = exclusive_scan(hcount);
+  std::vector<int32_t> rs(R + 1);
+  parallel_for(nchunks, [&](int64_t cb, int64_t ce) {
+    for (int64_t c = cb; c < ce; ++c) {
+      int64_t r = hcount[c];
+      for (int64_t n = c * chunk; n < std::min(N, (c + 1) * chunk); ++n)
+        if (n == 0 || !continues_et(n)) rs[r++] = int32_t(n);
+    }
+  }, 2);
+  rs[R] = int32_t(N);
   const int64_t Rpad = round_up(std::max<int64_t>(R, 1), kPad);
   std::vector<int32_t> rnb(size_t(6) * Rpad, -1);
   std::vector<uint32_t> rmask(Rpad, 0u);
-  for (int64_t r = 0; r < R; ++r) {
-    for (int k = 0; k < 6; ++k) rnb[k * Rpad + r] = nb[k * Np + rs[r]];
-    rmask[r] = mask[rs[r]];
-  }
+  parallel_for(R, [&](int64_t b, int64_t e) {
+    for (int64_t r = b; r < e; ++r) {
+      for (int k = 0; k < 6; ++k) rnb[k * Rpad + r] = nb[k * Np + rs[r]];
+      rmask[r] = mask[rs[r]];
+    }
+  });
   const int64_t nw = (N + kWarpNodes - 1) / kWarpNodes;
   std::vector<uint32_t> hb(nw, 0u);
   std::vector<int32_t> wr(nw, 0), wh(nw, 0);
