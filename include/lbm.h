@@ -25,6 +25,9 @@
  *    a handle (uploads, and the first Esoteric Twist query, which derives its
  *    tables) must not run concurrently with other calls on the same handle;
  *    stepping calls only read the handle and may overlap.
+ *  - Host tables are built with std::thread workers: as many as the hardware
+ *    threads (at most 64), or the environment variable LBM_HOST_THREADS
+ *    (1..256) when set.  The tables never depend on the thread count.
  *  - Device work is enqueued on `stream` (a cudaStream_t passed as void*;
  *    NULL selects the legacy default stream) and is asynchronous: a call
  *    returns once the kernels are queued.  Launch errors are reported as

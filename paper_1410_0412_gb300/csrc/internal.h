@@ -33,6 +33,11 @@ constexpr int kWarpNodes = 32;
 
 inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
+// Host threads of the table builders: LBM_HOST_THREADS (1..256) when set,
+// otherwise every hardware thread, at most 64.  Read on every call, so a
+// process may change it between builds; the tables do not depend on it.
+int host_threads();
+
 // Allocator whose value-less construct() leaves the element uninitialized, so
 // that resize() of a large table costs no serial fill: the builders then
 // write every element, in parallel.

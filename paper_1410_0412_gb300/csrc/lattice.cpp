@@ -13,6 +13,7 @@
 // none of it is on the timed path.
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <new>
@@ -21,12 +22,19 @@
 #include "internal.h"
 
 namespace lbm {
-namespace {
 
-int n_threads() {
-  unsigned h = std::thread::hardware_concurrency();
+int host_threads() {
+  if (const char* e = std::getenv("LBM_HOST_THREADS")) {
+    const long v = std::strtol(e, nullptr, 10);
+    if (v >= 1 && v <= 256) return static_cast<int>(v);
+  }
+  const unsigned h = std::thread::hardware_concurrency();
   return h == 0 ? 4 : static_cast<int>(std::min(h, 64u));
 }
+
+namespace {
+
+int n_threads() { return host_threads(); }
 
 // Run body(begin, end) over [0, n) split into contiguous chunks, one per thread.
 // Fewer than min_items items run on the calling thread: per-node loops keep

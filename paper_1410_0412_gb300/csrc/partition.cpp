@@ -32,8 +32,7 @@ namespace lbm {
 namespace {
 
 void parallel_parts(int P, const std::function<void(int)>& body) {
-  unsigned h = std::thread::hardware_concurrency();
-  int T = std::max(1, std::min<int>(P, h == 0 ? 4 : int(std::min(h, 64u))));
+  const int T = std::max(1, std::min(P, host_threads()));
   std::vector<std::thread> th;
   std::atomic<int> next{0};
   for (int t = 0; t < T; ++t)

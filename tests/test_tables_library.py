@@ -120,3 +120,22 @@ def test_hilbert_deep_curves(dims):
     X, Y, Z = dims
     solid = geometry.random_voxels(X, Y, Z, 0.2, X + Y + Z)
     _compare(solid, (0, 0, 0), False, "hilbert", 1)
+
+
+@pytest.mark.parametrize("enum,B", [("lex", 1), ("lex", 4), ("hilbert", 1)])
+def test_tables_do_not_depend_on_host_threads(enum, B, monkeypatch):
+    # the builders split nodes, slabs and runs into per-thread chunks; runs and
+    # phantom locations that cross a chunk boundary must come out the same
+    solid = geometry.random_voxels(37, 29, 23, 0.3, 11)
+    out = []
+    for threads in ("1", "3", "7"):
+        monkeypatch.setenv("LBM_HOST_THREADS", threads)
+        lat = lbm.Lattice(solid, periodic=(1, 0, 0), x_pressure=False, enum=enum, B=B)
+        t = lat.tables()
+        nb, mask = lat.et_tables()
+        out.append((t["node_xyz"], t["adj"], t["run_start"], t["run_adj"], nb, mask, lat.et_runs()))
+    for other in out[1:]:
+        for a, b in zip(out[0][:6], other[:6]):
+            assert np.array_equal(a, b)
+        for a, b in zip(out[0][6], other[6]):
+            assert np.array_equal(a, b)
