@@ -468,10 +468,13 @@ LBM_API int lbm_macroscopic(const lbm_lattice* lat, int prec, const lbm_params* 
  * results as lbm_macroscopic without the workspace: the per-block partial
  * sums live in a fixed 4 MiB array inside the library (present on every GPU
  * that loads it, until unload), so at most 16,777,216 fluid nodes are
- * accepted (LBM_ERR_ARG otherwise).  The first call on a device looks up that
- * array's address with the device current; make it before any stream capture.
- * All calls share the array: calls whose kernels overlap on the GPU race and
- * may return wrong sums.  Allocates nothing. */
+ * accepted (LBM_ERR_ARG otherwise).  Every layout of lbm_macroscopic is
+ * accepted, with the same table requirements.  The first call on a device
+ * looks up that array's address with the device current and caches it; make
+ * it before any stream capture, and do not call this entry point across a
+ * cudaDeviceReset (the cached address would be stale).  All calls share the
+ * array: calls whose kernels overlap on the GPU race and may return wrong
+ * sums.  Allocates nothing. */
 LBM_API int lbm_macroscopic_noalloc(const lbm_lattice* lat, int prec, const lbm_params* params, const void* pdf,
                                     int layout, const float* s, double* rho, double* u, double* sums,
                                     void* stream);

@@ -479,8 +479,19 @@ def lbm_macroscopic_noalloc(lat, prec, params, pdf, layout, s=None, rho=None, u=
     allocated here.  At most 16,777,216 fluid nodes; concurrent calls that
     overlap on the GPU share the array and race.
     """
+    torch = _torch()
     prec = _prec(prec)
-    _check_grid(lat, prec, pdf, "pdf")
+    _check_grid(lat, prec, pdf, "pdf", layout)
+    # the kernels write N, 3N and 4 doubles through these pointers: check them here
+    for name, t, n in (("rho", rho, lat.N), ("u", u, 3 * lat.N), ("sums", sums, 4)):
+        if t is None:
+            continue
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.device != pdf.device:
+            raise TypeError(f"{name} must be a CUDA tensor on the device of pdf")
+        if t.dtype != torch.float64:
+            raise TypeError(f"{name} has dtype {t.dtype}, needs torch.float64")
+        if not t.is_contiguous() or t.numel() < n:
+            raise ValueError(f"{name} must be contiguous with at least {n} elements")
     check(_lib.load().lbm_macroscopic_noalloc(lat.handle, prec, ctypes.byref(params.c()), _ptr(pdf), layout,
                                               _ptr(_check_s(lat, s)), _ptr(rho), _ptr(u), _ptr(sums),
                                               _stream(stream)), "lbm_macroscopic_noalloc")

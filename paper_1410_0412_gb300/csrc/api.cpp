@@ -54,6 +54,45 @@ int make_kparams(const lbm_params* p, int prec, KParams* kp) {
 
 using namespace lbm;
 
+namespace lbm {
+
+int check_lat(const lbm_lattice* L) {
+  if (!L) return set_error(LBM_ERR_ARG, "lattice handle is NULL");
+  return LBM_OK;
+}
+
+// Any uploaded addressing (adjacency preferred) for gathers that need one.
+int any_tables(const lbm_lattice* L, int* ria) {
+  if (L->uploaded & LBM_TABLES_ADJ) {
+    *ria = 0;
+    return LBM_OK;
+  }
+  if (L->uploaded & LBM_TABLES_RIA) {
+    *ria = 1;
+    return LBM_OK;
+  }
+  return set_error(LBM_ERR_ARG, "no device tables uploaded");
+}
+
+int check_layout(int layout) {
+  if (layout < LBM_LAYOUT_OSNT || layout > LBM_LAYOUT_ET_ODD) return set_error(LBM_ERR_ARG, "unknown layout");
+  return LBM_OK;
+}
+
+// The device tables a layout's gathers need: none for AA_EVEN, the Esoteric
+// Twist tables for the ET layouts, any addressing for the others.
+int layout_tables(const lbm_lattice* L, int layout) {
+  if (L->N == 0 || layout == LBM_LAYOUT_AA_EVEN) return LBM_OK;
+  if (layout >= LBM_LAYOUT_ET_EVEN) {
+    if (!(L->uploaded & LBM_TABLES_ET)) return set_error(LBM_ERR_ARG, "Esoteric Twist tables not uploaded to the device");
+    return LBM_OK;
+  }
+  int ria;
+  return any_tables(L, &ria);
+}
+
+}  // namespace lbm
+
 namespace {
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
@@ -101,11 +140,6 @@ TableLayout table_layout(const lbm_lattice* L, int which) {
   return t;
 }
 
-int check_lat(const lbm_lattice* L) {
-  if (!L) return set_error(LBM_ERR_ARG, "lattice handle is NULL");
-  return LBM_OK;
-}
-
 int check_tables(const lbm_lattice* L, int ria) {
   int need = ria ? LBM_TABLES_RIA : LBM_TABLES_ADJ;
   if (!(L->uploaded & need))
@@ -114,42 +148,12 @@ int check_tables(const lbm_lattice* L, int ria) {
   return LBM_OK;
 }
 
-// Any uploaded addressing (adjacency preferred) for gathers that need one.
-int any_tables(const lbm_lattice* L, int* ria) {
-  if (L->uploaded & LBM_TABLES_ADJ) {
-    *ria = 0;
-    return LBM_OK;
-  }
-  if (L->uploaded & LBM_TABLES_RIA) {
-    *ria = 1;
-    return LBM_OK;
-  }
-  return set_error(LBM_ERR_ARG, "no device tables uploaded");
-}
-
 // Whole-lattice operations that a partition's local lattice cannot do alone
 // (its ghost slots are not nodes).
 int check_whole(const lbm_lattice* L, const char* what) {
   if (L->partition_local)
     return set_error(LBM_ERR_UNSUPPORTED, std::string(what) + " needs a whole lattice, not a partition's local lattice");
   return LBM_OK;
-}
-
-int check_layout(int layout) {
-  if (layout < LBM_LAYOUT_OSNT || layout > LBM_LAYOUT_ET_ODD) return set_error(LBM_ERR_ARG, "unknown layout");
-  return LBM_OK;
-}
-
-// The device tables a layout's gathers need: none for AA_EVEN, the Esoteric
-// Twist tables for the ET layouts, any addressing for the others.
-int layout_tables(const lbm_lattice* L, int layout) {
-  if (L->N == 0 || layout == LBM_LAYOUT_AA_EVEN) return LBM_OK;
-  if (layout >= LBM_LAYOUT_ET_EVEN) {
-    if (!(L->uploaded & LBM_TABLES_ET)) return set_error(LBM_ERR_ARG, "Esoteric Twist tables not uploaded to the device");
-    return LBM_OK;
-  }
-  int ria;
-  return any_tables(L, &ria);
 }
 
 constexpr int kAllTables = LBM_TABLES_ADJ | LBM_TABLES_RIA | LBM_TABLES_ET;

@@ -187,6 +187,15 @@ struct KParams {
 
 int make_kparams(const lbm_params* p, int prec, KParams* kp);
 
+// Argument checks shared by the entry points (api.cpp): a non-NULL handle; a
+// known layout; the device tables the layout's gathers need (none for
+// LBM_LAYOUT_AA_EVEN, the Esoteric Twist tables for the ET layouts, any
+// addressing otherwise).  Each returns LBM_OK or sets the error message.
+int check_lat(const lbm_lattice* L);
+int any_tables(const lbm_lattice* L, int* ria);
+int check_layout(int layout);
+int layout_tables(const lbm_lattice* L, int layout);
+
 // Kernel launchers, one explicit instantiation per storage precision in
 // kernels_<prec>.cu.  All return a LBM_* status.
 template <int PREC>

@@ -14,7 +14,10 @@
 //    larger lattices are rejected with LBM_ERR_ARG;
 //  - the first call on a device looks up the array's device address (with that
 //    device current) and caches it; make that first call before any stream
-//    capture;
+//    capture.  The cache assumes the device's primary context lives as long
+//    as the process: after cudaDeviceReset (or anything else that destroys
+//    that context) the cached address is stale, so do not call this entry
+//    point across a reset;
 //  - every call shares the one array: calls whose kernels overlap on the GPU
 //    (e.g. on two streams without ordering) race on it and may return wrong
 //    sums.  Every partial a call reads is written by the same call first, so no
@@ -66,16 +69,16 @@ using namespace lbm;
 extern "C" int lbm_macroscopic_noalloc(const lbm_lattice* L, int prec, const lbm_params* params, const void* pdf,
                                        int layout, const float* s, double* rho, double* u, double* sums,
                                        void* stream) {
-  if (!L) return set_error(LBM_ERR_ARG, "lattice handle is NULL");
+  // the same checks as lbm_macroscopic, then the size limit of the fixed array
+  if (int rc = check_lat(L)) return rc;
   KParams kp;
   if (int rc = make_kparams(params, prec, &kp)) return rc;
-  if (layout < LBM_LAYOUT_OSNT || layout > LBM_LAYOUT_AA_ODD) return set_error(LBM_ERR_ARG, "unknown layout");
+  if (int rc = check_layout(layout)) return rc;
   if (!pdf) return set_error(LBM_ERR_ARG, "pdf is NULL");
   if (L->N > kNoAllocMaxNodes)
     return set_error(LBM_ERR_ARG, "lbm_macroscopic_noalloc handles at most 16777216 fluid nodes; "
                                   "use lbm_macroscopic with a workspace");
-  if (layout != LBM_LAYOUT_AA_EVEN && L->N > 0 && !(L->uploaded & (LBM_TABLES_ADJ | LBM_TABLES_RIA)))
-    return set_error(LBM_ERR_ARG, "no device tables uploaded");
+  if (int rc = layout_tables(L, layout)) return rc;
   double* partials = nullptr;
   if (int rc = partials_on_current_device(&partials)) return rc;
   const int64_t parts = reduce_parts(L);
