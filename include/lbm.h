@@ -328,6 +328,26 @@ LBM_API int lbm_check_finite(const double* values, int64_t count, void* stream);
  * LBM_ERR_ARG for NULL pointers or n < 0. */
 LBM_API int lbm_exact_moments_host(const double* d, int64_t n, double* out);
 
+/* Host image of the FP64 step's fixed-point pair update, so that it can be
+ * tested without a GPU.  The TRT collision (Sect. 2) relaxes the even and odd
+ * parts of each opposite pair (a, b = inv a); with the node's velocity u and
+ * the axis-class terms K0, T, O (halved for the face diagonals) the pair
+ * becomes p_a,b = e +- o, e = K0 + (c_a.u)(c_a.T) + qp (d_a + d_b),
+ * o = qm (d_a - d_b) + c_a.O, qm = (1 - l-)/2, qp = (1 - l+)/2.  The LBM_F64
+ * step kernels evaluate this in 64-bit fixed point at a scale 2^(es - 1080)
+ * tied to the node's largest PDF, with one rounding to double per output,
+ * whenever the node's values lie in that scale's range; this runs the same
+ * routine on the host.  d: host double [n][19] (node-major); terms: host
+ * double [n][10]: ux, uy, uz, K0, Tx, Ty, Tz, Ox, Oy, Oz; lp1: 1 for the
+ * l+ = 1 form (qp must be 0).  out: host double [n][19]: out[0] = es, out[1..18]
+ * the post-collision pair values; ok: host int [n], 0 where the node is
+ * outside the range (out is then 0; the kernels take the FP64 update there).
+ * Each value is within 8 units of 2^(es - 1080) of the exact rational result,
+ * before its rounding to nearest.  LBM_ERR_ARG for NULL pointers, n < 0, or
+ * |qm| or |qp| >= 1/2. */
+LBM_API int lbm_fx_pairs_host(const double* d, const double* terms, int64_t n, double qm, double qp, int lp1,
+                              double* out, int* ok);
+
 /* Check the host tables: entries in range, adjacency reciprocity
  * (adj[i][n] = m >= 0  <=>  adj[inv i][m] = n), run table decoding back to the
  * adjacency list exactly, runs sorted and covering [0, N).  Returns

@@ -563,6 +563,25 @@ def lbm_exact_moments_host(d):
     return out
 
 
+def lbm_fx_pairs_host(d, terms, qm, qp, lp1):
+    """Host image of the FP64 step's fixed-point pair update (``lbm_fx_pairs_host``).
+
+    d: [n, 19] PDFs; terms: [n, 10] (ux, uy, uz, K0, Tx, Ty, Tz, Ox, Oy, Oz).
+    Returns (out [n, 19], ok [n]): out[:, 0] is the pair scale es and
+    out[:, 1:] the post-collision pair values where ok.
+    """
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(d, dtype=np.float64))
+    t = np.ascontiguousarray(np.asarray(terms, dtype=np.float64))
+    if a.ndim != 2 or a.shape[1] != 19 or t.shape != (a.shape[0], 10):
+        raise ValueError("d must have shape [n, 19] and terms [n, 10]")
+    out = np.empty((a.shape[0], 19), dtype=np.float64)
+    ok = np.empty(a.shape[0], dtype=np.int32)
+    check(_lib.load().lbm_fx_pairs_host(a.ctypes.data, t.ctypes.data, a.shape[0], float(qm), float(qp),
+                                        1 if lp1 else 0, out.ctypes.data, ok.ctypes.data), "lbm_fx_pairs_host")
+    return out, ok.astype(bool)
+
+
 def lbm_bandwidth_kernel(kind, dst, src=None, arrays=1, stream=None):
     """One launch of the CNT-kA (kind 0, copy src -> dst with streaming stores) or
     U-kA (kind 1, update dst in place) bandwidth kernel over ``arrays`` equal
@@ -808,7 +827,7 @@ __all__ = [
     "PartitionedSolver", "lbm_halo_exchange", "lbm_partition_run_aa", "lbm_partition_run_osnt",
     "lbm_objective_flux", "lbm_adjoint_step", "lbm_ckpt_workspace_bytes", "lbm_flux_forward", "lbm_flux_backward",
     "flux_objective", "new_adjoint", "lbm_macroscopic_noalloc", "lbm_check_finite", "lbm_bandwidth_kernel",
-    "lbm_exact_moments_host",
+    "lbm_exact_moments_host", "lbm_fx_pairs_host",
     "State", "FluxObjective",
 ]
 

@@ -91,6 +91,7 @@ SIGNATURES = {
     "lbm_export_adjacency_rows": [_P, _P, _I64, _P],
     "lbm_check_finite": [_P, _I64, _P],
     "lbm_exact_moments_host": [_P, _I64, _P],
+    "lbm_fx_pairs_host": [_P, _P, _I64, ctypes.c_double, ctypes.c_double, _I, _P, _P],
     "lbm_device_table_bytes": [_P, _I, _PSZ],
     "lbm_lattice_upload": [_P, _I, _P, _SZ, _P],
     "lbm_pdf_bytes": [_P, _I, _PSZ],

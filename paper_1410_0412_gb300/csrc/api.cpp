@@ -350,6 +350,37 @@ int lbm_exact_moments_host(const double* d, int64_t n, double* out) {
   return LBM_OK;
 }
 
+int lbm_fx_pairs_host(const double* d, const double* terms, int64_t n, double qm, double qp, int lp1,
+                      double* out, int* ok) {
+  if (n < 0 || (n > 0 && (!d || !terms || !out || !ok)))
+    return set_error(LBM_ERR_ARG, "d, terms, out or ok is NULL, or n < 0");
+  if (!(std::fabs(qm) < 0.5) || !(std::fabs(qp) < 0.5) || (lp1 && qp != 0.0))
+    return set_error(LBM_ERR_ARG, "qm and qp must lie in (-1/2, 1/2), and qp = 0 when lp1");
+  const int64_t qm_fx = dev::q64_of(qm), qp_fx = dev::q64_of(qp);
+  for (int64_t k = 0; k < n; ++k) {
+    double f[19], p[19];
+    std::memcpy(f, d + 19 * k, sizeof f);
+    const double* t = terms + 10 * k;
+    int64_t Sk[10], D[10], S, Jx, Jy, Jz;
+    const int emax = dev::fx_moments<true>(f, Sk, D, S, Jx, Jy, Jz);
+    double* o = out + 19 * k;
+    ok[k] = dev::fx_class_ok(emax, t[0], t[1], t[2], t[3], t[4], t[5], t[6], t[7], t[8], t[9]) ? 1 : 0;
+    if (!ok[k]) {
+      for (int i = 0; i < 19; ++i) o[i] = 0.0;
+      continue;
+    }
+    const int kx = lp1 ? 4 : 2;
+    const dev::FxClass q = dev::fx_class(emax - kx, t[0], t[1], t[2], t[3], t[4], t[5], t[6], t[7], t[8], t[9]);
+    if (lp1)
+      dev::fx_pairs<true, 4>(q, D, Sk, qm_fx, qp_fx, emax - kx, p);
+    else
+      dev::fx_pairs<false, 2>(q, D, Sk, qm_fx, qp_fx, emax - kx, p);
+    o[0] = static_cast<double>(emax - kx);  // the pair scale es: units of 2^(es - 1080)
+    for (int i = 1; i < 19; ++i) o[i] = p[i];
+  }
+  return LBM_OK;
+}
+
 int lbm_validate_tables(const lbm_lattice* L) {
   if (int rc = check_lat(L)) return rc;
   try {

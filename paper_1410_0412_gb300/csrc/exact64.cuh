@@ -21,6 +21,7 @@
 // moments bit for bit against exact rational arithmetic.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 
@@ -122,16 +123,15 @@ __host__ __device__ __forceinline__ int fx_scale(const uint64_t (&b)[Q]) {
   return emax;
 }
 
-// The moments of one D3Q19 node from its 19 PDFs d (pair k = 1..9 holds the
-// opposite directions 2k-1 and 2k; the first directions of the pairs are
-// (1,0,0) (0,1,0) (0,0,1) (1,1,0) (1,-1,0) (1,0,1) (1,0,-1) (0,1,1) (0,1,-1)):
-// pair sums sa_k (only when NEED_SA) and differences da_k, the density
-// deviation drho = sum d_i and the momentum j = sum c_i d_i, each the double
-// nearest to the exact fixed-point sum.  A node whose scale reaches kFxMaxExp
-// (an Inf, a NaN or |d_i| >= 2^1017) gets drho = NaN.
+// The exact fixed-point moments of one D3Q19 node from its 19 PDFs d (pair
+// k = 1..9 holds the opposite directions 2k-1 and 2k; the first directions of
+// the pairs are (1,0,0) (0,1,0) (0,0,1) (1,1,0) (1,-1,0) (1,0,1) (1,0,-1)
+// (0,1,1) (0,1,-1)) at the node scale emax (returned): pair sums Sk[k] (only
+// when NEED_SA) and differences D[k], the density deviation S = sum d_i and
+// the momentum J = sum c_i d_i, all as integers times 2^(emax - 1080).
 template <bool NEED_SA>
-__host__ __device__ __forceinline__ void exact_moments(const double (&d)[19], double (&sa)[10], double (&da)[10],
-                                                       double& drho, double& jx, double& jy, double& jz) {
+__host__ __device__ __forceinline__ int fx_moments(const double (&d)[19], int64_t (&Sk)[10], int64_t (&D)[10],
+                                                   int64_t& S, int64_t& Jx, int64_t& Jy, int64_t& Jz) {
   uint64_t b[19];
 #pragma unroll
   for (int i = 0; i < 19; ++i) b[i] = dbits(d[i]);
@@ -139,20 +139,162 @@ __host__ __device__ __forceinline__ void exact_moments(const double (&d)[19], do
   int64_t f[19];
 #pragma unroll
   for (int i = 0; i < 19; ++i) f[i] = fx_of(b[i], emax);
-  int64_t S = f[0], D[10];
+  S = f[0];
 #pragma unroll
   for (int k = 1; k <= 9; ++k) {
-    const int64_t Sk = f[2 * k - 1] + f[2 * k];
+    const int64_t s = f[2 * k - 1] + f[2 * k];
     D[k] = f[2 * k - 1] - f[2 * k];
-    S += Sk;
-    if (NEED_SA) sa[k] = fx_to_double(Sk, emax);
+    S += s;
+    if (NEED_SA) Sk[k] = s;
+  }
+  Jx = D[1] + D[4] + D[5] + D[6] + D[7];
+  Jy = D[2] + D[4] - D[5] + D[8] + D[9];
+  Jz = D[3] + D[6] - D[7] + D[8] - D[9];
+  return emax;
+}
+
+// The moments as doubles: pair sums sa_k (only when NEED_SA) and differences
+// da_k, the density deviation drho = sum d_i and the momentum j = sum c_i d_i,
+// each the double nearest to the exact fixed-point sum.  A node whose scale
+// reaches kFxMaxExp (an Inf, a NaN or |d_i| >= 2^1017) gets drho = NaN.
+template <bool NEED_SA>
+__host__ __device__ __forceinline__ void exact_moments(const double (&d)[19], double (&sa)[10], double (&da)[10],
+                                                       double& drho, double& jx, double& jy, double& jz) {
+  int64_t Sk[10], D[10], S, Jx, Jy, Jz;
+  const int emax = fx_moments<NEED_SA>(d, Sk, D, S, Jx, Jy, Jz);
+#pragma unroll
+  for (int k = 1; k <= 9; ++k) {
+    if (NEED_SA) sa[k] = fx_to_double(Sk[k], emax);
     da[k] = fx_to_double(D[k], emax);
   }
   drho = emax < kFxMaxExp ? fx_to_double(S, emax) : dfrom(0x7ff8000000000000ull);
-  jx = fx_to_double(D[1] + D[4] + D[5] + D[6] + D[7], emax);
-  jy = fx_to_double(D[2] + D[4] - D[5] + D[8] + D[9], emax);
-  jz = fx_to_double(D[3] + D[6] - D[7] + D[8] - D[9], emax);
+  jx = fx_to_double(Jx, emax);
+  jy = fx_to_double(Jy, emax);
+  jz = fx_to_double(Jz, emax);
 }
+
+// floor(a * b / 2^64) for signed 64-bit a, b: the product of a Q64 fraction
+// (|a| < 2^63, the value a / 2^64) with a fixed-point value, at the latter's scale.
+__host__ __device__ __forceinline__ int64_t mulhi_q64(int64_t a, int64_t b) {
+#ifdef __CUDA_ARCH__
+  return __mul64hi(a, b);
+#else
+  return static_cast<int64_t>((static_cast<__int128>(a) * b) >> 64);
+#endif
+}
+
+// Biased exponent field of a double.
+__host__ __device__ __forceinline__ int dexp(double x) { return static_cast<int>(dbits(x) >> 52) & 0x7ff; }
+
+// The pair update of the FP64 collision in fixed point (scale 2^(emax - 1080),
+// the node's moment scale).  Given the class values of the TRT collision with
+// Guo forcing -- the velocity u, the even constant K0 and the vectors T and O
+// of the axis class (the diagonal class uses them halved) -- and the exact
+// pair sums Sk and differences Dk, the post-collision pair is
+//   e = K0 + (c.u)(c.T) [+ qp Sk],  o = qm Dk + c.O,  p_a = e + o,  p_b = e - o,
+// with qm = (1 - l-)/2 and qp = (1 - l+)/2 as Q64 fractions.  The pair stage
+// works at a scale kx bits finer than the moments, 2^(es - 1080) with
+// es = emax - kx (kx = 4 when qp = 0, else 2): Dk and Sk enter shifted left by
+// kx, exactly.  Every sum is exact; the products (c.u)(c.T), qm Dk and qp Sk
+// are truncated to the scale (floor), and so are u, K0, T and O when they
+// enter.  The error of p before its one rounding to double is below 8 units
+// of 2^(es - 1080), i.e. below 2^-(54 + kx) of B = 2^(emax - 1023), the
+// binade of the node's largest PDF (for PDFs near w_i rho, below a quarter of
+// an ulp of the smallest, the diagonal ones, when kx = 4).
+//
+// Valid when |u_a| < 1/4 (biased exponent <= 1020), |K0| < B/2 (exponent
+// <= emax - 2) and |T_a|, |O_a| < B/4 (exponent <= emax - 3); with every
+// |d_i| < 2B this keeps |c.u| < 1/2 and every intermediate below 2^63 at
+// either kx.  fx_class_ok checks it.
+struct FxClass {
+  int64_t ux, uy, uz;  // Q64
+  int64_t K0, Tx, Ty, Tz, Ox, Oy, Oz;
+};
+
+__host__ __device__ __forceinline__ bool fx_class_ok(int emax, double ux, double uy, double uz, double K0, double Tx,
+                                                     double Ty, double Tz, double Ox, double Oy, double Oz) {
+  int eu = dexp(ux);
+  eu = dexp(uy) > eu ? dexp(uy) : eu;
+  eu = dexp(uz) > eu ? dexp(uz) : eu;
+  int eto = dexp(Tx);
+  const double v[5] = {Ty, Tz, Ox, Oy, Oz};
+#pragma unroll
+  for (int i = 0; i < 5; ++i) eto = dexp(v[i]) > eto ? dexp(v[i]) : eto;
+  return emax < kFxMaxExp && eu <= 1020 && dexp(K0) <= emax - 2 && eto <= emax - 3;
+}
+
+// The class values at the pair scale es (see above).
+__host__ __device__ __forceinline__ FxClass fx_class(int es, double ux, double uy, double uz, double K0, double Tx,
+                                                     double Ty, double Tz, double Ox, double Oy, double Oz) {
+  FxClass q;
+  q.ux = fx_of(dbits(ux), 1016);  // u * 2^64
+  q.uy = fx_of(dbits(uy), 1016);
+  q.uz = fx_of(dbits(uz), 1016);
+  q.K0 = fx_of(dbits(K0), es);
+  q.Tx = fx_of(dbits(Tx), es);
+  q.Ty = fx_of(dbits(Ty), es);
+  q.Tz = fx_of(dbits(Tz), es);
+  q.Ox = fx_of(dbits(Ox), es);
+  q.Oy = fx_of(dbits(Oy), es);
+  q.Oz = fx_of(dbits(Oz), es);
+  return q;
+}
+
+// c . v for a direction with components X, Y, Z in {-1, 0, 1} (exact integer sums).
+template <int X, int Y, int Z>
+__host__ __device__ __forceinline__ int64_t fx_cdot(int64_t vx, int64_t vy, int64_t vz) {
+  int64_t acc = 0;
+  if (X) acc = X > 0 ? vx : -vx;
+  if (Y) acc = X ? (Y > 0 ? acc + vy : acc - vy) : (Y > 0 ? vy : -vy);
+  if (Z) acc = (X || Y) ? (Z > 0 ? acc + vz : acc - vz) : (Z > 0 ? vz : -vz);
+  return acc;
+}
+
+// Pair with first direction (X, Y, Z): DIAG for the face diagonals (weight
+// 1/36: K0, T and O halved), LP1 when qp = 0.
+template <int X, int Y, int Z, bool DIAG, bool LP1>
+__host__ __device__ __forceinline__ void fx_pair(const FxClass& q, int64_t Dk, int64_t Sk, int64_t qm, int64_t qp,
+                                                 int es, double& pa, double& pb) {
+  const int64_t cu = fx_cdot<X, Y, Z>(q.ux, q.uy, q.uz);
+  const int64_t ct = fx_cdot<X, Y, Z>(q.Tx, q.Ty, q.Tz);
+  const int64_t co = fx_cdot<X, Y, Z>(q.Ox, q.Oy, q.Oz);
+  int64_t e = q.K0 + mulhi_q64(cu, ct);
+  int64_t o = mulhi_q64(qm, Dk);
+  if (DIAG) {
+    e >>= 1;
+    o += co >> 1;
+  } else {
+    o += co;
+  }
+  if (!LP1) e += mulhi_q64(qp, Sk);
+  pa = fx_to_double(e + o, es);
+  pb = fx_to_double(e - o, es);
+}
+
+// The nine pairs in the direction order of the lattice (see fx_moments), from
+// the moment-scale D and Sk of fx_moments; es = emax - KX.
+template <bool LP1, int KX>
+__host__ __device__ __forceinline__ void fx_pairs(const FxClass& q, const int64_t (&D)[10], const int64_t (&Sk)[10],
+                                                  int64_t qm, int64_t qp, int es, double (&p)[19]) {
+  int64_t Df[10], Sf[10];
+#pragma unroll
+  for (int k = 1; k <= 9; ++k) {
+    Df[k] = static_cast<int64_t>(static_cast<uint64_t>(D[k]) << KX);
+    Sf[k] = LP1 ? 0 : static_cast<int64_t>(static_cast<uint64_t>(Sk[k]) << KX);
+  }
+  fx_pair<1, 0, 0, false, LP1>(q, Df[1], Sf[1], qm, qp, es, p[1], p[2]);
+  fx_pair<0, 1, 0, false, LP1>(q, Df[2], Sf[2], qm, qp, es, p[3], p[4]);
+  fx_pair<0, 0, 1, false, LP1>(q, Df[3], Sf[3], qm, qp, es, p[5], p[6]);
+  fx_pair<1, 1, 0, true, LP1>(q, Df[4], Sf[4], qm, qp, es, p[7], p[8]);
+  fx_pair<1, -1, 0, true, LP1>(q, Df[5], Sf[5], qm, qp, es, p[9], p[10]);
+  fx_pair<1, 0, 1, true, LP1>(q, Df[6], Sf[6], qm, qp, es, p[11], p[12]);
+  fx_pair<1, 0, -1, true, LP1>(q, Df[7], Sf[7], qm, qp, es, p[13], p[14]);
+  fx_pair<0, 1, 1, true, LP1>(q, Df[8], Sf[8], qm, qp, es, p[15], p[16]);
+  fx_pair<0, 1, -1, true, LP1>(q, Df[9], Sf[9], qm, qp, es, p[17], p[18]);
+}
+
+// Q64 image of a rate constant |x| < 1/2: round(x * 2^64).
+inline int64_t q64_of(double x) { return static_cast<int64_t>(std::llround(std::ldexp(x, 64))); }
 
 }  // namespace dev
 }  // namespace lbm

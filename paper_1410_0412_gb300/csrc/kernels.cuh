@@ -176,6 +176,7 @@ template <class R> struct CollConst {
   R abb_in[2], abb_out[2];  // 2 w (rho_bc - rho_s) for w = 1/18 and 1/36
   double abb64_in[2], abb64_out[2];  // the same in double (the double-float odd step's FP64 gather)
   R inv_s;                  // 1 / storage scale of the scaled collision (see make_coll_step)
+  long long qm_fx, qp_fx;   // qm and qp as Q64 fractions (the FP64 fixed-point pair update)
   bool gx;                  // the body force points along x (g_y = g_z = 0)
 };
 
@@ -203,6 +204,8 @@ template <class R> inline CollConst<R> make_coll(const KParams& kp) {
   }
   c.rho_s = R(kp.rho_s);
   c.inv_s = R(1.0f);
+  c.qm_fx = q64_of((1.0 - kp.lm) / 2);
+  c.qp_fx = q64_of((1.0 - kp.lp) / 2);
   c.gx = kp.g[1] == 0.0 && kp.g[2] == 0.0;
   for (int k = 0; k < 2; ++k) {
     const double w = k == 0 ? 1.0 / 18.0 : 1.0 / 36.0;
@@ -329,16 +332,16 @@ __device__ __forceinline__ double halve(double x) { return halve_exact(x); }
 __device__ __forceinline__ float halve(float x) { return half(x); }
 __device__ __forceinline__ df halve(df x) { return half(x); }
 
-// s: Brinkman solid fraction of the node (DRAG only).  LP1: the caller knows
-// l+ = 1, so (1 - l+)/2 = 0 and 1 - l+ = 0: the even parts relax fully to
-// equilibrium, and the ten products with those zeros are skipped
-// (fma(0, x, e) = e, so the values are unchanged).
-// SC: the PDFs are in storage units (make_coll_step); rho and j are scaled back.
-// collide_m: the collision from given moments (sa only read when !LP1; d[0]
-// only read when !LP1).
-template <class R, bool FORCE, bool DRAG, bool LP1 = false>
-__device__ __forceinline__ void collide_m(R (&d)[kQ], const CollConst<R>& c, const R s, const R (&sa)[10],
-                                          const R (&da)[10], const R drho, const R jx, const R jy, const R jz) {
+// The per-node terms of the collision: the velocity u and the axis-class
+// even constant K0 and vectors T and O (the face diagonals use them halved).
+template <class R> struct NodeTerms {
+  R ux, uy, uz, K0a, Tx, Ty, Tz, Ox, Oy, Oz;
+};
+
+// s: Brinkman solid fraction of the node (DRAG only).
+template <class R, bool FORCE, bool DRAG>
+__device__ __forceinline__ NodeTerms<R> node_terms(const CollConst<R>& c, const R s, const R drho, const R jx,
+                                                   const R jy, const R jz) {
   using ::fma;
   const R rho = c.rho_s + drho;
   const R irho = recip(rho);
@@ -402,6 +405,20 @@ __device__ __forceinline__ void collide_m(R (&d)[kQ], const CollConst<R>& c, con
     Oy = K2a * uy;
     Oz = K2a * uz;
   }
+  return NodeTerms<R>{ux, uy, uz, K0a, Tx, Ty, Tz, Ox, Oy, Oz};
+}
+
+// The nine pairs and the rest PDF from the node terms.  LP1: the caller knows
+// l+ = 1, so (1 - l+)/2 = 0 and 1 - l+ = 0: the even parts relax fully to
+// equilibrium, and the ten products with those zeros are skipped
+// (fma(0, x, e) = e, so the values are unchanged).  sa and d[0] are only read
+// when !LP1.
+template <class R, bool LP1>
+__device__ __forceinline__ void pair_terms(R (&d)[kQ], const CollConst<R>& c, const NodeTerms<R>& t,
+                                           const R (&sa)[10], const R (&da)[10]) {
+  using ::fma;
+  const R ux = t.ux, uy = t.uy, uz = t.uz, K0a = t.K0a;
+  const R Tx = t.Tx, Ty = t.Ty, Tz = t.Tz, Ox = t.Ox, Oy = t.Oy, Oz = t.Oz;
   // axis pairs (weight 1/18)
   coll_pair<R, 1, LP1>(d, sa[1], da[1], ux, uy, uz, K0a, Tx, Ty, Tz, Ox, Oy, Oz, c.qp, c.qm);
   coll_pair<R, 2, LP1>(d, sa[2], da[2], ux, uy, uz, K0a, Tx, Ty, Tz, Ox, Oy, Oz, c.qp, c.qm);
@@ -420,8 +437,48 @@ __device__ __forceinline__ void collide_m(R (&d)[kQ], const CollConst<R>& c, con
   d[0] = LP1 ? 6.0f * K0a : fma(c.omlp, d[0], 6.0f * K0a);
 }
 
+// collide_m: the collision from given moments.
+template <class R, bool FORCE, bool DRAG, bool LP1 = false>
+__device__ __forceinline__ void collide_m(R (&d)[kQ], const CollConst<R>& c, const R s, const R (&sa)[10],
+                                          const R (&da)[10], const R drho, const R jx, const R jy, const R jz) {
+  pair_terms<R, LP1>(d, c, node_terms<R, FORCE, DRAG>(c, s, drho, jx, jy, jz), sa, da);
+}
+
+// The FP64 collision: exact fixed-point moments (exact64.cuh), the node terms
+// in FP64, and the pair update in fixed point on the integer pipe when the
+// node's values are in its range (fx_class_ok; a warp-uniform branch),
+// otherwise in FP64 from the moments rounded to double.  NaN or Inf PDFs
+// take the FP64 branch and come out NaN.
+template <bool FORCE, bool DRAG, bool LP1>
+__device__ __forceinline__ void collide_f64(double (&d)[kQ], const CollConst<double>& c, const double s) {
+  int64_t Sk[10], D[10], S, Jx, Jy, Jz;
+  const int emax = fx_moments<!LP1>(d, Sk, D, S, Jx, Jy, Jz);
+  const double drho = emax < kFxMaxExp ? fx_to_double(S, emax) : dfrom(0x7ff8000000000000ull);
+  const NodeTerms<double> t = node_terms<double, FORCE, DRAG>(c, s, drho, fx_to_double(Jx, emax),
+                                                              fx_to_double(Jy, emax), fx_to_double(Jz, emax));
+  const bool ok = fx_class_ok(emax, t.ux, t.uy, t.uz, t.K0a, t.Tx, t.Ty, t.Tz, t.Ox, t.Oy, t.Oz);
+  if (__all_sync(__activemask(), ok)) {
+    constexpr int kx = LP1 ? 4 : 2;
+    const FxClass q = fx_class(emax - kx, t.ux, t.uy, t.uz, t.K0a, t.Tx, t.Ty, t.Tz, t.Ox, t.Oy, t.Oz);
+    fx_pairs<LP1, kx>(q, D, Sk, c.qm_fx, c.qp_fx, emax - kx, d);
+    d[0] = LP1 ? 6.0 * t.K0a : ::fma(c.omlp, d[0], 6.0 * t.K0a);
+  } else {
+    double sa[10], da[10];
+#pragma unroll
+    for (int k = 1; k <= 9; ++k) {
+      if (!LP1) sa[k] = fx_to_double(Sk[k], emax);
+      da[k] = fx_to_double(D[k], emax);
+    }
+    pair_terms<double, LP1>(d, c, t, sa, da);
+  }
+}
+
 template <class R, bool FORCE, bool DRAG, bool LP1 = false, bool SC = false>
 __device__ __forceinline__ void collide(R (&d)[kQ], const CollConst<R>& c, const R s) {
+  if constexpr (std::is_same<R, double>::value) {
+    collide_f64<FORCE, DRAG, LP1>(d, c, s);
+    return;
+  }
   R sa[10], da[10], drho, jx, jy, jz;
   moments<R, !LP1>(d, sa, da, drho, jx, jy, jz);
   if (SC) {  // storage units -> physical units for the moments
