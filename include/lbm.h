@@ -338,14 +338,16 @@ LBM_API int lbm_exact_moments_host(const double* d, int64_t n, double* out);
  * tied to the node's largest PDF, with one rounding to double per output,
  * whenever the node's values lie in that scale's range; this runs the same
  * routine on the host.  d: host double [n][19] (node-major); terms: host
- * double [n][10]: ux, uy, uz, K0, Tx, Ty, Tz, Ox, Oy, Oz; lp1: 1 for the
- * l+ = 1 form (qp must be 0).  out: host double [n][19]: out[0] = es, out[1..18]
+ * double [n][10]: ux, uy, uz, K0, Tx, Ty, Tz, Ox, Oy, Oz; flags: bit 0 for
+ * the l+ = 1 form (qp must be 0), bit 1 to take the general conversions
+ * everywhere (the kernels take shorter ones for positive values in a common
+ * range; the results are the same bits).  out: host double [n][19]: out[0] = es, out[1..18]
  * the post-collision pair values; ok: host int [n], 0 where the node is
  * outside the range (out is then 0; the kernels take the FP64 update there).
  * Each value is within 8 units of 2^(es - 1080) of the exact rational result,
  * before its rounding to nearest.  LBM_ERR_ARG for NULL pointers, n < 0, or
  * |qm| or |qp| >= 1/2. */
-LBM_API int lbm_fx_pairs_host(const double* d, const double* terms, int64_t n, double qm, double qp, int lp1,
+LBM_API int lbm_fx_pairs_host(const double* d, const double* terms, int64_t n, double qm, double qp, int flags,
                               double* out, int* ok);
 
 /* Check the host tables: entries in range, adjacency reciprocity
@@ -509,6 +511,15 @@ LBM_API int lbm_macroscopic_noalloc(const lbm_lattice* lat, int prec, const lbm_
  * multiple of 16; buffers 16-byte aligned.  One launch, asynchronous. */
 LBM_API int lbm_bandwidth_kernel(int kind, const void* src, void* dst, int64_t bytes_per_array, int arrays,
                                  void* stream);
+
+/* The FP64 pipe's throughput, the compute roof beside the bandwidth roof of
+ * Sect. 5.2 for the native FP64 step (whose arithmetic, not HBM, bounds it on
+ * this GPU).  One launch of `threads` threads (a positive multiple of 256, at
+ * most 2^31), each running 8 independent chains of `iters` fused
+ * multiply-adds x <- fma(x, 1, 1) (8 * threads * iters DFMA in total).  out:
+ * device double [threads]; out[t] = 8 (t mod 1024) + 28 + 8 iters exactly.
+ * iters in [1, 2^24].  Asynchronous on `stream`. */
+LBM_API int lbm_fp64_peak_kernel(double* out, int64_t threads, int iters, void* stream);
 
 /* ---- objective, discrete adjoint and checkpointed gradient ------------------------ */
 /* None of these has a counterpart in the paper: they differentiate the step of

@@ -563,12 +563,13 @@ def lbm_exact_moments_host(d):
     return out
 
 
-def lbm_fx_pairs_host(d, terms, qm, qp, lp1):
+def lbm_fx_pairs_host(d, terms, qm, qp, lp1, general=False):
     """Host image of the FP64 step's fixed-point pair update (``lbm_fx_pairs_host``).
 
     d: [n, 19] PDFs; terms: [n, 10] (ux, uy, uz, K0, Tx, Ty, Tz, Ox, Oy, Oz).
     Returns (out [n, 19], ok [n]): out[:, 0] is the pair scale es and
-    out[:, 1:] the post-collision pair values where ok.
+    out[:, 1:] the post-collision pair values where ok.  ``general`` takes the
+    general conversions everywhere (the same bits as the shorter ones).
     """
     import numpy as np
     a = np.ascontiguousarray(np.asarray(d, dtype=np.float64))
@@ -578,7 +579,8 @@ def lbm_fx_pairs_host(d, terms, qm, qp, lp1):
     out = np.empty((a.shape[0], 19), dtype=np.float64)
     ok = np.empty(a.shape[0], dtype=np.int32)
     check(_lib.load().lbm_fx_pairs_host(a.ctypes.data, t.ctypes.data, a.shape[0], float(qm), float(qp),
-                                        1 if lp1 else 0, out.ctypes.data, ok.ctypes.data), "lbm_fx_pairs_host")
+                                        (1 if lp1 else 0) | (2 if general else 0), out.ctypes.data,
+                                        ok.ctypes.data), "lbm_fx_pairs_host")
     return out, ok.astype(bool)
 
 
@@ -590,6 +592,16 @@ def lbm_bandwidth_kernel(kind, dst, src=None, arrays=1, stream=None):
     per = nbytes // arrays
     check(_lib.load().lbm_bandwidth_kernel(int(kind), _ptr(src), _ptr(dst), per, int(arrays), _stream(stream)),
           "lbm_bandwidth_kernel")
+
+
+def lbm_fp64_peak_kernel(out, iters, stream=None):
+    """One launch of the FP64-pipe throughput kernel over ``out.numel()`` threads
+    (8 DFMA chains of ``iters`` steps each); ``out`` a CUDA float64 tensor."""
+    torch = _torch()
+    if not isinstance(out, torch.Tensor) or not out.is_cuda or out.dtype != torch.float64 or not out.is_contiguous():
+        raise TypeError("out must be a contiguous CUDA float64 tensor")
+    check(_lib.load().lbm_fp64_peak_kernel(_ptr(out), out.numel(), int(iters), _stream(stream)),
+          "lbm_fp64_peak_kernel")
 
 
 def _adjoint_dtype(prec):
@@ -826,7 +838,7 @@ __all__ = [
     "LBM_LAYOUT_ET_EVEN", "LBM_LAYOUT_ET_ODD", "LBM_TABLES_ET", "lbm_step_et", "lbm_run_et", "Partitioning",
     "PartitionedSolver", "lbm_halo_exchange", "lbm_partition_run_aa", "lbm_partition_run_osnt",
     "lbm_objective_flux", "lbm_adjoint_step", "lbm_ckpt_workspace_bytes", "lbm_flux_forward", "lbm_flux_backward",
-    "flux_objective", "new_adjoint", "lbm_macroscopic_noalloc", "lbm_check_finite", "lbm_bandwidth_kernel",
+    "flux_objective", "new_adjoint", "lbm_macroscopic_noalloc", "lbm_check_finite", "lbm_bandwidth_kernel", "lbm_fp64_peak_kernel",
     "lbm_exact_moments_host", "lbm_fx_pairs_host",
     "State", "FluxObjective",
 ]

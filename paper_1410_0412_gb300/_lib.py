@@ -109,6 +109,7 @@ SIGNATURES = {
     "lbm_reduce_workspace_bytes": [_P, _PSZ],
     "lbm_macroscopic": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _P, _P, _P, _P, _P, _SZ, _P],
     "lbm_bandwidth_kernel": [_I, _P, _P, _I64, _I, _P],
+    "lbm_fp64_peak_kernel": [_P, _I64, _I, _P],
     "lbm_macroscopic_noalloc": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _P, _P, _P, _P, _P],
     "lbm_objective_flux": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _P, _P, _P, _P, _P, _SZ, _P],
     "lbm_adjoint_step": [_P, _I, ctypes.POINTER(lbm_params), _P, _P, _P, _P, _P, _I, _P],

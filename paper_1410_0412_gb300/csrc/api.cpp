@@ -350,8 +350,9 @@ int lbm_exact_moments_host(const double* d, int64_t n, double* out) {
   return LBM_OK;
 }
 
-int lbm_fx_pairs_host(const double* d, const double* terms, int64_t n, double qm, double qp, int lp1,
+int lbm_fx_pairs_host(const double* d, const double* terms, int64_t n, double qm, double qp, int flags,
                       double* out, int* ok) {
+  const int lp1 = flags & 1, general = flags & 2;
   if (n < 0 || (n > 0 && (!d || !terms || !out || !ok)))
     return set_error(LBM_ERR_ARG, "d, terms, out or ok is NULL, or n < 0");
   if (!(std::fabs(qm) < 0.5) || !(std::fabs(qp) < 0.5) || (lp1 && qp != 0.0))
@@ -362,7 +363,8 @@ int lbm_fx_pairs_host(const double* d, const double* terms, int64_t n, double qm
     std::memcpy(f, d + 19 * k, sizeof f);
     const double* t = terms + 10 * k;
     int64_t Sk[10], D[10], S, Jx, Jy, Jz;
-    const int emax = dev::fx_moments<true>(f, Sk, D, S, Jx, Jy, Jz);
+    const int emax = !general && dev::fx_pos_near_ok(f) ? dev::fx_moments<true, true>(f, Sk, D, S, Jx, Jy, Jz)
+                                                         : dev::fx_moments<true>(f, Sk, D, S, Jx, Jy, Jz);
     double* o = out + 19 * k;
     ok[k] = dev::fx_class_ok(emax, t[0], t[1], t[2], t[3], t[4], t[5], t[6], t[7], t[8], t[9]) ? 1 : 0;
     if (!ok[k]) {
@@ -372,9 +374,11 @@ int lbm_fx_pairs_host(const double* d, const double* terms, int64_t n, double qm
     const int kx = lp1 ? 4 : 2;
     const dev::FxClass q = dev::fx_class(emax - kx, t[0], t[1], t[2], t[3], t[4], t[5], t[6], t[7], t[8], t[9]);
     if (lp1)
-      dev::fx_pairs<true, 4>(q, D, Sk, qm_fx, qp_fx, emax - kx, p);
+      general ? dev::fx_pairs<true, 4, true>(q, D, Sk, qm_fx, qp_fx, emax - kx, p)
+              : dev::fx_pairs<true, 4>(q, D, Sk, qm_fx, qp_fx, emax - kx, p);
     else
-      dev::fx_pairs<false, 2>(q, D, Sk, qm_fx, qp_fx, emax - kx, p);
+      general ? dev::fx_pairs<false, 2, true>(q, D, Sk, qm_fx, qp_fx, emax - kx, p)
+              : dev::fx_pairs<false, 2>(q, D, Sk, qm_fx, qp_fx, emax - kx, p);
     o[0] = static_cast<double>(emax - kx);  // the pair scale es: units of 2^(es - 1080)
     for (int i = 1; i < 19; ++i) o[i] = p[i];
   }

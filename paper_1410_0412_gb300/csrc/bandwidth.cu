@@ -6,6 +6,8 @@
 //   U-kA:   k arrays updated in place (read, write back), the access pattern of
 //           the AA even step.
 // The arrays are [k][n] slices of one buffer, like the SoA PDF grids.
+// A third kernel measures the FP64 pipe's throughput, the compute roof of the
+// native FP64 step on this GPU.
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -34,10 +36,43 @@ __global__ void __launch_bounds__(kBwBlock) k_bw_update(float4* __restrict__ buf
     }
 }
 
+// FP64 pipe throughput: kFmaChains independent DFMA chains per thread, iters
+// steps each, x <- fma(x, a, b).  With a = b = 1 every chain counts up by one
+// per step exactly (integers below 2^53), so the output is checkable:
+// out[t] = sum over chains c of (t mod 1024 + c + iters).
+constexpr int kFmaChains = 8;
+
+__global__ void __launch_bounds__(kBwBlock) k_fp64_peak(double* __restrict__ out, double a, double b, int iters) {
+  const int64_t t = blockIdx.x * int64_t(kBwBlock) + threadIdx.x;
+  double x[kFmaChains];
+#pragma unroll
+  for (int c = 0; c < kFmaChains; ++c) x[c] = double(t % 1024) + c;
+  for (int k = 0; k < iters; ++k) {
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c) x[c] = ::fma(x[c], a, b);
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int c = 0; c < kFmaChains; ++c) sum += x[c];
+  out[t] = sum;
+}
+
 }  // namespace dev
 }  // namespace lbm
 
 using namespace lbm;
+
+extern "C" int lbm_fp64_peak_kernel(double* out, int64_t threads, int iters, void* stream) {
+  if (!out) return set_error(LBM_ERR_ARG, "out is NULL");
+  if (threads < dev::kBwBlock || threads % dev::kBwBlock || threads > (int64_t(1) << 31))
+    return set_error(LBM_ERR_ARG, "threads must be a positive multiple of 256, at most 2^31");
+  if (iters < 1 || iters > (1 << 24)) return set_error(LBM_ERR_ARG, "iters must lie in [1, 2^24]");
+  auto st = static_cast<cudaStream_t>(stream);
+  dev::k_fp64_peak<<<unsigned(threads / dev::kBwBlock), dev::kBwBlock, 0, st>>>(out, 1.0, 1.0, iters);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(LBM_ERR_CUDA, std::string("fp64 peak kernel: ") + cudaGetErrorString(e));
+  return LBM_OK;
+}
 
 extern "C" int lbm_bandwidth_kernel(int kind, const void* src, void* dst, int64_t bytes_per_array, int arrays,
                                     void* stream) {

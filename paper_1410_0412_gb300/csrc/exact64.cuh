@@ -111,6 +111,56 @@ __host__ __device__ __forceinline__ double fx_to_double(int64_t v, int emax) {
   return dfrom(((static_cast<uint64_t>(emax + 5 - lz) << 52) + m) | s);
 }
 
+// 32-bit funnel shifts (the PTX shf instructions) with a portable host image.
+__host__ __device__ __forceinline__ uint32_t shf_l(uint32_t lo, uint32_t hi, unsigned n) {  // n in [0, 31]
+#ifdef __CUDA_ARCH__
+  return __funnelshift_l(lo, hi, n);
+#else
+  return n ? (hi << n) | (lo >> (32 - n)) : hi;
+#endif
+}
+__host__ __device__ __forceinline__ uint32_t shf_r(uint32_t lo, uint32_t hi, unsigned n) {  // n in [0, 31]
+#ifdef __CUDA_ARCH__
+  return __funnelshift_r(lo, hi, n);
+#else
+  return n ? (lo >> n) | (hi << (32 - n)) : lo;
+#endif
+}
+__host__ __device__ __forceinline__ int clz32(uint32_t a) {
+#ifdef __CUDA_ARCH__
+  return __clz(static_cast<int>(a));
+#else
+  return a ? __builtin_clz(a) : 32;
+#endif
+}
+
+// fx_of for the common case, in 32-bit halves: a positive double (sign bit
+// clear) whose shift sh = emax - e + 5 lies in [5, 31], i.e. within 26
+// binades of the node's largest.  Same value as fx_of (exact here).
+__host__ __device__ __forceinline__ int64_t fx_of_pos_near(uint64_t b, unsigned sh) {
+  const uint32_t hi = static_cast<uint32_t>(b >> 32), lo = static_cast<uint32_t>(b);
+  const uint32_t mh = (hi & 0x000fffffu) | 0x00100000u;  // significand bits 52..32, hidden bit included
+  const uint32_t h10 = shf_l(lo, mh, 10), l10 = lo << 10;  // significand << 10, below 2^63
+  return static_cast<int64_t>((static_cast<uint64_t>(h10 >> sh) << 32) | shf_r(l10, h10, sh));
+}
+
+// fx_to_double for the common case, in 32-bit halves: 2^32 <= v < 2^63 (the
+// high word is a positive int32).  Same bits as fx_to_double.
+__host__ __device__ __forceinline__ double fx_to_double_pos(int64_t v, int emax) {
+  const uint32_t hi = static_cast<uint32_t>(static_cast<uint64_t>(v) >> 32), lo = static_cast<uint32_t>(v);
+  const int lz = clz32(hi);                                // 1..31
+  const uint32_t ah = shf_l(lo, hi, lz), al = lo << lz;    // leading one at bit 63
+  const uint32_t mh = ah >> 11, ml = shf_r(al, ah, 11);    // 53 significant bits
+  // round to nearest, ties to even: the 11 bits below plus 0x3ff plus the
+  // last kept bit reach 2^11 exactly when rounding up
+  const uint32_t up = ((al & 0x7ffu) + 0x3ffu + (ml & 1u)) >> 11;
+  const uint64_t m = ((static_cast<uint64_t>(mh) << 32) | ml) + up;  // may carry to 2^53: exponent + 1
+  return dfrom((static_cast<uint64_t>(emax + 5 - lz) << 52) + m);
+}
+
+// True when fx_to_double_pos applies to v.
+__host__ __device__ __forceinline__ bool fx_pos_wide(int64_t v) { return (v >> 32) >= 1; }
+
 // Node scale of the 19 PDFs: the largest biased exponent, at least kFxMinExp.
 template <int Q>
 __host__ __device__ __forceinline__ int fx_scale(const uint64_t (&b)[Q]) {
@@ -129,16 +179,32 @@ __host__ __device__ __forceinline__ int fx_scale(const uint64_t (&b)[Q]) {
 // (0,1,1) (0,1,-1)) at the node scale emax (returned): pair sums Sk[k] (only
 // when NEED_SA) and differences D[k], the density deviation S = sum d_i and
 // the momentum J = sum c_i d_i, all as integers times 2^(emax - 1080).
-template <bool NEED_SA>
+// FAST: the caller has checked fx_pos_near_ok (positive PDFs within 26
+// binades of the largest), and the conversions take the shorter
+// fx_of_pos_near; the integers are the same.
+template <bool NEED_SA, bool FAST = false>
 __host__ __device__ __forceinline__ int fx_moments(const double (&d)[19], int64_t (&Sk)[10], int64_t (&D)[10],
                                                    int64_t& S, int64_t& Jx, int64_t& Jy, int64_t& Jz) {
   uint64_t b[19];
 #pragma unroll
   for (int i = 0; i < 19; ++i) b[i] = dbits(d[i]);
-  const int emax = fx_scale(b);
   int64_t f[19];
+  int emax;
+  if (FAST) {
+    // positive: the exponent is the high word shifted, no sign to clear
+    emax = kFxMinExp;
 #pragma unroll
-  for (int i = 0; i < 19; ++i) f[i] = fx_of(b[i], emax);
+    for (int i = 0; i < 19; ++i) {
+      const int e = static_cast<int>(b[i] >> 52);
+      emax = e > emax ? e : emax;
+    }
+#pragma unroll
+    for (int i = 0; i < 19; ++i) f[i] = fx_of_pos_near(b[i], static_cast<unsigned>(emax + 5 - static_cast<int>(b[i] >> 52)));
+  } else {
+    emax = fx_scale(b);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) f[i] = fx_of(b[i], emax);
+  }
   S = f[0];
 #pragma unroll
   for (int k = 1; k <= 9; ++k) {
@@ -151,6 +217,23 @@ __host__ __device__ __forceinline__ int fx_moments(const double (&d)[19], int64_
   Jy = D[2] + D[4] - D[5] + D[8] + D[9];
   Jz = D[3] + D[6] - D[7] + D[8] - D[9];
   return emax;
+}
+
+// True when the fast conversions of fx_moments apply: every PDF positive and
+// finite-scaled (node scale below kFxMaxExp) and at most 26 binades below the
+// largest (so fx_of_pos_near's shift stays in [5, 31]).
+__host__ __device__ __forceinline__ bool fx_pos_near_ok(const double (&d)[19]) {
+  uint32_t sgn = 0;
+  int emax = 0, emin = 2047;
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    const uint32_t hi = static_cast<uint32_t>(dbits(d[i]) >> 32);
+    sgn |= hi;
+    const int e = static_cast<int>(hi >> 20);
+    emax = e > emax ? e : emax;
+    emin = e < emin ? e : emin;
+  }
+  return !(sgn & 0x80000000u) && emin >= kFxMinExp && emax < kFxMaxExp && emax - emin <= 26;
 }
 
 // The moments as doubles: pair sums sa_k (only when NEED_SA) and differences
@@ -251,8 +334,10 @@ __host__ __device__ __forceinline__ int64_t fx_cdot(int64_t vx, int64_t vy, int6
 }
 
 // Pair with first direction (X, Y, Z): DIAG for the face diagonals (weight
-// 1/36: K0, T and O halved), LP1 when qp = 0.
-template <int X, int Y, int Z, bool DIAG, bool LP1>
+// 1/36: K0, T and O halved), LP1 when qp = 0.  The two values are converted
+// with fx_to_double_pos when both qualify in every thread of the warp (on the
+// host: in this node), otherwise with fx_to_double; the bits are the same.
+template <int X, int Y, int Z, bool DIAG, bool LP1, bool GENERAL = false>
 __host__ __device__ __forceinline__ void fx_pair(const FxClass& q, int64_t Dk, int64_t Sk, int64_t qm, int64_t qp,
                                                  int es, double& pa, double& pb) {
   const int64_t cu = fx_cdot<X, Y, Z>(q.ux, q.uy, q.uz);
@@ -267,13 +352,23 @@ __host__ __device__ __forceinline__ void fx_pair(const FxClass& q, int64_t Dk, i
     o += co;
   }
   if (!LP1) e += mulhi_q64(qp, Sk);
-  pa = fx_to_double(e + o, es);
-  pb = fx_to_double(e - o, es);
+  const int64_t va = e + o, vb = e - o;
+  bool fast = !GENERAL && fx_pos_wide(va) && fx_pos_wide(vb);
+#ifdef __CUDA_ARCH__
+  fast = __all_sync(__activemask(), fast);
+#endif
+  if (fast) {
+    pa = fx_to_double_pos(va, es);
+    pb = fx_to_double_pos(vb, es);
+  } else {
+    pa = fx_to_double(va, es);
+    pb = fx_to_double(vb, es);
+  }
 }
 
 // The nine pairs in the direction order of the lattice (see fx_moments), from
 // the moment-scale D and Sk of fx_moments; es = emax - KX.
-template <bool LP1, int KX>
+template <bool LP1, int KX, bool GENERAL = false>
 __host__ __device__ __forceinline__ void fx_pairs(const FxClass& q, const int64_t (&D)[10], const int64_t (&Sk)[10],
                                                   int64_t qm, int64_t qp, int es, double (&p)[19]) {
   int64_t Df[10], Sf[10];
@@ -282,15 +377,15 @@ __host__ __device__ __forceinline__ void fx_pairs(const FxClass& q, const int64_
     Df[k] = static_cast<int64_t>(static_cast<uint64_t>(D[k]) << KX);
     Sf[k] = LP1 ? 0 : static_cast<int64_t>(static_cast<uint64_t>(Sk[k]) << KX);
   }
-  fx_pair<1, 0, 0, false, LP1>(q, Df[1], Sf[1], qm, qp, es, p[1], p[2]);
-  fx_pair<0, 1, 0, false, LP1>(q, Df[2], Sf[2], qm, qp, es, p[3], p[4]);
-  fx_pair<0, 0, 1, false, LP1>(q, Df[3], Sf[3], qm, qp, es, p[5], p[6]);
-  fx_pair<1, 1, 0, true, LP1>(q, Df[4], Sf[4], qm, qp, es, p[7], p[8]);
-  fx_pair<1, -1, 0, true, LP1>(q, Df[5], Sf[5], qm, qp, es, p[9], p[10]);
-  fx_pair<1, 0, 1, true, LP1>(q, Df[6], Sf[6], qm, qp, es, p[11], p[12]);
-  fx_pair<1, 0, -1, true, LP1>(q, Df[7], Sf[7], qm, qp, es, p[13], p[14]);
-  fx_pair<0, 1, 1, true, LP1>(q, Df[8], Sf[8], qm, qp, es, p[15], p[16]);
-  fx_pair<0, 1, -1, true, LP1>(q, Df[9], Sf[9], qm, qp, es, p[17], p[18]);
+  fx_pair<1, 0, 0, false, LP1, GENERAL>(q, Df[1], Sf[1], qm, qp, es, p[1], p[2]);
+  fx_pair<0, 1, 0, false, LP1, GENERAL>(q, Df[2], Sf[2], qm, qp, es, p[3], p[4]);
+  fx_pair<0, 0, 1, false, LP1, GENERAL>(q, Df[3], Sf[3], qm, qp, es, p[5], p[6]);
+  fx_pair<1, 1, 0, true, LP1, GENERAL>(q, Df[4], Sf[4], qm, qp, es, p[7], p[8]);
+  fx_pair<1, -1, 0, true, LP1, GENERAL>(q, Df[5], Sf[5], qm, qp, es, p[9], p[10]);
+  fx_pair<1, 0, 1, true, LP1, GENERAL>(q, Df[6], Sf[6], qm, qp, es, p[11], p[12]);
+  fx_pair<1, 0, -1, true, LP1, GENERAL>(q, Df[7], Sf[7], qm, qp, es, p[13], p[14]);
+  fx_pair<0, 1, 1, true, LP1, GENERAL>(q, Df[8], Sf[8], qm, qp, es, p[15], p[16]);
+  fx_pair<0, 1, -1, true, LP1, GENERAL>(q, Df[9], Sf[9], qm, qp, es, p[17], p[18]);
 }
 
 // Q64 image of a rate constant |x| < 1/2: round(x * 2^64).

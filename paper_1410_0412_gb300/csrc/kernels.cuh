@@ -452,7 +452,10 @@ __device__ __forceinline__ void collide_m(R (&d)[kQ], const CollConst<R>& c, con
 template <bool FORCE, bool DRAG, bool LP1>
 __device__ __forceinline__ void collide_f64(double (&d)[kQ], const CollConst<double>& c, const double s) {
   int64_t Sk[10], D[10], S, Jx, Jy, Jz;
-  const int emax = fx_moments<!LP1>(d, Sk, D, S, Jx, Jy, Jz);
+  // the shorter conversions when every node of the warp has positive PDFs
+  // within 26 binades of its largest (full-f storage near equilibrium)
+  const int emax = __all_sync(__activemask(), fx_pos_near_ok(d)) ? fx_moments<!LP1, true>(d, Sk, D, S, Jx, Jy, Jz)
+                                                                 : fx_moments<!LP1>(d, Sk, D, S, Jx, Jy, Jz);
   const double drho = emax < kFxMaxExp ? fx_to_double(S, emax) : dfrom(0x7ff8000000000000ull);
   const NodeTerms<double> t = node_terms<double, FORCE, DRAG>(c, s, drho, fx_to_double(Jx, emax),
                                                               fx_to_double(Jy, emax), fx_to_double(Jz, emax));

@@ -101,6 +101,20 @@ def test_fx_pairs_is_as_tight_as_a_quarter_ulp_at_rest_scale():
             assert err <= Fraction(3, 4) * Fraction(float(_ulp(float(ex[i])))), (n, i)
 
 
+@pytest.mark.parametrize("lp1", [True, False])
+@pytest.mark.parametrize("shifted", [False, True])
+def test_fx_pairs_short_conversions_give_the_same_bits(lp1, shifted):
+    # the kernels convert positive values in a common range with shorter
+    # routines (moments: positive PDFs within 26 binades of the largest;
+    # outputs: 2^32 <= v < 2^63); they must give the general routines' bits
+    d, terms = _nodes(2000, 20 + shifted + 2 * lp1, shifted)
+    qp = 0.0 if lp1 else 0.125
+    fast, ok1 = lbm.lbm_fx_pairs_host(d, terms, -1.0 / 14.0, qp, lp1)
+    gen, ok2 = lbm.lbm_fx_pairs_host(d, terms, -1.0 / 14.0, qp, lp1, general=True)
+    assert ok1.all() and ok2.all()
+    assert np.array_equal(fast.view(np.uint64), gen.view(np.uint64))
+
+
 def test_fx_pairs_refuses_values_outside_its_range():
     d, terms = _nodes(6, 11, False)
     B = 2.0 ** np.floor(np.log2(np.abs(d).max(1)))

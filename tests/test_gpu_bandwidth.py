@@ -1,7 +1,9 @@
 """What the pattern-specific bandwidth kernels write (Sect. 5.2, Table 3).
 
 CNT-kA copies k arrays with streaming stores and U-kA updates k arrays in
-place; their GB/s figures are the roofline denominators P = b / B_l.  A kernel
+place; their GB/s figures are the roofline denominators P = b / B_l.  The
+FP64 throughput kernel (the compute roof of the native FP64 step) is checked
+the same way: its chains count exactly.  A kernel
 that skipped part of its work would only look faster, so these tests read back
 every byte: after CNT-kA each of the k destination arrays equals its source
 bit for bit; after U-kA every float of the k arrays has grown by exactly 1
@@ -65,3 +67,16 @@ def test_bandwidth_kernel_rejects_bad_sizes():
         rc = _lib.load().lbm_bandwidth_kernel(kind, ctypes.c_void_p(buf.data_ptr()), ctypes.c_void_p(buf.data_ptr()),
                                               ctypes.c_int64(per), arrays, ctypes.c_void_p(0))
         assert rc == _lib.LBM_ERR_ARG
+
+
+def test_fp64_peak_kernel_counts_every_fma():
+    """The FP64 throughput kernel: 8 chains of x <- fma(x, 1, 1) per thread, so
+    each thread's output is 8 (t mod 1024) + 28 + 8 iters, exactly."""
+    threads, iters = 152 * 256 * 2, 1000
+    out = torch.full((threads,), float("nan"), dtype=torch.float64, device="cuda")
+    lbm.lbm_fp64_peak_kernel(out, iters)
+    torch.cuda.synchronize()
+    t = torch.arange(threads, device="cuda", dtype=torch.float64)
+    assert torch.equal(out, 8 * torch.remainder(t, 1024) + 28 + 8 * iters)
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_fp64_peak_kernel(out[:100], iters)
