@@ -35,22 +35,18 @@ import geometry  # noqa: E402
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-# FP64 pipe of GB300: 152 SMs x 2 DP lanes/clk x 2.07 GHz (measured 0.60 T DFMA/s burst)
-FP64_PEAK_GINSTR = 152 * 2 * 2.07e9 / 1e9
 # FP64-pipe instructions per node of the AA steps with a uniform body force
-# along x (adds, multiplies, FMAs and the reciprocal's Newton steps each take
-# one FP64 slot; the moments and the halvings run on the integer pipe), counted
-# by ncu (smsp__sass_thread_inst_executed_op_{dadd,dfma,dmul}_pred_on.sum over
-# the nodes), the same for the even and odd step: 91 in general (37 DADD,
-# 41 DFMA, 13 DMUL); 81 when omega_plus = 1, where the kernels skip the ten
-# products with (1 - l+)/2 = 0 and 1 - l+ = 0 (37 DADD, 31 DFMA, 13 DMUL).
-COLL_DP_INSTR_GENERAL = 91
-COLL_DP_INSTR_UNIT_OMEGA = 81
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
-# dominant kernel, the FP64 AA odd step with RIA (l+ = 1 collision), on the
-# 10,896,954-node bed: 1,823,148,032 + 1,595,339,520 from one ncu capture of
-# this kernel version (313.7 B/node against the model's 319.7).
-TRAFFIC_AA_ODD_RIA_F64 = 1823148032 + 1595339520
+# along x, counted by ncu (smsp__sass_thread_inst_executed_op_{dadd,dfma,dmul}
+# _pred_on.sum over the nodes of one launch), the same for the even and odd
+# step.  The moments and the pair update run on the integer pipe in fixed
+# point; what stays on the FP64 pipe is the per-node terms (density, the
+# reciprocal's Newton steps, velocity, K0, T, O) and the rest PDF.
+COLL_DP_INSTR_GENERAL = 32
+COLL_DP_INSTR_UNIT_OMEGA = 28
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a
+# kernel on the 10,896,954-node bed, from an ncu capture of the current kernel
+# version, with the profile that holds it; kernels not listed print null.
+TRAFFIC_PROFILED = {}
 
 WORKLOAD = dict(name="packed_bed_256_rsa_r12", X=256, Y=256, Z=256, radius=12.0, seed=1, rejections=20000,
                 periodic=(1, 0, 0), g=(1e-6, 0.0, 0.0), omega_plus=1.0, magic=3.0 / 16.0)
@@ -109,6 +105,189 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def fp64_pipe_peak(lbm, torch, dev, stream, seconds=1.0):
+    """Measured FP64-pipe throughput: the library's DFMA-chain kernel timed with
+    CUDA events over about ``seconds``, with the SM clock sampled meanwhile."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    threads = sms * 8 * 256
+    out = torch.empty(threads, dtype=torch.float64, device=dev)
+    iters = 2048
+    for _ in range(2):
+        lbm.lbm_fp64_peak_kernel(out, iters, stream)
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    lbm.lbm_fp64_peak_kernel(out, iters, stream)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    reps = max(3, int(seconds / max(a.elapsed_time(b) / 1e3, 1e-6)))
+    with Clocks(dev.index if dev.index is not None else 0) as clk:
+        a.record(stream)
+        for _ in range(reps):
+            lbm.lbm_fp64_peak_kernel(out, iters, stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b)
+    c = clk.summary()
+    g = 8 * threads * iters * reps / (ms / 1e3) / 1e9
+    return {"G_dfma_per_s": g, "sm_mhz": c.get("sm_mhz"), "samples": c.get("samples"), "launches": reps,
+            "what": "lbm_fp64_peak_kernel: 8 independent DFMA chains per thread, 8 CTAs of 256 threads per SM, "
+                    "CUDA events"}
+
+
+class NvmlEnergy:
+    """Board energy from NVML's cumulative counter (read only), through ctypes."""
+
+    def __init__(self, torch, dev):
+        import ctypes
+        self.ok = False
+        try:
+            self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.lib.nvmlInit_v2() != 0:
+                return
+            want = str(torch.cuda.get_device_properties(dev).uuid)
+            n = ctypes.c_uint(0)
+            self.lib.nvmlDeviceGetCount_v2(ctypes.byref(n))
+            buf = ctypes.create_string_buffer(96)
+            for i in range(n.value):
+                h = ctypes.c_void_p()
+                if self.lib.nvmlDeviceGetHandleByIndex_v2(i, ctypes.byref(h)) != 0:
+                    continue
+                if self.lib.nvmlDeviceGetUUID(h, buf, 96) != 0:
+                    continue
+                if buf.value.decode().replace("GPU-", "") == want.replace("GPU-", ""):
+                    self.handle = h
+                    self.ok = True
+                    break
+        except Exception:
+            self.ok = False
+
+    def millijoules(self):
+        import ctypes
+        if not self.ok:
+            return None
+        v = ctypes.c_ulonglong(0)
+        if self.lib.nvmlDeviceGetTotalEnergyConsumption(self.handle, ctypes.byref(v)) != 0:
+            return None
+        return int(v.value)
+
+
+def energy_leg(lbm, torch, lat, dev, stream, seconds=5.0):
+    """Energy to solution of AA-R pairs (the paper's J per lattice update,
+    Sect. 5.5) in FP64, FP32 and FP16S: a region of at least ``seconds`` per
+    precision, board energy from NVML's counter before and after, power also
+    sampled by nvidia-smi every 100 ms."""
+    w = WORKLOAD
+    nv = NvmlEnergy(torch, dev)
+    out = {}
+    for prec in ("f64", "f32", "f16s"):
+        params = lbm.Params(omega_plus=w["omega_plus"], magic=w["magic"], g=w["g"], shifted=(prec != "f64"))
+        sv = lbm.Solver(lat, prec, params, form="aa", ria=True)
+        sv.init_equilibrium(1.0)
+        sv.step(8, stream)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sv.step(20, stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        pair_s = a.elapsed_time(b) / 1e3 / 10
+        pairs = int(seconds / pair_s) + 1
+        with Clocks(dev.index if dev.index is not None else 0, period_ms=100) as clk:
+            e0 = nv.millijoules()
+            a.record(stream)
+            sv.step(2 * pairs, stream)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            e1 = nv.millijoules()
+        sec = a.elapsed_time(b) / 1e3
+        gflup = 2 * lat.N * pairs / 1e9
+        c = clk.summary()
+        rec = {"seconds": sec, "pairs": pairs, "GFLUPs": gflup / sec, "smi_mean_power_w": c.get("power_w_mean"),
+               "smi_samples": c.get("samples"), "sm_mhz": c.get("sm_mhz")}
+        if e0 is not None and e1 is not None:
+            J = (e1 - e0) / 1e3
+            rec.update({"J": J, "J_per_GFLUP": J / gflup, "mean_power_w": J / sec,
+                        "source": "NVML total energy counter"})
+        elif c.get("power_w_mean"):
+            J = c["power_w_mean"] * sec
+            rec.update({"J": J, "J_per_GFLUP": J / gflup, "mean_power_w": c["power_w_mean"],
+                        "source": "nvidia-smi power.draw at 10 Hz"})
+        out[prec] = rec
+        del sv
+        torch.cuda.empty_cache()
+    return out
+
+
+def precision_leg(lbm, torch, lat, dev, stream, steps=1000):
+    """FP32 and FP16S storage against FP64 on the same workload (AA-R, from rest,
+    ``steps`` steps): PDF max-norm, velocity max and L2, and mass."""
+    w = WORKLOAD
+    res = {}
+    ref = None
+    for prec in ("f64", "f32", "f16s"):
+        params = lbm.Params(omega_plus=w["omega_plus"], magic=w["magic"], g=w["g"], shifted=(prec != "f64"))
+        sv = lbm.Solver(lat, prec, params, form="aa", ria=True)
+        sv.init_equilibrium(1.0)
+        sv.step(steps, stream)
+        F = sv.canonical(stream)
+        rho, u, sums = sv.macroscopic(stream=stream)
+        if ref is None:
+            ref = (F, u, float(sums[0]))
+        else:
+            Fr, ur, mr = ref
+            res[prec] = {"pdf_max_rel": float((F - Fr).abs().max() / Fr.abs().max()),
+                         "u_max_rel": float((u - ur).abs().max() / ur.abs().max()),
+                         "u_l2_rel": float((u - ur).norm() / ur.norm()),
+                         "mass_rel": abs(float(sums[0]) - mr) / mr}
+        del sv, F, rho, u
+        torch.cuda.empty_cache()
+    res["steps"] = steps
+    res["max_u_f64"] = float(ref[1].abs().max())
+    res["what"] = ("AA-R from rest at rho = 1 on the same bed; errors relative to the FP64 run's max-norm "
+                   "(PDFs, velocity) or L2 norm (velocity); FP32 and FP16S store f - w rho0")
+    return res
+
+
+def adjoint_leg(lbm, torch, solid, dev, T=100, K=10):
+    """Cost of the checkpointed discrete adjoint on a z < 64 slab of the bed: the
+    forward (T steps with checkpoints) and the backward pass (recomputation plus
+    T adjoint steps), FP64 and FP32 storage, and the FP32 gradient's error."""
+    w = WORKLOAD
+    crop = np.ascontiguousarray(solid[:64])
+    lat = lbm.Lattice(crop, periodic=w["periodic"], enum="lex", B=1).upload(device=dev)
+    s = torch.as_tensor(geometry.node_field(geometry.smooth_noise(crop.shape[2], crop.shape[1], crop.shape[0], 3.0,
+                                                                  2), lat.tables(adj=False, runs=False)["node_xyz"]),
+                        device=dev).float()
+    out = {"fluid_nodes": lat.N, "T": T, "K": K}
+    grads = {}
+    for prec in ("f64", "f32"):
+        params = lbm.Params(omega_plus=1.0, magic=3 / 16, g=(1e-5, 0.0, 0.0), shifted=True)
+        G0 = lat.new_grid(prec, device=dev)
+        lbm.lbm_init_equilibrium(lat, prec, params, G0, lbm.LBM_LAYOUT_OSNT, 1.0)
+        nb = lbm.lbm_ckpt_workspace_bytes(lat, prec, T, K)
+        ws = torch.empty((nb + 7) // 8, dtype=torch.float64, device=dev)
+        lbm.lbm_flux_forward(lat, prec, params, G0, s, T, K, ws, ria=True)   # warm-up
+        lbm.lbm_flux_backward(lat, prec, params, s, T, K, ws, ria=True)
+        torch.cuda.synchronize(dev)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        J = lbm.lbm_flux_forward(lat, prec, params, G0, s, T, K, ws, ria=True)
+        e[1].record()
+        grad = lbm.lbm_flux_backward(lat, prec, params, s, T, K, ws, ria=True)
+        e[2].record()
+        torch.cuda.synchronize(dev)
+        fwd, bwd = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+        out[prec] = {"J": float(J), "forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd}
+        grads[prec] = grad.clone()
+        del ws, G0
+        torch.cuda.empty_cache()
+    out["f32_grad_max_rel_vs_f64"] = float((grads["f32"] - grads["f64"]).abs().max() / grads["f64"].abs().max())
+    out["what"] = ("objective J = mean x-momentum after T steps of OS-NT-R with a Brinkman field (smoothed noise, "
+                   "sigma 3, seed 2); backward = recomputation from checkpoints every K steps plus T adjoint steps")
+    return out
+
+
 def make_geometry(box=None):
     w = WORKLOAD
     n = box or w["X"]
@@ -124,15 +303,16 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, period_ms: int = 200):
         self.index = index
+        self.period_ms = period_ms
         self.proc = None
         self.path = os.path.join("/tmp", f"lbm_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -563,7 +743,8 @@ def suite_bed40(args, lbm, torch):
             del sv
             torch.cuda.empty_cache()
     dp = COLL_DP_INSTR_UNIT_OMEGA if w["omega_plus"] == 1.0 else COLL_DP_INSTR_GENERAL
-    out["aa_r_f64_fp64_pipe_frac"] = out["variants"]["aa_r_f64"]["GFLUPs"] * dp / FP64_PEAK_GINSTR
+    fp = fp64_pipe_peak(lbm, torch, torch.device("cuda", 0), torch.cuda.current_stream())
+    out["aa_r_f64_fp64_pipe_frac"] = out["variants"]["aa_r_f64"]["GFLUPs"] * dp / fp["G_dfma_per_s"]
     out["hbm_peak_GBs"] = hbm
     return out
 
@@ -751,23 +932,23 @@ def main():
     dom_name = f"aa_{'odd_ria' if odd_dom else 'even'}_{hp}"
     dom_bl = loop_balance("aa_odd_r" if odd_dom else "aa_even", p, r)
     achieved_gbs = dom_bl * N / (dom_ms / 1e3) / 1e9
-    roofline_hbm = {"kernel": dom_name, "bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved_gbs / hbm,
-                    "traffic": TRAFFIC_AA_ODD_RIA_F64 if (hp == "f64" and args.box is None and N == 10896954
-                                                          and odd_dom) else None,
-                    "peak_kind": hbm_kind, "bytes_per_node": dom_bl,
-                    "kernel_ms": {"even": even_ms, "odd": odd_ms}}
+    prof = TRAFFIC_PROFILED.get((dom_name, N)) if args.box is None else None
+    roofline = {"kernel": dom_name, "bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                "frac": achieved_gbs / hbm, "traffic": prof[0] if prof else None,
+                "traffic_source": prof[1] if prof else None,
+                "peak_kind": f"{hbm_kind} copy bandwidth (STREAM-style), burst",
+                "bytes_per_node": dom_bl, "units_per_launch": N,
+                "kernel_ms": {"even": even_ms, "odd": odd_ms},
+                "step_GBs": (loop_balance("aa_r", p, r) * 2 * N) / (ms / K / 1e3) / 1e9}
     if hp == "f64":
+        # the native FP64 step's second roof: its FP64-pipe work against the
+        # pipe's measured throughput (DFMA chains, CUDA events, clock sampled)
+        fp = fp64_pipe_peak(lbm, torch, dev, stream)
         dp_instr = COLL_DP_INSTR_UNIT_OMEGA if w["omega_plus"] == 1.0 else COLL_DP_INSTR_GENERAL
         dp_rate = dp_instr * N / (dom_ms / 1e3) / 1e9
-        full_bed = (args.box is None and N == 10896954 and odd_dom)
-        roofline = {"kernel": dom_name, "bound": "alu", "achieved": dp_rate, "peak": FP64_PEAK_GINSTR,
-                    "unit": "G FP64-instr/s", "frac": dp_rate / FP64_PEAK_GINSTR,
-                    "traffic": TRAFFIC_AA_ODD_RIA_F64 if full_bed else None,
-                    "peak_kind": "FP64 pipe from unit counts: 152 SM x 2 DP lanes/clk x 2.07 GHz",
-                    "dp_instr_per_node": dp_instr}
-    else:
-        roofline = roofline_hbm
+        roofline["fp64_pipe"] = {"bound": "alu", "achieved": dp_rate, "peak": fp["G_dfma_per_s"],
+                                 "unit": "G FP64-instr/s", "frac": dp_rate / fp["G_dfma_per_s"],
+                                 "dp_instr_per_node": dp_instr, "peak_measured": fp}
 
     # ---- the same pair with the double-float collision (FP64 grids, same FP64 parity bar) -------------
     companion = None
@@ -872,6 +1053,13 @@ def main():
                 del sv
                 torch.cuda.empty_cache()
 
+    # ---- the metric's comparisons: FP32 / FP16S against FP64, the adjoint's cost, energy -------------
+    vs_f64 = adjoint = energy = None
+    if not args.no_variants:
+        vs_f64 = precision_leg(lbm, torch, lat, dev, stream)
+        adjoint = adjoint_leg(lbm, torch, solid, dev)
+        energy = energy_leg(lbm, torch, lat, dev, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         try:
@@ -889,13 +1077,6 @@ def main():
             cpu = {"error": str(e)}
 
     clock_summary = clk.summary()
-    energy = None
-    if clock_summary.get("power_w_mean"):
-        # energy to solution of the timed pairs (board power x time), the GPU
-        # analogue of the paper's J per lattice update (Sect. 5.5)
-        joules = clock_summary["power_w_mean"] * ms / 1e3
-        energy = {"mean_power_w": clock_summary["power_w_mean"], "J": joules,
-                  "J_per_GFLUP": joules / (2 * N * K / 1e9), "source": "nvidia-smi power.draw samples"}
     line = {
         "metric": "sparse D3Q19 TRT AA-R FP64 lattice updates per second" if hp == "f64"
                   else f"sparse D3Q19 TRT AA-R lattice updates per second ({hp} storage)",
@@ -909,8 +1090,8 @@ def main():
                    "step": "AA even + odd with RIA (2 lattice updates)", "parallelism": "replicas" if world > 1
                    else "single GPU", "l2": "inputs larger than L2 (state %.2f GB)" % (19 * lat.Npad * 8 / 1e9),
                    "setup_s": setup_s, "mass_after": mass},
-        "roofline": roofline, "roofline_hbm": roofline_hbm, "f64_double_float": companion,
-        "variants": variants, "cpu_baseline": cpu,
+        "roofline": roofline, "f64_double_float": companion,
+        "variants": variants, "vs_f64": vs_f64, "adjoint": adjoint, "cpu_baseline": cpu,
         "e2e": e2e, "gpu_launches": 2 * K, "clocks": clock_summary, "energy": energy,
         "paper_context": {"what": "the paper's roofline predictions, FP64 on 7 Haswell cores of one ccNUMA domain "
                                   "(Table 4, channel, 2.6 GHz), MFLUP/s; context, not a target",
