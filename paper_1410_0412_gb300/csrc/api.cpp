@@ -100,6 +100,8 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 struct TableLayout {
   size_t adj = 0, run_adj = 0, head_bits = 0, warp_run0 = 0, warp_head0 = 0, et_nb = 0, et_mask = 0;
   size_t et_run_nb = 0, et_run_mask = 0, et_head_bits = 0, et_warp_run0 = 0, et_warp_head0 = 0, total = 0;
+  size_t run_slot = 0;
+  bool has_run_slot = false;
 };
 
 TableLayout table_layout(const lbm_lattice* L, int which) {
@@ -118,6 +120,11 @@ TableLayout table_layout(const lbm_lattice* L, int which) {
     off = align256(off + size_t(std::max<int64_t>(L->nwarps, 1)) * 4);
     t.warp_head0 = off;
     off = align256(off + size_t(std::max<int64_t>(L->nwarps, 1)) * 4);
+    if (L->run_slot_state == 1) {
+      t.run_slot = off;
+      t.has_run_slot = true;
+      off = align256(off + size_t(18) * L->Rpad * 4);
+    }
   }
   if (which & LBM_TABLES_ET) {
     t.et_nb = off;
@@ -400,6 +407,8 @@ int lbm_device_table_bytes(const lbm_lattice* L, int which, size_t* bytes) {
   if (which <= 0 || which > kAllTables) return set_error(LBM_ERR_ARG, "bad table selection");
   if (which & LBM_TABLES_ET)
     if (int rc = derive_et(const_cast<lbm_lattice*>(L))) return rc;
+  if (which & LBM_TABLES_RIA)
+    if (int rc = derive_run_slots(const_cast<lbm_lattice*>(L))) return rc;
   *bytes = table_layout(L, which).total;
   return LBM_OK;
 }
@@ -409,6 +418,8 @@ int lbm_lattice_upload(lbm_lattice* L, int which, void* dev, size_t bytes, void*
   if (which <= 0 || which > kAllTables) return set_error(LBM_ERR_ARG, "bad table selection");
   if (which & LBM_TABLES_ET)
     if (int rc = derive_et(L)) return rc;
+  if (which & LBM_TABLES_RIA)
+    if (int rc = derive_run_slots(L)) return rc;
   TableLayout t = table_layout(L, which);
   if (!dev) return set_error(LBM_ERR_ARG, "device table buffer is NULL");
   if (reinterpret_cast<uintptr_t>(dev) % 256) return set_error(LBM_ERR_ARG, "device table buffer not 256-byte aligned");
@@ -432,8 +443,11 @@ int lbm_lattice_upload(lbm_lattice* L, int which, void* dev, size_t bytes, void*
     if (e == cudaSuccess && L->nwarps > 0)
       e = cudaMemcpyAsync(base + t.warp_head0, L->warp_head0.data(), L->warp_head0.size() * 4, cudaMemcpyHostToDevice,
                           st);
+    if (e == cudaSuccess && t.has_run_slot)
+      e = cudaMemcpyAsync(base + t.run_slot, L->run_slot.data(), L->run_slot.size() * 4, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return set_error(LBM_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
     L->dev.run_adj = reinterpret_cast<const int32_t*>(base + t.run_adj);
+    L->dev.run_slot = t.has_run_slot ? reinterpret_cast<const int32_t*>(base + t.run_slot) : nullptr;
     L->dev.head_bits = reinterpret_cast<const uint32_t*>(base + t.head_bits);
     L->dev.warp_run0 = reinterpret_cast<const int32_t*>(base + t.warp_run0);
     L->dev.warp_head0 = reinterpret_cast<const int32_t*>(base + t.warp_head0);

@@ -61,6 +61,9 @@ struct DevTables {
   const uint32_t* head_bits = nullptr;  // [nwarps]     bit j of word w: node 32w+j starts a run
   const int32_t* warp_run0 = nullptr;   // [nwarps]     run holding node 32w
   const int32_t* warp_head0 = nullptr;  // [nwarps]     first node of that run
+  // [18][Rpad] the AA odd step's slots of each run's first node (see
+  // derive_run_slots), or NULL where the lattice does not qualify
+  const int32_t* run_slot = nullptr;
   int64_t Npad = 0, Rpad = 0, R = 0, nwarps = 0;
   uint32_t npad = 0, rpad = 0;          // the same strides as 32-bit values (N < 2^31)
   int pressure = 0;                     // the lattice has inlet/outlet markers
@@ -115,6 +118,10 @@ struct lbm_lattice {
   std::vector<int32_t> warp_run0;  // [nwarps]  run holding node 32w
   std::vector<int32_t> warp_head0; // [nwarps]  first node of that run
   int64_t hist[33] = {0};
+  // The AA odd step's slots per run (derive_run_slots): -1 not derived yet,
+  // 0 the lattice does not qualify, 1 run_slot holds them
+  int run_slot_state = -1;
+  lbm::TableVec run_slot;          // [18][Rpad]
   // Esoteric Twist tables, derived on first use (derive_et)
   int et_ready = 0;
   int64_t et_S = 0, et_Spad = 0;   // storage locations (nodes + phantoms) and the padded grid stride
@@ -173,6 +180,7 @@ int validate_partitioning(const lbm_partitioning* S, const lbm_lattice* G);
 int launch_halo(const lbm_partitioning* S, int prec, void* const* grids, int mode, void* stream);  // halo.cu
 int derive_ria(lbm_lattice* L);
 int derive_et(lbm_lattice* L);   // Esoteric Twist tables (idempotent)
+int derive_run_slots(lbm_lattice* L);  // the AA odd step's run slots (idempotent)
 int validate(const lbm_lattice* L);
 int validate_runs(const lbm_lattice* L);  // the RIA tables alone (any index range)
 

@@ -627,6 +627,47 @@ __global__ void __launch_bounds__(kBlock, MinCtasOdd<PREC, RIA>::value) k_aa_odd
   const int n = blockIdx.x * kBlock + threadIdx.x;
   if (n >= N) return;
   R d[kQ];
+  if (RIA && t.run_slot) {
+    // Pre-resolved run slots (no pressure faces; the grid below 2^31 slots):
+    // f_i is read from slot run_slot[i][r] + off of the flat grid, and P_i
+    // goes back to the slot f_inv(i) came from.
+    const RiaCursor cur = ria_locate(t, n);
+    unsigned sl[18];
+#pragma unroll
+    for (int j = 0; j < 18; ++j) {
+      sl[j] = static_cast<unsigned>(__ldg(t.run_slot + at(j, t.rpad, cur.r)) + cur.off);
+      s_m[j][threadIdx.x] = static_cast<int>(sl[j]);
+    }
+    if constexpr (PREC == LBM_F64_DF) {
+      const double* g = reinterpret_cast<const double*>(A);
+      double g64[kQ];
+      g64[0] = __ldg(g + n);
+#pragma unroll
+      for (int i = 1; i < kQ; ++i) g64[i] = __ldg(g + sl[i - 1]);
+      double sa64[10], da64[10], drho64, jx64, jy64, jz64;
+      moments<double, !LP1, true>(g64, sa64, da64, drho64, jx64, jy64, jz64);
+      R sa[10], da[10];
+#pragma unroll
+      for (int k = 1; k <= 9; ++k) {
+        if (!LP1) sa[k] = df_from_double(sa64[k]);
+        da[k] = df_from_double(da64[k]);
+      }
+      if (!LP1) d[0] = df_from_double(g64[0]);
+      const R sn = DRAG ? R(__ldg(s + n)) : R(0);
+      collide_m<R, FORCE, DRAG, LP1>(d, c, sn, sa, da, df_from_double(drho64), df_from_double(jx64),
+                                     df_from_double(jy64), df_from_double(jz64));
+    } else {
+      d[0] = ld_step<PREC>(A + n, kp.inv_scale);
+#pragma unroll
+      for (int i = 1; i < kQ; ++i) d[i] = ld_step<PREC>(A + sl[i - 1], kp.inv_scale);
+      const R sn = DRAG ? R(__ldg(s + n)) : R(0);
+      collide<R, FORCE, DRAG, LP1, kScaled<PREC>>(d, c, sn);
+    }
+    st_step<PREC>(A + n, d[0], kp.scale);
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) st_step<PREC>(A + static_cast<unsigned>(s_m[inv(i) - 1][threadIdx.x]), d[i], kp.scale);
+    return;
+  }
   {
     int m[18];
     if (RIA) {
@@ -930,7 +971,9 @@ __global__ void __launch_bounds__(kBlock) k_load_canonical(DevTables t, KParams 
 }
 
 // Canonical pre-collision state of one node, FP64, unshifted.
-template <int PREC, bool RIA>
+// SHIFT: add the storage shift w_i rho_s back (the canonical PDFs); without
+// it F holds the stored deviations, for callers that form exact moments.
+template <int PREC, bool RIA, bool SHIFT = true>
 __device__ __forceinline__ bool node_canonical(const DevTables& t, const KParams& kp,
                                                const CollConst<typename St<PREC>::R>& c,
                                                const typename St<PREC>::T* pdf, int layout, int n, int N,
@@ -947,7 +990,7 @@ __device__ __forceinline__ bool node_canonical(const DevTables& t, const KParams
       d[i] = St<PREC>::ld(pdf + at(layout == LBM_LAYOUT_ET_ODD ? inv(i) : i, t.spad, loc[et_row(inv(i)) + 1]),
                           kp.inv_scale);
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) F[i] = double(d[i]) + wgt(i) * kp.rho_s;
+    for (int i = 0; i < kQ; ++i) F[i] = SHIFT ? double(d[i]) + wgt(i) * kp.rho_s : double(d[i]);
     return true;
   }
   int m[18];
@@ -971,7 +1014,7 @@ __device__ __forceinline__ bool node_canonical(const DevTables& t, const KParams
     gather<PREC, true>(pdf, t.npad, n, m, d, kp.inv_scale, c.abb_in, c.abb_out, t.pressure);
   }
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) F[i] = double(d[i]) + wgt(i) * kp.rho_s;
+  for (int i = 0; i < kQ; ++i) F[i] = SHIFT ? double(d[i]) + wgt(i) * kp.rho_s : double(d[i]);
   return true;
 }
 

@@ -460,6 +460,60 @@ int partition_ghosts(const lbm_lattice* L, int P, int64_t* ghosts) {
 // lexicographic order of the (wrapped) coordinates, x fastest.
 int derive_et_tables(lbm_lattice* L);
 
+// The AA odd step's slots per run.  With RIA, node n = head + off of run r
+// reads f_i from slot (inv i, run_adj[i][r] + off) when the head pulls from a
+// fluid node, and from its own slot (i, head + off) through a bounce-back
+// marker; as a flat index of the [19][Npad] grid this is
+// run_slot[i][r] + off in both cases, with
+//   run_slot[i][r] = inv(i) Npad + run_adj[i][r]   (fluid source)
+//                  = i Npad + run_start[r]          (bounce-back).
+// The step also writes P_i to the slot f_inv(i) came from, so the same entries
+// give its stores.  This pre-resolves the table (the same 4 bytes per run and
+// direction as run_adj) so the kernel spends one add per access.  Lattices
+// with pressure markers (whose anti-bounce-back needs the marker kind) or a
+// grid of 2^31 or more slots do not qualify: run_slot_state = 0.
+int derive_run_slots(lbm_lattice* L) {
+  if (L->run_slot_state >= 0) return LBM_OK;
+  if (int64_t(19) * L->Npad >= (int64_t(1) << 31) || L->bc.x_pressure) {
+    L->run_slot_state = 0;
+    return LBM_OK;
+  }
+  try {
+    std::atomic<bool> marker{false};
+    parallel_for(int64_t(L->run_adj.size()), [&](int64_t b, int64_t e) {
+      for (int64_t k = b; k < e; ++k)
+        if (L->run_adj[size_t(k)] < LBM_MARK_WALL) {
+          marker = true;
+          return;
+        }
+    });
+    if (marker) {
+      L->run_slot_state = 0;
+      return LBM_OK;
+    }
+    L->run_slot.resize(size_t(18) * L->Rpad);
+    parallel_for(L->Rpad, [&](int64_t rb, int64_t re) {
+      for (int i = 1; i <= 18; ++i) {
+        const int32_t* ra = L->run_adj.data() + size_t(i - 1) * L->Rpad;
+        int32_t* rs = L->run_slot.data() + size_t(i - 1) * L->Rpad;
+        for (int64_t r = rb; r < re; ++r) {
+          if (r >= L->R) {
+            rs[r] = 0;  // padding
+          } else {
+            const int32_t a = ra[r];
+            rs[r] = a >= 0 ? int32_t(int64_t(kInv[i]) * L->Npad + a) : int32_t(int64_t(i) * L->Npad + L->run_start[size_t(r)]);
+          }
+        }
+      }
+    });
+  } catch (const std::bad_alloc&) {
+    L->run_slot.clear();
+    return set_error(LBM_ERR_ALLOC, "out of host memory for the run slot table");
+  }
+  L->run_slot_state = 1;
+  return LBM_OK;
+}
+
 int derive_et(lbm_lattice* L) {
   if (L->et_ready) return LBM_OK;
   try {
