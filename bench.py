@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -307,7 +308,9 @@ class Clocks:
         self.index = index
         self.period_ms = period_ms
         self.proc = None
-        self.path = os.path.join("/tmp", f"lbm_clocks_{os.getpid()}.csv")
+        import tempfile
+        fd, self.path = tempfile.mkstemp(prefix="lbm_clocks_", suffix=".csv")
+        os.close(fd)
 
     def __enter__(self):
         try:
@@ -519,32 +522,52 @@ def suite_adjoint(args, lbm, torch):
         gv = out["variants"][prec]["grad"]
         out["variants"][prec]["grad_err_max_rel"] = float((gv - ref).abs().max() / ref.abs().max())
     if args.fd:
-        # central differences of the FP64 forward (shifted storage) at 20 nodes
+        # central differences of the FP64 forward (shifted storage) at args.fd
+        # nodes, at h, 2h and 4h, each beside its round-off floor: the same
+        # forward with unshifted storage (the same arithmetic, rounded at other
+        # places) gives J's rounding noise dJ, and an FD quotient then carries
+        # about sqrt(2) dJ / (2 h) of noise
         rng = np.random.default_rng(4)
-        params = lbm.Params(omega_plus=1.0, magic=3 / 16, g=(1e-5, 0.0, 0.0), shifted=True)
-        G0 = lat.new_grid("f64")
-        lbm.lbm_init_equilibrium(lat, "f64", params, G0, lbm.LBM_LAYOUT_OSNT, 1.0)
+        runs = {}
+        for shifted in (True, False):
+            params = lbm.Params(omega_plus=1.0, magic=3 / 16, g=(1e-5, 0.0, 0.0), shifted=shifted)
+            G0 = lat.new_grid("f64")
+            lbm.lbm_init_equilibrium(lat, "f64", params, G0, lbm.LBM_LAYOUT_OSNT, 1.0)
+            runs[shifted] = (params, G0)
         nb = lbm.lbm_ckpt_workspace_bytes(lat, "f64", T, K)
         ws = torch.empty((nb + 7) // 8, dtype=torch.float64, device="cuda")
+        J_s = float(lbm.lbm_flux_forward(lat, "f64", runs[True][0], runs[True][1], s, T, K, ws))
+        J_u = float(lbm.lbm_flux_forward(lat, "f64", runs[False][0], runs[False][1], s, T, K, ws))
+        dJ = abs(J_s - J_u)
+        params, G0 = runs[True]
         nodes = rng.choice(lat.N, args.fd, replace=False)
         gmax = float(ref.abs().max())
-        for h in (1e-4, 4e-4):
-            worst, worst_g = 0.0, 0.0
+        fds = {}
+        for h in (1e-4, 2e-4, 4e-4):
+            errs, floors, vals = [], [], []
             for node in nodes:
-                vals = []
+                Jv = []
                 for sign in (1, -1):
                     sp = s.clone()
                     sp[node] = float(s[node]) + sign * h
                     hh = float(sp[node].double() - s[node].double())
-                    vals.append((float(lbm.lbm_flux_forward(lat, "f64", params, G0, sp, T, K, ws)), hh))
-                fd = (vals[0][0] - vals[1][0]) / (vals[0][1] - vals[1][1])
-                worst = max(worst, abs(fd - float(ref[node])) / abs(float(ref[node])))
-                worst_g = max(worst_g, abs(fd - float(ref[node])) / gmax)
-            out[f"fd_h{h:g}"] = {"max_rel_err": worst, "max_err_over_max_grad": worst_g}
+                    Jv.append((float(lbm.lbm_flux_forward(lat, "f64", params, G0, sp, T, K, ws)), hh))
+                fd = (Jv[0][0] - Jv[1][0]) / (Jv[0][1] - Jv[1][1])
+                g = float(ref[node])
+                vals.append(fd)
+                errs.append(abs(fd - g) / abs(g))
+                floors.append(math.sqrt(2) * dJ / (Jv[0][1] - Jv[1][1]) / abs(g))
+            fds[h] = np.array(vals)
+            out[f"fd_h{h:g}"] = {"max_rel_err": max(errs), "median_rel_err": float(np.median(errs)),
+                                 "noise_floor_max_rel": max(floors), "noise_floor_median_rel": float(np.median(floors)),
+                                 "max_err_over_max_grad": max(abs(v - float(ref[nd])) for v, nd in zip(vals, nodes)) / gmax}
+        out["fd_h_vs_2h_max_rel"] = float(np.max(np.abs(fds[1e-4] - fds[2e-4]) / np.abs(fds[2e-4])))
         out["fd_nodes"] = args.fd
-        out["fd_note"] = ("central differences of the FP64 forward (shifted storage); at this size the difference "
-                          "quotient is ~1e-10 of J, so FP64 rounding noise of the 2000-step forward sets a floor "
-                          "near 1e-6 that shrinks as h grows while truncation error grows as h^2")
+        out["J_rounding_noise"] = {"J_shifted": J_s, "J_unshifted": J_u, "dJ": dJ, "dJ_over_J": dJ / abs(J_s)}
+        out["fd_note"] = ("central differences of the FP64 forward (shifted storage) against the FP64 adjoint "
+                          "gradient; noise_floor = sqrt(2) dJ / (2 h) / |dJ/ds_n| with dJ the difference of J "
+                          "between shifted and unshifted FP64 storage (the same forward, other rounding)")
+        del ws
     for v in out["variants"].values():
         v.pop("grad", None)
     return out
@@ -918,6 +941,7 @@ def main():
         stop.record(stream)
         barrier()
     solver.t += 2 * (args.warmup + K)
+    clock_summary = clk.summary()
     ms, value = job_time_and_value(start.elapsed_time(stop), K, N, world, dev)
     even_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / K
     odd_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / K
@@ -1076,7 +1100,6 @@ def main():
         except Exception as e:  # the baseline must never hide the GPU number
             cpu = {"error": str(e)}
 
-    clock_summary = clk.summary()
     line = {
         "metric": "sparse D3Q19 TRT AA-R FP64 lattice updates per second" if hp == "f64"
                   else f"sparse D3Q19 TRT AA-R lattice updates per second ({hp} storage)",

@@ -322,13 +322,14 @@ __global__ void __launch_bounds__(kBlock) k_objective(DevTables t, KParams kp, C
   const int n = n0 + threadIdx.x;
   double f[kQ];
   double hi = 0.0, lo = 0.0;
-  if (node_canonical<PREC, RIA>(t, kp, c, pdf, layout, n, N, f)) {
-    double r = 0.0, jx = 0.0;
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-      r += f[i];
-      if (cx(i)) jx += cx(i) > 0 ? f[i] : -f[i];
-    }
+  if (node_canonical<PREC, RIA, false>(t, kp, c, pdf, layout, n, N, f)) {
+    // rho and j_x from the stored values as exact fixed-point sums, each
+    // rounded once (exact64.cuh): the objective's per-node terms carry no
+    // summation error, which keeps finite differences of J above round-off
+    int64_t Sk[10], D[10], S, Jx, Jy, Jz;
+    const int emax = fx_moments<false>(f, Sk, D, S, Jx, Jy, Jz);
+    const double r = kp.rho_s + (emax < kFxMaxExp ? fx_to_double(S, emax) : dfrom(0x7ff8000000000000ull));
+    const double jx = fx_to_double(Jx, emax);
     const double kd = s ? 1.0 / (1.0 + 0.5 * double(s[n])) : 1.0;
     const double rux = (jx + 0.5 * kp.g[0] * r) * kd;  // rho u_x
     hi = rux;

@@ -37,26 +37,42 @@ __host__ __device__ constexpr double wgt(int i) { return i == 0 ? 1.0 / 3.0 : (i
 
 constexpr int kBlock = 128;  // nodes per CTA of the step kernels (one node per thread)
 // Minimum resident CTAs per SM of the step kernels (caps registers at
-// 65536 / (128 * n)), from sweeps of 4..12 on GB300.  The indirect steps are
+// 65536 / (128 * n)), from sweeps on GB300.  The indirect steps are
 // latency-bound (index words, then gathers, then scattered stores): with RIA
-// (fewer live index registers) FP32 and FP16 are fastest at 10 CTAs
-// (<= 51 registers), with the adjacency list at 8 (AA odd) or 5 (OS-NT).  The
-// double-float path takes 8 (AA odd) and 6 (others).  Native FP64 stays at 5:
-// it is bound by the FP64 pipe, and its time did not move between 4 and 7.
+// FP32 is fastest at 10 CTAs (<= 51 registers), FP16 at 12 (<= 42; 16 spills
+// and loses 7 %), with the adjacency list at 8 (AA odd) or 5 (OS-NT).  The
+// double-float path takes 8 (AA odd) and 6 (others).  Native FP64: the AA
+// steps fit 64 registers without spills and are fastest at 8 CTAs (AA-R on the
+// 256^3 bed 12.8 / 13.6 / 14.2 / 14.6 GFLUP/s at 5 / 6 / 7 / 8); OS-NT and
+// the Esoteric Twist step spill at 7 and take 6.
+#ifndef LBM_MIN_CTAS_F64
+#define LBM_MIN_CTAS_F64 6
+#endif
+#ifndef LBM_MIN_CTAS_F64_AA
+#define LBM_MIN_CTAS_F64_AA 8
+#endif
 template <int PREC, bool RIA> struct MinCtasOsnt { static constexpr int value = RIA ? 10 : 5; };
-template <bool RIA> struct MinCtasOsnt<LBM_F64, RIA> { static constexpr int value = 5; };
+template <bool RIA> struct MinCtasOsnt<LBM_F64, RIA> { static constexpr int value = LBM_MIN_CTAS_F64; };
 template <bool RIA> struct MinCtasOsnt<LBM_F64_DF, RIA> { static constexpr int value = 6; };
 template <int PREC> struct MinCtasEven { static constexpr int value = 5; };
+template <> struct MinCtasEven<LBM_F64> { static constexpr int value = LBM_MIN_CTAS_F64_AA; };
 template <> struct MinCtasEven<LBM_F64_DF> { static constexpr int value = 6; };
-template <int PREC, bool RIA> struct MinCtasOdd { static constexpr int value = RIA ? 10 : 8; };
-template <bool RIA> struct MinCtasOdd<LBM_F64, RIA> { static constexpr int value = 5; };
+#ifndef LBM_MIN_CTAS_ODD_RIA
+#define LBM_MIN_CTAS_ODD_RIA 10
+#endif
+#ifndef LBM_MIN_CTAS_ODD_RIA_F16
+#define LBM_MIN_CTAS_ODD_RIA_F16 12
+#endif
+template <int PREC, bool RIA> struct MinCtasOdd { static constexpr int value = RIA ? LBM_MIN_CTAS_ODD_RIA : 8; };
+template <bool RIA> struct MinCtasOdd<LBM_F16S, RIA> { static constexpr int value = RIA ? LBM_MIN_CTAS_ODD_RIA_F16 : 8; };
+template <bool RIA> struct MinCtasOdd<LBM_F64, RIA> { static constexpr int value = LBM_MIN_CTAS_F64_AA; };
 template <bool RIA> struct MinCtasOdd<LBM_F64_DF, RIA> { static constexpr int value = 8; };
 // The Esoteric Twist step: every step is indirect, and a sweep of 6/8/10/12
 // on GB300 put FP32 and FP16 at 10 CTAs (<= 51 registers; +3-5 % over 8),
-// double-float at 8 (+3 % over 6), native FP64 at 5.
+// double-float at 8 (+3 % over 6); native FP64 takes 6 (see above).
 template <int PREC> struct MinCtasEt { static constexpr int value = 10; };
 template <> struct MinCtasEt<LBM_F64_DF> { static constexpr int value = 8; };
-template <> struct MinCtasEt<LBM_F64> { static constexpr int value = 5; };
+template <> struct MinCtasEt<LBM_F64> { static constexpr int value = LBM_MIN_CTAS_F64; };
 static_assert(kBlock % kWarpNodes == 0, "a warp must cover one run-index group");
 
 // ---- storage traits -----------------------------------------------------------------
