@@ -523,28 +523,22 @@ def suite_adjoint(args, lbm, torch):
         out["variants"][prec]["grad_err_max_rel"] = float((gv - ref).abs().max() / ref.abs().max())
     if args.fd:
         # central differences of the FP64 forward (shifted storage) at args.fd
-        # nodes, at h, 2h and 4h, each beside its round-off floor: the same
-        # forward with unshifted storage (the same arithmetic, rounded at other
-        # places) gives J's rounding noise dJ, and an FD quotient then carries
-        # about sqrt(2) dJ / (2 h) of noise
+        # nodes, at h, 2h and 4h.  Truncation error (O(h^2), below 1e-8 here)
+        # is far below round-off, so the spread of the quotients between h and
+        # 2h estimates the round-off noise of the quotient at h: the noise
+        # floor printed beside each comparison at h
         rng = np.random.default_rng(4)
-        runs = {}
-        for shifted in (True, False):
-            params = lbm.Params(omega_plus=1.0, magic=3 / 16, g=(1e-5, 0.0, 0.0), shifted=shifted)
-            G0 = lat.new_grid("f64")
-            lbm.lbm_init_equilibrium(lat, "f64", params, G0, lbm.LBM_LAYOUT_OSNT, 1.0)
-            runs[shifted] = (params, G0)
+        params = lbm.Params(omega_plus=1.0, magic=3 / 16, g=(1e-5, 0.0, 0.0), shifted=True)
+        G0 = lat.new_grid("f64")
+        lbm.lbm_init_equilibrium(lat, "f64", params, G0, lbm.LBM_LAYOUT_OSNT, 1.0)
         nb = lbm.lbm_ckpt_workspace_bytes(lat, "f64", T, K)
         ws = torch.empty((nb + 7) // 8, dtype=torch.float64, device="cuda")
-        J_s = float(lbm.lbm_flux_forward(lat, "f64", runs[True][0], runs[True][1], s, T, K, ws))
-        J_u = float(lbm.lbm_flux_forward(lat, "f64", runs[False][0], runs[False][1], s, T, K, ws))
-        dJ = abs(J_s - J_u)
-        params, G0 = runs[True]
         nodes = rng.choice(lat.N, args.fd, replace=False)
+        g = np.array([float(ref[int(nd)]) for nd in nodes])
         gmax = float(ref.abs().max())
         fds = {}
         for h in (1e-4, 2e-4, 4e-4):
-            errs, floors, vals = [], [], []
+            vals = []
             for node in nodes:
                 Jv = []
                 for sign in (1, -1):
@@ -552,21 +546,19 @@ def suite_adjoint(args, lbm, torch):
                     sp[node] = float(s[node]) + sign * h
                     hh = float(sp[node].double() - s[node].double())
                     Jv.append((float(lbm.lbm_flux_forward(lat, "f64", params, G0, sp, T, K, ws)), hh))
-                fd = (Jv[0][0] - Jv[1][0]) / (Jv[0][1] - Jv[1][1])
-                g = float(ref[node])
-                vals.append(fd)
-                errs.append(abs(fd - g) / abs(g))
-                floors.append(math.sqrt(2) * dJ / (Jv[0][1] - Jv[1][1]) / abs(g))
+                vals.append((Jv[0][0] - Jv[1][0]) / (Jv[0][1] - Jv[1][1]))
             fds[h] = np.array(vals)
-            out[f"fd_h{h:g}"] = {"max_rel_err": max(errs), "median_rel_err": float(np.median(errs)),
-                                 "noise_floor_max_rel": max(floors), "noise_floor_median_rel": float(np.median(floors)),
-                                 "max_err_over_max_grad": max(abs(v - float(ref[nd])) for v, nd in zip(vals, nodes)) / gmax}
-        out["fd_h_vs_2h_max_rel"] = float(np.max(np.abs(fds[1e-4] - fds[2e-4]) / np.abs(fds[2e-4])))
+        for h, h2 in ((1e-4, 2e-4), (2e-4, 4e-4)):
+            err = np.abs(fds[h] - g) / np.abs(g)
+            floor = np.abs(fds[h] - fds[h2]) / np.abs(g)
+            out[f"fd_h{h:g}"] = {"max_rel_err": float(err.max()), "median_rel_err": float(np.median(err)),
+                                 "noise_floor_max_rel": float(floor.max()),
+                                 "noise_floor_median_rel": float(np.median(floor)),
+                                 "max_err_over_max_grad": float(np.max(np.abs(fds[h] - g)) / gmax)}
         out["fd_nodes"] = args.fd
-        out["J_rounding_noise"] = {"J_shifted": J_s, "J_unshifted": J_u, "dJ": dJ, "dJ_over_J": dJ / abs(J_s)}
         out["fd_note"] = ("central differences of the FP64 forward (shifted storage) against the FP64 adjoint "
-                          "gradient; noise_floor = sqrt(2) dJ / (2 h) / |dJ/ds_n| with dJ the difference of J "
-                          "between shifted and unshifted FP64 storage (the same forward, other rounding)")
+                          "gradient; noise_floor = |FD(h) - FD(2h)| / |dJ/ds_n|, the round-off spread of the "
+                          "quotient (truncation is O(h^2), far below it)")
         del ws
     for v in out["variants"].values():
         v.pop("grad", None)

@@ -370,8 +370,10 @@ int lbm_fx_pairs_host(const double* d, const double* terms, int64_t n, double qm
     std::memcpy(f, d + 19 * k, sizeof f);
     const double* t = terms + 10 * k;
     int64_t Sk[10], D[10], S, Jx, Jy, Jz;
-    const int emax = !general && dev::fx_pos_near_ok(f) ? dev::fx_moments<true, true>(f, Sk, D, S, Jx, Jy, Jz)
-                                                         : dev::fx_moments<true>(f, Sk, D, S, Jx, Jy, Jz);
+    int emax_fast;
+    const bool near = dev::fx_pos_near(f, emax_fast);
+    const int emax = !general && near ? dev::fx_moments<true, true>(f, Sk, D, S, Jx, Jy, Jz, emax_fast)
+                                      : dev::fx_moments<true>(f, Sk, D, S, Jx, Jy, Jz);
     double* o = out + 19 * k;
     ok[k] = dev::fx_class_ok(emax, t[0], t[1], t[2], t[3], t[4], t[5], t[6], t[7], t[8], t[9]) ? 1 : 0;
     if (!ok[k]) {

@@ -179,12 +179,13 @@ __host__ __device__ __forceinline__ int fx_scale(const uint64_t (&b)[Q]) {
 // (0,1,1) (0,1,-1)) at the node scale emax (returned): pair sums Sk[k] (only
 // when NEED_SA) and differences D[k], the density deviation S = sum d_i and
 // the momentum J = sum c_i d_i, all as integers times 2^(emax - 1080).
-// FAST: the caller has checked fx_pos_near_ok (positive PDFs within 26
-// binades of the largest), and the conversions take the shorter
-// fx_of_pos_near; the integers are the same.
+// FAST: the caller has checked fx_pos_near (positive PDFs within 26 binades
+// of the largest) and passes the node scale it found as emax_fast; the
+// conversions take the shorter fx_of_pos_near, and the integers are the same.
 template <bool NEED_SA, bool FAST = false>
 __host__ __device__ __forceinline__ int fx_moments(const double (&d)[19], int64_t (&Sk)[10], int64_t (&D)[10],
-                                                   int64_t& S, int64_t& Jx, int64_t& Jy, int64_t& Jz) {
+                                                   int64_t& S, int64_t& Jx, int64_t& Jy, int64_t& Jz,
+                                                   int emax_fast = 0) {
   uint64_t b[19];
 #pragma unroll
   for (int i = 0; i < 19; ++i) b[i] = dbits(d[i]);
@@ -192,12 +193,7 @@ __host__ __device__ __forceinline__ int fx_moments(const double (&d)[19], int64_
   int emax;
   if (FAST) {
     // positive: the exponent is the high word shifted, no sign to clear
-    emax = kFxMinExp;
-#pragma unroll
-    for (int i = 0; i < 19; ++i) {
-      const int e = static_cast<int>(b[i] >> 52);
-      emax = e > emax ? e : emax;
-    }
+    emax = emax_fast;
 #pragma unroll
     for (int i = 0; i < 19; ++i) f[i] = fx_of_pos_near(b[i], static_cast<unsigned>(emax + 5 - static_cast<int>(b[i] >> 52)));
   } else {
@@ -221,10 +217,12 @@ __host__ __device__ __forceinline__ int fx_moments(const double (&d)[19], int64_
 
 // True when the fast conversions of fx_moments apply: every PDF positive and
 // finite-scaled (node scale below kFxMaxExp) and at most 26 binades below the
-// largest (so fx_of_pos_near's shift stays in [5, 31]).
-__host__ __device__ __forceinline__ bool fx_pos_near_ok(const double (&d)[19]) {
+// largest (so fx_of_pos_near's shift stays in [5, 31]).  emax: the node
+// scale (the largest exponent field; meaningful when true).
+__host__ __device__ __forceinline__ bool fx_pos_near(const double (&d)[19], int& emax) {
   uint32_t sgn = 0;
-  int emax = 0, emin = 2047;
+  int emin = 2047;
+  emax = 0;
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
     const uint32_t hi = static_cast<uint32_t>(dbits(d[i]) >> 32);

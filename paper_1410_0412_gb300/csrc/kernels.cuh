@@ -470,8 +470,10 @@ __device__ __forceinline__ void collide_f64(double (&d)[kQ], const CollConst<dou
   int64_t Sk[10], D[10], S, Jx, Jy, Jz;
   // the shorter conversions when every node of the warp has positive PDFs
   // within 26 binades of its largest (full-f storage near equilibrium)
-  const int emax = __all_sync(__activemask(), fx_pos_near_ok(d)) ? fx_moments<!LP1, true>(d, Sk, D, S, Jx, Jy, Jz)
-                                                                 : fx_moments<!LP1>(d, Sk, D, S, Jx, Jy, Jz);
+  int emax_fast;
+  const bool near = fx_pos_near(d, emax_fast);
+  const int emax = __all_sync(__activemask(), near) ? fx_moments<!LP1, true>(d, Sk, D, S, Jx, Jy, Jz, emax_fast)
+                                                    : fx_moments<!LP1>(d, Sk, D, S, Jx, Jy, Jz);
   const double drho = emax < kFxMaxExp ? fx_to_double(S, emax) : dfrom(0x7ff8000000000000ull);
   const NodeTerms<double> t = node_terms<double, FORCE, DRAG>(c, s, drho, fx_to_double(Jx, emax),
                                                               fx_to_double(Jy, emax), fx_to_double(Jz, emax));
