@@ -100,7 +100,7 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 struct TableLayout {
   size_t adj = 0, run_adj = 0, head_bits = 0, warp_run0 = 0, warp_head0 = 0, et_nb = 0, et_mask = 0;
   size_t et_run_nb = 0, et_run_mask = 0, et_head_bits = 0, et_warp_run0 = 0, et_warp_head0 = 0, total = 0;
-  size_t run_slot = 0;
+  size_t run_slot = 0, run_slot_osnt = 0;
   bool has_run_slot = false;
 };
 
@@ -123,6 +123,8 @@ TableLayout table_layout(const lbm_lattice* L, int which) {
     if (L->run_slot_state == 1) {
       t.run_slot = off;
       t.has_run_slot = true;
+      off = align256(off + size_t(18) * L->Rpad * 4);
+      t.run_slot_osnt = off;
       off = align256(off + size_t(18) * L->Rpad * 4);
     }
   }
@@ -447,9 +449,13 @@ int lbm_lattice_upload(lbm_lattice* L, int which, void* dev, size_t bytes, void*
                           st);
     if (e == cudaSuccess && t.has_run_slot)
       e = cudaMemcpyAsync(base + t.run_slot, L->run_slot.data(), L->run_slot.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && t.has_run_slot)
+      e = cudaMemcpyAsync(base + t.run_slot_osnt, L->run_slot_osnt.data(), L->run_slot_osnt.size() * 4,
+                          cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return set_error(LBM_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
     L->dev.run_adj = reinterpret_cast<const int32_t*>(base + t.run_adj);
     L->dev.run_slot = t.has_run_slot ? reinterpret_cast<const int32_t*>(base + t.run_slot) : nullptr;
+    L->dev.run_slot_osnt = t.has_run_slot ? reinterpret_cast<const int32_t*>(base + t.run_slot_osnt) : nullptr;
     L->dev.head_bits = reinterpret_cast<const uint32_t*>(base + t.head_bits);
     L->dev.warp_run0 = reinterpret_cast<const int32_t*>(base + t.warp_run0);
     L->dev.warp_head0 = reinterpret_cast<const int32_t*>(base + t.warp_head0);

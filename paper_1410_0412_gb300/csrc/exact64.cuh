@@ -135,13 +135,13 @@ __host__ __device__ __forceinline__ int clz32(uint32_t a) {
 }
 
 // fx_of for the common case, in 32-bit halves: a positive double (sign bit
-// clear) whose shift sh = emax - e + 5 lies in [5, 31], i.e. within 26
-// binades of the node's largest.  Same value as fx_of (exact here).
-__host__ __device__ __forceinline__ int64_t fx_of_pos_near(uint64_t b, unsigned sh) {
+// clear) at most 5 binades below the node's largest, so that fx_of's value
+// m * 2^(10 - sh) is the significand m shifted left by k = 5 - (emax - e) in
+// [0, 5].  Same value as fx_of (exact here).
+__host__ __device__ __forceinline__ int64_t fx_of_pos_near(uint64_t b, unsigned k) {
   const uint32_t hi = static_cast<uint32_t>(b >> 32), lo = static_cast<uint32_t>(b);
   const uint32_t mh = (hi & 0x000fffffu) | 0x00100000u;  // significand bits 52..32, hidden bit included
-  const uint32_t h10 = shf_l(lo, mh, 10), l10 = lo << 10;  // significand << 10, below 2^63
-  return static_cast<int64_t>((static_cast<uint64_t>(h10 >> sh) << 32) | shf_r(l10, h10, sh));
+  return static_cast<int64_t>((static_cast<uint64_t>(shf_l(lo, mh, k)) << 32) | (lo << k));
 }
 
 // fx_to_double for the common case, in 32-bit halves: 2^32 <= v < 2^63 (the
@@ -179,7 +179,7 @@ __host__ __device__ __forceinline__ int fx_scale(const uint64_t (&b)[Q]) {
 // (0,1,1) (0,1,-1)) at the node scale emax (returned): pair sums Sk[k] (only
 // when NEED_SA) and differences D[k], the density deviation S = sum d_i and
 // the momentum J = sum c_i d_i, all as integers times 2^(emax - 1080).
-// FAST: the caller has checked fx_pos_near (positive PDFs within 26 binades
+// FAST: the caller has checked fx_pos_near (positive PDFs within 5 binades
 // of the largest) and passes the node scale it found as emax_fast; the
 // conversions take the shorter fx_of_pos_near, and the integers are the same.
 template <bool NEED_SA, bool FAST = false>
@@ -195,7 +195,7 @@ __host__ __device__ __forceinline__ int fx_moments(const double (&d)[19], int64_
     // positive: the exponent is the high word shifted, no sign to clear
     emax = emax_fast;
 #pragma unroll
-    for (int i = 0; i < 19; ++i) f[i] = fx_of_pos_near(b[i], static_cast<unsigned>(emax + 5 - static_cast<int>(b[i] >> 52)));
+    for (int i = 0; i < 19; ++i) f[i] = fx_of_pos_near(b[i], static_cast<unsigned>(static_cast<int>(b[i] >> 52) + 5 - emax));
   } else {
     emax = fx_scale(b);
 #pragma unroll
@@ -216,9 +216,9 @@ __host__ __device__ __forceinline__ int fx_moments(const double (&d)[19], int64_
 }
 
 // True when the fast conversions of fx_moments apply: every PDF positive and
-// finite-scaled (node scale below kFxMaxExp) and at most 26 binades below the
-// largest (so fx_of_pos_near's shift stays in [5, 31]).  emax: the node
-// scale (the largest exponent field; meaningful when true).
+// finite-scaled (node scale below kFxMaxExp) and at most 5 binades below the
+// largest (so fx_of_pos_near's shift stays in [0, 5]; PDFs near w_i rho span
+// 4).  emax: the node scale (the largest exponent field; meaningful when true).
 __host__ __device__ __forceinline__ bool fx_pos_near(const double (&d)[19], int& emax) {
   uint32_t sgn = 0;
   int emin = 2047;
@@ -231,7 +231,7 @@ __host__ __device__ __forceinline__ bool fx_pos_near(const double (&d)[19], int&
     emax = e > emax ? e : emax;
     emin = e < emin ? e : emin;
   }
-  return !(sgn & 0x80000000u) && emin >= kFxMinExp && emax < kFxMaxExp && emax - emin <= 26;
+  return !(sgn & 0x80000000u) && emin >= kFxMinExp && emax < kFxMaxExp && emax - emin <= 5;
 }
 
 // The moments as doubles: pair sums sa_k (only when NEED_SA) and differences

@@ -61,9 +61,10 @@ struct DevTables {
   const uint32_t* head_bits = nullptr;  // [nwarps]     bit j of word w: node 32w+j starts a run
   const int32_t* warp_run0 = nullptr;   // [nwarps]     run holding node 32w
   const int32_t* warp_head0 = nullptr;  // [nwarps]     first node of that run
-  // [18][Rpad] the AA odd step's slots of each run's first node (see
-  // derive_run_slots), or NULL where the lattice does not qualify
+  // [18][Rpad] the AA odd step's and the OS-NT step's slots of each run's
+  // first node (see derive_run_slots), or NULL where the lattice does not qualify
   const int32_t* run_slot = nullptr;
+  const int32_t* run_slot_osnt = nullptr;
   int64_t Npad = 0, Rpad = 0, R = 0, nwarps = 0;
   uint32_t npad = 0, rpad = 0;          // the same strides as 32-bit values (N < 2^31)
   int pressure = 0;                     // the lattice has inlet/outlet markers
@@ -121,7 +122,8 @@ struct lbm_lattice {
   // The AA odd step's slots per run (derive_run_slots): -1 not derived yet,
   // 0 the lattice does not qualify, 1 run_slot holds them
   int run_slot_state = -1;
-  lbm::TableVec run_slot;          // [18][Rpad]
+  lbm::TableVec run_slot;          // [18][Rpad] AA odd step
+  lbm::TableVec run_slot_osnt;     // [18][Rpad] OS-NT step
   // Esoteric Twist tables, derived on first use (derive_et)
   int et_ready = 0;
   int64_t et_S = 0, et_Spad = 0;   // storage locations (nodes + phantoms) and the padded grid stride

@@ -51,7 +51,11 @@ constexpr int kBlock = 128;  // nodes per CTA of the step kernels (one node per 
 #ifndef LBM_MIN_CTAS_F64_AA
 #define LBM_MIN_CTAS_F64_AA 8
 #endif
+#ifndef LBM_MIN_CTAS_OSNT_RIA_F16
+#define LBM_MIN_CTAS_OSNT_RIA_F16 10
+#endif
 template <int PREC, bool RIA> struct MinCtasOsnt { static constexpr int value = RIA ? 10 : 5; };
+template <bool RIA> struct MinCtasOsnt<LBM_F16S, RIA> { static constexpr int value = RIA ? LBM_MIN_CTAS_OSNT_RIA_F16 : 5; };
 template <bool RIA> struct MinCtasOsnt<LBM_F64, RIA> { static constexpr int value = LBM_MIN_CTAS_F64; };
 template <bool RIA> struct MinCtasOsnt<LBM_F64_DF, RIA> { static constexpr int value = 6; };
 template <int PREC> struct MinCtasEven { static constexpr int value = 5; };
@@ -469,7 +473,7 @@ template <bool FORCE, bool DRAG, bool LP1>
 __device__ __forceinline__ void collide_f64(double (&d)[kQ], const CollConst<double>& c, const double s) {
   int64_t Sk[10], D[10], S, Jx, Jy, Jz;
   // the shorter conversions when every node of the warp has positive PDFs
-  // within 26 binades of its largest (full-f storage near equilibrium)
+  // within 5 binades of its largest (full-f storage near equilibrium)
   int emax_fast;
   const bool near = fx_pos_near(d, emax_fast);
   const int emax = __all_sync(__activemask(), near) ? fx_moments<!LP1, true>(d, Sk, D, S, Jx, Jy, Jz, emax_fast)
@@ -561,6 +565,24 @@ __global__ void __launch_bounds__(kBlock, MinCtasOsnt<PREC, RIA>::value) k_osnt(
   using R = typename St<PREC>::R;
   const int n0 = blockIdx.x * kBlock;
   const int n = n0 + threadIdx.x;
+  if (RIA && t.run_slot_osnt) {
+    // Pre-resolved run slots (no pressure faces; the grid below 2^31 slots):
+    // P_i (or P_inv(i) through a bounce-back marker) is pulled from slot
+    // run_slot_osnt[i][r] + off of the flat source grid.
+    if (n >= N) return;
+    const RiaCursor cur = ria_locate(t, n);
+    R d[kQ];
+    d[0] = ld_step<PREC>(src + n, kp.inv_scale);
+#pragma unroll
+    for (int i = 1; i < kQ; ++i)
+      d[i] = ld_step<PREC>(src + static_cast<unsigned>(__ldg(t.run_slot_osnt + at(i - 1, t.rpad, cur.r)) + cur.off),
+                           kp.inv_scale);
+    const R sn = DRAG ? R(__ldg(s + n)) : R(0);
+    collide<R, FORCE, DRAG, LP1, kScaled<PREC>>(d, c, sn);
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) st_stream_step<PREC>(dst + at(i, t.npad, n), d[i], kp.scale);
+    return;
+  }
   int m[18];
   if (RIA) {
     if (n >= N) return;

@@ -468,8 +468,12 @@ int derive_et_tables(lbm_lattice* L);
 //   run_slot[i][r] = inv(i) Npad + run_adj[i][r]   (fluid source)
 //                  = i Npad + run_start[r]          (bounce-back).
 // The step also writes P_i to the slot f_inv(i) came from, so the same entries
-// give its stores.  This pre-resolves the table (the same 4 bytes per run and
-// direction as run_adj) so the kernel spends one add per access.  Lattices
+// give its stores.  The OS-NT step pulls post-collision P_i from slot
+// (i, run_adj[i][r] + off) of the source grid, or P_inv(i) from the node's own
+// slot (inv i, head + off) through a marker: run_slot_osnt[i][r] =
+// i Npad + run_adj[i][r] or inv(i) Npad + run_start[r].  This pre-resolves the
+// table (the same 4 bytes per run and direction as run_adj) so the kernel
+// spends one add per access.  Lattices
 // with pressure markers (whose anti-bounce-back needs the marker kind) or a
 // grid of 2^31 or more slots do not qualify: run_slot_state = 0.
 int derive_run_slots(lbm_lattice* L) {
@@ -492,22 +496,27 @@ int derive_run_slots(lbm_lattice* L) {
       return LBM_OK;
     }
     L->run_slot.resize(size_t(18) * L->Rpad);
+    L->run_slot_osnt.resize(size_t(18) * L->Rpad);
     parallel_for(L->Rpad, [&](int64_t rb, int64_t re) {
       for (int i = 1; i <= 18; ++i) {
         const int32_t* ra = L->run_adj.data() + size_t(i - 1) * L->Rpad;
         int32_t* rs = L->run_slot.data() + size_t(i - 1) * L->Rpad;
+        int32_t* ro = L->run_slot_osnt.data() + size_t(i - 1) * L->Rpad;
         for (int64_t r = rb; r < re; ++r) {
           if (r >= L->R) {
-            rs[r] = 0;  // padding
+            rs[r] = ro[r] = 0;  // padding
           } else {
             const int32_t a = ra[r];
-            rs[r] = a >= 0 ? int32_t(int64_t(kInv[i]) * L->Npad + a) : int32_t(int64_t(i) * L->Npad + L->run_start[size_t(r)]);
+            const int64_t head = L->run_start[size_t(r)];
+            rs[r] = a >= 0 ? int32_t(int64_t(kInv[i]) * L->Npad + a) : int32_t(int64_t(i) * L->Npad + head);
+            ro[r] = a >= 0 ? int32_t(int64_t(i) * L->Npad + a) : int32_t(int64_t(kInv[i]) * L->Npad + head);
           }
         }
       }
     });
   } catch (const std::bad_alloc&) {
     L->run_slot.clear();
+    L->run_slot_osnt.clear();
     return set_error(LBM_ERR_ALLOC, "out of host memory for the run slot table");
   }
   L->run_slot_state = 1;

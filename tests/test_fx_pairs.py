@@ -105,7 +105,7 @@ def test_fx_pairs_is_as_tight_as_a_quarter_ulp_at_rest_scale():
 @pytest.mark.parametrize("shifted", [False, True])
 def test_fx_pairs_short_conversions_give_the_same_bits(lp1, shifted):
     # the kernels convert positive values in a common range with shorter
-    # routines (moments: positive PDFs within 26 binades of the largest;
+    # routines (moments: positive PDFs within 5 binades of the largest;
     # outputs: 2^32 <= v < 2^63); they must give the general routines' bits
     d, terms = _nodes(2000, 20 + shifted + 2 * lp1, shifted)
     qp = 0.0 if lp1 else 0.125
