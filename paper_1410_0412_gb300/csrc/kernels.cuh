@@ -40,7 +40,8 @@ constexpr int kBlock = 128;  // nodes per CTA of the step kernels (one node per 
 // 65536 / (128 * n)), from sweeps on GB300.  The indirect steps are
 // latency-bound (index words, then gathers, then scattered stores): with RIA
 // FP32 is fastest at 10 CTAs (<= 51 registers), FP16 at 12 (<= 42; 16 spills
-// and loses 7 %), with the adjacency list at 8 (AA odd) or 5 (OS-NT).  The
+// and loses 7 %; OS-NT-R FP16 on the paper's channel 49.1 -> 51.5 GFLUP/s from
+// 10 to 12), with the adjacency list at 8 (AA odd) or 5 (OS-NT).  The
 // double-float path takes 8 (AA odd) and 6 (others).  Native FP64: the AA
 // steps fit 64 registers without spills and are fastest at 8 CTAs (AA-R on the
 // 256^3 bed 12.8 / 13.6 / 14.2 / 14.6 GFLUP/s at 5 / 6 / 7 / 8); OS-NT and
@@ -52,7 +53,7 @@ constexpr int kBlock = 128;  // nodes per CTA of the step kernels (one node per 
 #define LBM_MIN_CTAS_F64_AA 8
 #endif
 #ifndef LBM_MIN_CTAS_OSNT_RIA_F16
-#define LBM_MIN_CTAS_OSNT_RIA_F16 10
+#define LBM_MIN_CTAS_OSNT_RIA_F16 12
 #endif
 template <int PREC, bool RIA> struct MinCtasOsnt { static constexpr int value = RIA ? 10 : 5; };
 template <bool RIA> struct MinCtasOsnt<LBM_F16S, RIA> { static constexpr int value = RIA ? LBM_MIN_CTAS_OSNT_RIA_F16 : 5; };
