@@ -502,8 +502,11 @@ def suite_adjoint(args, lbm, torch):
     lat = lbm.Lattice(solid, periodic=(1, 1, 1)).upload()
     s = torch.as_tensor(geometry.smooth_noise(n, n, n, 3.0, 2).reshape(-1), device="cuda")
     out = {"suite": "adjoint", "box": n, "fluid_nodes": lat.N, "T": T, "K": K, "variants": {}}
-    for prec in ("f32", "f64df", "f64"):
-        params = lbm.Params(omega_plus=1.0, magic=3 / 16, g=(1e-5, 0.0, 0.0), shifted=True)
+    # deviation (shifted) storage in every precision, plus FP64 with full-f
+    # storage, the form that takes the fixed-point pair update in its forward
+    for name, prec, shifted in (("f32", "f32", True), ("f64df", "f64df", True), ("f64", "f64", True),
+                                ("f64_full", "f64", False)):
+        params = lbm.Params(omega_plus=1.0, magic=3 / 16, g=(1e-5, 0.0, 0.0), shifted=shifted)
         G0 = lat.new_grid(prec)
         lbm.lbm_init_equilibrium(lat, prec, params, G0, lbm.LBM_LAYOUT_OSNT, 1.0)
         nb = lbm.lbm_ckpt_workspace_bytes(lat, prec, T, K)
@@ -517,15 +520,15 @@ def suite_adjoint(args, lbm, torch):
         e[2].record()
         torch.cuda.synchronize()
         fwd, bwd = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
-        out["variants"][prec] = {"J": float(J), "forward_ms": fwd, "backward_ms": bwd,
+        out["variants"][name] = {"J": float(J), "forward_ms": fwd, "backward_ms": bwd,
                                  "backward_over_forward": bwd / fwd, "workspace_GB": nb / 1e9,
                                  "grad_norm": float(grad.norm()), "grad": grad.cpu()}
         del ws, G0
         torch.cuda.empty_cache()
     ref = out["variants"]["f64"]["grad"]
-    for prec in ("f32", "f64df"):
-        gv = out["variants"][prec]["grad"]
-        out["variants"][prec]["grad_err_max_rel"] = float((gv - ref).abs().max() / ref.abs().max())
+    for name in ("f32", "f64df", "f64_full"):
+        gv = out["variants"][name]["grad"]
+        out["variants"][name]["grad_err_max_rel"] = float((gv - ref).abs().max() / ref.abs().max())
     if args.fd:
         # central differences of the FP64 forward (shifted storage) at args.fd
         # nodes, at h, 2h and 4h.  Truncation error (O(h^2), below 1e-8 here)

@@ -475,11 +475,16 @@ __device__ __forceinline__ void collide_f64(double (&d)[kQ], const CollConst<dou
   int64_t Sk[10], D[10], S, Jx, Jy, Jz;
   // the shorter conversions when every node of the warp has positive PDFs
   // within 5 binades of its largest (full-f storage near equilibrium)
-  int emax_fast;
-  const bool near = fx_pos_near(d, emax_fast);
-  const int emax = __all_sync(__activemask(), near) ? fx_moments<!LP1, true>(d, Sk, D, S, Jx, Jy, Jz, emax_fast)
-                                                    : fx_moments<!LP1>(d, Sk, D, S, Jx, Jy, Jz);
-  const double drho = emax < kFxMaxExp ? fx_to_double(S, emax) : dfrom(0x7ff8000000000000ull);
+  int emax_fast, emax;
+  double drho;
+  if (__all_sync(__activemask(), fx_pos_near(d, emax_fast))) {
+    emax = fx_moments<!LP1, true>(d, Sk, D, S, Jx, Jy, Jz, emax_fast);
+    // positive PDFs: S >= the largest one's image >= 2^57, so the short conversion applies
+    drho = fx_to_double_pos(S, emax);
+  } else {
+    emax = fx_moments<!LP1>(d, Sk, D, S, Jx, Jy, Jz);
+    drho = emax < kFxMaxExp ? fx_to_double(S, emax) : dfrom(0x7ff8000000000000ull);
+  }
   const NodeTerms<double> t = node_terms<double, FORCE, DRAG>(c, s, drho, fx_to_double(Jx, emax),
                                                               fx_to_double(Jy, emax), fx_to_double(Jz, emax));
   const bool ok = fx_class_ok(emax, t.ux, t.uy, t.uz, t.K0a, t.Tx, t.Ty, t.Tz, t.Ox, t.Oy, t.Oz);
@@ -774,6 +779,69 @@ __global__ void __launch_bounds__(kBlock, MinCtasOdd<PREC, RIA>::value) k_aa_odd
       const int node = mo >= 0 ? mo : n;
       st_step<PREC>(A + at(dir, t.npad, node), d[i], kp.scale);
     }
+  }
+}
+
+// AA odd step with RIA through the run slot table, two nodes per thread (n
+// and n + kBlock of a 2 kBlock-node CTA), for FP32 storage.  The step is bound
+// by the latency of its two dependent rounds of loads (run slots, then the
+// scattered PDFs), not by bytes or issue; two independent nodes per thread put
+// twice the loads in flight per warp.  Same arithmetic and slots as
+// k_aa_odd's slot path.  Measured on the 256^3 bed: FP32 0.354 -> 0.336 ms per
+// launch at 8 CTAs per SM (0.340 at 6); FP16 is slower this way (0.260 ->
+// 0.293 ms at 8, 0.276 at 6: its 12 one-node CTAs already hide the latency
+// better than 8 two-node ones), so it keeps k_aa_odd.
+#ifndef LBM_MIN_CTAS_ODD_X2
+#define LBM_MIN_CTAS_ODD_X2 8
+#endif
+template <int PREC, bool FORCE, bool DRAG>
+__global__ void __launch_bounds__(kBlock, LBM_MIN_CTAS_ODD_X2) k_aa_odd_x2(DevTables t, KParams kp,
+                                                                         CollConst<typename St<PREC>::R> c,
+                                                                         typename St<PREC>::T* __restrict__ A,
+                                                                         const float* __restrict__ s, int N) {
+  using R = typename St<PREC>::R;
+  static_assert(std::is_same<R, float>::value, "float-collision precisions only");
+  __shared__ int s_sl[2][18][kBlock];
+  const int n0 = blockIdx.x * (2 * kBlock) + threadIdx.x;
+  if (n0 >= N) return;
+  const int n1 = n0 + kBlock;
+  const bool has1 = n1 < N;
+  R d0[kQ], d1[kQ];
+  {
+    const RiaCursor c0 = ria_locate(t, n0);
+    const RiaCursor c1 = ria_locate(t, has1 ? n1 : n0);
+    unsigned sl0[18], sl1[18];
+#pragma unroll
+    for (int j = 0; j < 18; ++j) {
+      sl0[j] = static_cast<unsigned>(__ldg(t.run_slot + at(j, t.rpad, c0.r)) + c0.off);
+      sl1[j] = static_cast<unsigned>(__ldg(t.run_slot + at(j, t.rpad, c1.r)) + c1.off);
+    }
+#pragma unroll
+    for (int j = 0; j < 18; ++j) {
+      s_sl[0][j][threadIdx.x] = static_cast<int>(sl0[j]);
+      s_sl[1][j][threadIdx.x] = static_cast<int>(sl1[j]);
+    }
+    d0[0] = ld_step<PREC>(A + n0, kp.inv_scale);
+    d1[0] = ld_step<PREC>(A + (has1 ? n1 : n0), kp.inv_scale);
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) {
+      d0[i] = ld_step<PREC>(A + sl0[i - 1], kp.inv_scale);
+      d1[i] = ld_step<PREC>(A + sl1[i - 1], kp.inv_scale);
+    }
+  }
+  const R s0 = DRAG ? R(__ldg(s + n0)) : R(0);
+  collide<R, FORCE, DRAG, false, kScaled<PREC>>(d0, c, s0);
+  st_step<PREC>(A + n0, d0[0], kp.scale);
+#pragma unroll
+  for (int i = 1; i < kQ; ++i)
+    st_step<PREC>(A + static_cast<unsigned>(s_sl[0][inv(i) - 1][threadIdx.x]), d0[i], kp.scale);
+  if (has1) {
+    const R s1 = DRAG ? R(__ldg(s + n1)) : R(0);
+    collide<R, FORCE, DRAG, false, kScaled<PREC>>(d1, c, s1);
+    st_step<PREC>(A + n1, d1[0], kp.scale);
+#pragma unroll
+    for (int i = 1; i < kQ; ++i)
+      st_step<PREC>(A + static_cast<unsigned>(s_sl[1][inv(i) - 1][threadIdx.x]), d1[i], kp.scale);
   }
 }
 
@@ -1209,6 +1277,11 @@ int launch_osnt_t(const lbm_lattice* L, const KParams& kp, const void* src, void
   return cuda_check("OS-NT step launch");
 }
 
+#ifndef LBM_ODD_X2
+#define LBM_ODD_X2 1
+#endif
+constexpr bool kOddX2 = LBM_ODD_X2 != 0;
+
 template <int PREC>
 int launch_aa_t(const lbm_lattice* L, const KParams& kp, void* pdf, int parity, const float* s, int ria,
                 void* stream) {
@@ -1236,6 +1309,15 @@ int launch_aa_t(const lbm_lattice* L, const KParams& kp, void* pdf, int parity, 
     else if (f) LBM_LAUNCH_LP1(k_aa_even, LBM_TARGS2(true, false), (L->dev, kp, c, A, s, N));
     else LBM_LAUNCH_LP1(k_aa_even, LBM_TARGS2(false, false), (L->dev, kp, c, A, s, N));
     return cuda_check("AA even step launch");
+  }
+  if constexpr (PREC == LBM_F32) {
+    if (ria && L->dev.run_slot && kOddX2) {
+      const unsigned g2 = unsigned((L->N + 2 * dev::kBlock - 1) / (2 * dev::kBlock));
+      if (s) dev::k_aa_odd_x2<PREC, true, true><<<g2, dev::kBlock, 0, st>>>(L->dev, kp, c, A, s, N);
+      else if (f) dev::k_aa_odd_x2<PREC, true, false><<<g2, dev::kBlock, 0, st>>>(L->dev, kp, c, A, s, N);
+      else dev::k_aa_odd_x2<PREC, false, false><<<g2, dev::kBlock, 0, st>>>(L->dev, kp, c, A, s, N);
+      return cuda_check("AA odd step launch");
+    }
   }
 #define LBM_AAODD(R_, F_, D_) LBM_LAUNCH_LP1(k_aa_odd, LBM_TARGS3(R_, F_, D_), (L->dev, kp, c, A, s, N))
   if (s) {
