@@ -161,6 +161,22 @@ __host__ __device__ __forceinline__ double fx_to_double_pos(int64_t v, int emax)
 // True when fx_to_double_pos applies to v.
 __host__ __device__ __forceinline__ bool fx_pos_wide(int64_t v) { return (v >> 32) >= 1; }
 
+// fx_to_double through the hardware's int64 -> double conversion (round to
+// nearest, ties to even: the same rounding, so the same bits), then an exact
+// scaling by 2^(emax - 1080) as an exponent-field add.  The conversion runs
+// on the FP64 pipe, the rest on the integer pipe; the kernels use it for part
+// of the outputs to balance the two.  For kFxMinExp - 4 <= emax < kFxMaxExp
+// every non-zero result is a normal number.
+__host__ __device__ __forceinline__ double fx_to_double_cvt(int64_t v, int emax) {
+#ifdef __CUDA_ARCH__
+  const double x = __ll2double_rn(static_cast<long long>(v));
+#else
+  const double x = static_cast<double>(v);
+#endif
+  const uint64_t scaled = dbits(x) + (static_cast<uint64_t>(static_cast<int64_t>(emax - 1080)) << 52);
+  return v == 0 ? 0.0 : dfrom(scaled);
+}
+
 // Node scale of the 19 PDFs: the largest biased exponent, at least kFxMinExp.
 template <int Q>
 __host__ __device__ __forceinline__ int fx_scale(const uint64_t (&b)[Q]) {
@@ -335,7 +351,8 @@ __host__ __device__ __forceinline__ int64_t fx_cdot(int64_t vx, int64_t vy, int6
 // 1/36: K0, T and O halved), LP1 when qp = 0.  The two values are converted
 // with fx_to_double_pos when both qualify in every thread of the warp (on the
 // host: in this node), otherwise with fx_to_double; the bits are the same.
-template <int X, int Y, int Z, bool DIAG, bool LP1, bool GENERAL = false>
+// CVT: convert with fx_to_double_cvt (the FP64 pipe's int64 -> double).
+template <int X, int Y, int Z, bool DIAG, bool LP1, bool GENERAL = false, bool CVT = false>
 __host__ __device__ __forceinline__ void fx_pair(const FxClass& q, int64_t Dk, int64_t Sk, int64_t qm, int64_t qp,
                                                  int es, double& pa, double& pb) {
   const int64_t cu = fx_cdot<X, Y, Z>(q.ux, q.uy, q.uz);
@@ -351,6 +368,11 @@ __host__ __device__ __forceinline__ void fx_pair(const FxClass& q, int64_t Dk, i
   }
   if (!LP1) e += mulhi_q64(qp, Sk);
   const int64_t va = e + o, vb = e - o;
+  if (CVT && !GENERAL) {
+    pa = fx_to_double_cvt(va, es);
+    pb = fx_to_double_cvt(vb, es);
+    return;
+  }
   bool fast = !GENERAL && fx_pos_wide(va) && fx_pos_wide(vb);
 #ifdef __CUDA_ARCH__
   fast = __all_sync(__activemask(), fast);
@@ -364,6 +386,11 @@ __host__ __device__ __forceinline__ void fx_pair(const FxClass& q, int64_t Dk, i
   }
 }
 
+#ifndef LBM_FX_CVT_PAIRS
+#define LBM_FX_CVT_PAIRS 2
+#endif
+constexpr int kFxCvtPairs = LBM_FX_CVT_PAIRS;
+
 // The nine pairs in the direction order of the lattice (see fx_moments), from
 // the moment-scale D and Sk of fx_moments; es = emax - KX.
 template <bool LP1, int KX, bool GENERAL = false>
@@ -375,15 +402,16 @@ __host__ __device__ __forceinline__ void fx_pairs(const FxClass& q, const int64_
     Df[k] = static_cast<int64_t>(static_cast<uint64_t>(D[k]) << KX);
     Sf[k] = LP1 ? 0 : static_cast<int64_t>(static_cast<uint64_t>(Sk[k]) << KX);
   }
-  fx_pair<1, 0, 0, false, LP1, GENERAL>(q, Df[1], Sf[1], qm, qp, es, p[1], p[2]);
-  fx_pair<0, 1, 0, false, LP1, GENERAL>(q, Df[2], Sf[2], qm, qp, es, p[3], p[4]);
-  fx_pair<0, 0, 1, false, LP1, GENERAL>(q, Df[3], Sf[3], qm, qp, es, p[5], p[6]);
-  fx_pair<1, 1, 0, true, LP1, GENERAL>(q, Df[4], Sf[4], qm, qp, es, p[7], p[8]);
-  fx_pair<1, -1, 0, true, LP1, GENERAL>(q, Df[5], Sf[5], qm, qp, es, p[9], p[10]);
-  fx_pair<1, 0, 1, true, LP1, GENERAL>(q, Df[6], Sf[6], qm, qp, es, p[11], p[12]);
-  fx_pair<1, 0, -1, true, LP1, GENERAL>(q, Df[7], Sf[7], qm, qp, es, p[13], p[14]);
-  fx_pair<0, 1, 1, true, LP1, GENERAL>(q, Df[8], Sf[8], qm, qp, es, p[15], p[16]);
-  fx_pair<0, 1, -1, true, LP1, GENERAL>(q, Df[9], Sf[9], qm, qp, es, p[17], p[18]);
+  // the first kFxCvtPairs pairs convert on the FP64 pipe (fx_to_double_cvt)
+  fx_pair<1, 0, 0, false, LP1, GENERAL, (kFxCvtPairs > 0)>(q, Df[1], Sf[1], qm, qp, es, p[1], p[2]);
+  fx_pair<0, 1, 0, false, LP1, GENERAL, (kFxCvtPairs > 1)>(q, Df[2], Sf[2], qm, qp, es, p[3], p[4]);
+  fx_pair<0, 0, 1, false, LP1, GENERAL, (kFxCvtPairs > 2)>(q, Df[3], Sf[3], qm, qp, es, p[5], p[6]);
+  fx_pair<1, 1, 0, true, LP1, GENERAL, (kFxCvtPairs > 3)>(q, Df[4], Sf[4], qm, qp, es, p[7], p[8]);
+  fx_pair<1, -1, 0, true, LP1, GENERAL, (kFxCvtPairs > 4)>(q, Df[5], Sf[5], qm, qp, es, p[9], p[10]);
+  fx_pair<1, 0, 1, true, LP1, GENERAL, (kFxCvtPairs > 5)>(q, Df[6], Sf[6], qm, qp, es, p[11], p[12]);
+  fx_pair<1, 0, -1, true, LP1, GENERAL, (kFxCvtPairs > 6)>(q, Df[7], Sf[7], qm, qp, es, p[13], p[14]);
+  fx_pair<0, 1, 1, true, LP1, GENERAL, (kFxCvtPairs > 7)>(q, Df[8], Sf[8], qm, qp, es, p[15], p[16]);
+  fx_pair<0, 1, -1, true, LP1, GENERAL, (kFxCvtPairs > 8)>(q, Df[9], Sf[9], qm, qp, es, p[17], p[18]);
 }
 
 // Q64 image of a rate constant |x| < 1/2: round(x * 2^64).
