@@ -37,21 +37,22 @@ import geometry  # noqa: E402
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 # FP64-pipe instructions per node of the AA steps with a uniform body force
-# along x, counted by ncu (smsp__sass_thread_inst_executed_op_{dadd,dfma,dmul}
-# _pred_on.sum over the nodes of one launch): 27 with omega_plus = 1 (1 DADD,
-# 13 DFMA, 13 DMUL), the same for the even and odd step.  The moments and the
-# pair update run on the integer pipe in fixed point; what stays on the FP64
-# pipe is the per-node terms (density, the reciprocal's Newton steps,
-# velocity, K0, T, O) and the rest PDF, which takes one FMA more when
-# omega_plus != 1.
-COLL_DP_INSTR_GENERAL = 28
-COLL_DP_INSTR_UNIT_OMEGA = 27
+# along x, counted by ncu over the nodes of one launch, the same for the even
+# and odd step: sm__inst_executed_pipe_fp64.sum = 31 per node with
+# omega_plus = 1, of which 27 are arithmetic (smsp__sass_thread_inst_executed
+# _op_{dadd,dfma,dmul}_pred_on.sum: 1 DADD, 13 DFMA, 13 DMUL) and 4 the int64 ->
+# double conversions of two pairs' outputs.  The moments and the pair update
+# run on the integer pipe in fixed point; what stays on the FP64 pipe is the
+# per-node terms (density, the reciprocal's Newton steps, velocity, K0, T, O)
+# and the rest PDF, which takes one FMA more when omega_plus != 1.
+COLL_DP_INSTR_GENERAL = 32
+COLL_DP_INSTR_UNIT_OMEGA = 31
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a
 # kernel on the 10,896,954-node bed, from an ncu capture of the current kernel
 # version, with the profile that holds it; kernels not listed print null.
 TRAFFIC_PROFILED = {
-    ("aa_odd_ria_f64", 10896954): (1823296512 + 1595326976, "profiles/aa_pair_f64_packed_bed_256.md"),
-    ("aa_even_f64", 10896954): (1656411136 + 1594696704, "profiles/aa_pair_f64_packed_bed_256.md"),
+    ("aa_odd_ria_f64", 10896954): (1823450368 + 1595747584, "profiles/aa_pair_f64_packed_bed_256.md"),
+    ("aa_even_f64", 10896954): (1656418048 + 1594644992, "profiles/aa_pair_f64_packed_bed_256.md"),
 }
 
 WORKLOAD = dict(name="packed_bed_256_rsa_r12", X=256, Y=256, Z=256, radius=12.0, seed=1, rejections=20000,
