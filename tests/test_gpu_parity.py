@@ -293,3 +293,28 @@ def test_cuda_graph_replay_matches_direct_launches(form):
     torch.cuda.synchronize()
     assert b.t == 40
     assert torch.equal(a.canonical(), b.canonical())
+
+
+@pytest.mark.parametrize("form,ria", [("aa", True), ("aa", False), ("osnt", True), ("et", False)])
+def test_f64_mixed_arithmetic_paths(form, ria):
+    """The FP64 collision picks, per warp, between the fixed-point pair update with
+    short conversions, the same update with the general conversions, and the FP64
+    update.  A state that mixes nodes for all three in one launch (most near
+    equilibrium; some with |u_x| = 0.3, beyond the fixed-point range; some with
+    PDFs spread over more than 5 binades; some with a negative PDF) still
+    matches the oracle to 1e-12 after every step."""
+    solid = geometry.random_voxels(23, 19, 17, 0.25, 77)
+    per = (1, 0, 0)
+    T = otables.Tables(solid, periodic=per)
+    lat = lbm.Lattice(solid, periodic=per).upload(lbm.LBM_TABLES_ADJ | lbm.LBM_TABLES_RIA | lbm.LBM_TABLES_ET)
+    op, lp = _params(g=(1e-4, 0.0, 0.0), omega=1.0)
+    F0 = _state(T.N, 31)
+    fast = olbm.uniform_state(T.N, op, 1.0, (0.3, 0.0, 0.0))
+    idx = torch.arange(T.N)
+    F0[:, idx % 37 == 5] = fast[:, idx % 37 == 5]          # |u| beyond the fixed-point range
+    F0[7, idx % 41 == 3] *= 1e-3                              # PDFs over more than 5 binades
+    F0[12, idx % 53 == 8] = -1e-4                             # a negative PDF
+    for steps in (1, 2, 3):
+        ref = _run_oracle(T, F0, op, steps, None, "osnt" if form == "et" else form)
+        got = _run_gpu(lat, "f64", lp, F0, steps, None, form, ria)
+        assert _relerr(got, ref) <= TOL64, (steps, _relerr(got, ref))
