@@ -99,27 +99,28 @@ template <class R> AdjConst<R> make_adj(const KParams& kp) {
 // w0 mu_0 for M0).  FP64 forms those sums exactly in fixed point on the
 // integer pipe (exact64.cuh) and rounds each once; P_k is converted only when
 // the caller needs it (l+ != 1).
-template <class R, bool NEED_P>
+// NEED_PD: convert P and D to R (the FP64 pair update needs them; the
+// fixed-point one reads the integers Pi, Di at the scale emax instead).
+template <class R, bool NEED_P, bool NEED_PD = true>
 __device__ __forceinline__ void adj_moments(const R (&mu)[kQ], const AdjConst<R>& c, R (&P)[10], R (&D)[10], R& M0,
                                             R& M1x, R& M1y, R& M1z, R& Mxx, R& Myy, R& Mzz, R& Mxy, R& Mxz,
-                                            R& Myz) {
+                                            R& Myz, int64_t (&Pi)[10], int64_t (&Di)[10], int& emax) {
   using ::fma;
   const R w2 = c.w[2];
   if constexpr (std::is_same<R, double>::value) {
     uint64_t b[kQ];
 #pragma unroll
     for (int i = 0; i < kQ; ++i) b[i] = dbits(mu[i]);
-    const int emax = fx_scale(b);
+    emax = fx_scale(b);
     int64_t f[kQ];
 #pragma unroll
     for (int i = 0; i < kQ; ++i) f[i] = fx_of(b[i], emax);
-    int64_t Pi[10], Di[10];
 #pragma unroll
     for (int k = 1; k <= 9; ++k) {
       Pi[k] = f[2 * k - 1] + f[2 * k];
       Di[k] = f[2 * k - 1] - f[2 * k];
-      if (NEED_P) P[k] = fx_to_double(Pi[k], emax);
-      D[k] = fx_to_double(Di[k], emax);
+      if (NEED_PD && NEED_P) P[k] = fx_to_double(Pi[k], emax);
+      if (NEED_PD) D[k] = fx_to_double(Di[k], emax);
     }
     // every integer sum below has at most 24 terms of magnitude < 2^58
     const int64_t A1 = Pi[1] + Pi[2] + Pi[3];
@@ -206,7 +207,10 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(DevTables t, KParams kp, Col
     mu[j] = mp < -1 ? -v : v;
   }
   R P[10], D[10], M0, M1x, M1y, M1z, Mxx, Myy, Mzz, Mxy, Mxz, Myz;
-  adj_moments<R, !LP1>(mu, c, P, D, M0, M1x, M1y, M1z, Mxx, Myy, Mzz, Mxy, Mxz, Myz);
+  int64_t Pi[10], Di[10];
+  int emax_mu = 0;
+  constexpr bool kFxOut = std::is_same<R, double>::value;  // the fixed-point pair update below
+  adj_moments<R, !LP1, !kFxOut>(mu, c, P, D, M0, M1x, M1y, M1z, Mxx, Myy, Mzz, Mxy, Mxz, Myz, Pi, Di, emax_mu);
   const R M2ux = fma(Mxx, ux, fma(Mxy, uy, Mxz * uz));
   const R M2uy = fma(Mxy, ux, fma(Myy, uy, Myz * uz));
   const R M2uz = fma(Mxz, ux, fma(Myz, uy, Mzz * uz));
@@ -260,6 +264,40 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(DevTables t, KParams kp, Col
     grad_s[n] += L::to_double(gs);
   }
   L::st(lam + n, LP1 ? A : fma(c.omlp, mu[0], A));
+  if constexpr (kFxOut) {
+    // The pair update lambda_a,b = e +- o, e = A + qp P_k, o = qm D_k + c_a.B, in
+    // 64-bit fixed point at one bit finer than the adjoint moments' scale:
+    // P_k and D_k enter exactly, A and B truncated, the products floored,
+    // each output rounded once.  |mu_i| < 2 B_mu gives |D_k|, |P_k| < 4 B_mu;
+    // with |A|, |B_a| < 4 B_mu (checked) every value stays below 16 B_mu, half
+    // the int64 range at this scale.  Otherwise the warp takes the FP64 update.
+    constexpr int kxa = 1;
+    const bool ok = emax_mu < kFxMaxExp && dexp(A) <= emax_mu + 1 && dexp(Bx) <= emax_mu + 1 &&
+                    dexp(By) <= emax_mu + 1 && dexp(Bz) <= emax_mu + 1;
+    if (__all_sync(__activemask(), ok)) {
+      const int es = emax_mu - kxa;
+      const int64_t Af = fx_of(dbits(A), es);
+      const int64_t Bxf = fx_of(dbits(Bx), es), Byf = fx_of(dbits(By), es), Bzf = fx_of(dbits(Bz), es);
+#pragma unroll
+      for (int k = 1; k <= 9; ++k) {
+        const int a = 2 * k - 1;
+        const int64_t Bc = k == 1 ? Bxf : k == 2 ? Byf : k == 3 ? Bzf : k == 4 ? Bxf + Byf : k == 5 ? Bxf - Byf
+                         : k == 6 ? Bxf + Bzf : k == 7 ? Bxf - Bzf : k == 8 ? Byf + Bzf : Byf - Bzf;
+        const int64_t Df = static_cast<int64_t>(static_cast<uint64_t>(Di[k]) << kxa);
+        int64_t e = Af;
+        if (!LP1) e += mulhi_q64(cc.qp_fx, static_cast<int64_t>(static_cast<uint64_t>(Pi[k]) << kxa));
+        const int64_t o = mulhi_q64(cc.qm_fx, Df) + Bc;
+        L::st(lam + at(a, t.npad, n), fx_to_double(e + o, es));
+        L::st(lam + at(a + 1, t.npad, n), fx_to_double(e - o, es));
+      }
+      return;
+    }
+#pragma unroll
+    for (int k = 1; k <= 9; ++k) {
+      if (!LP1) P[k] = fx_to_double(Pi[k], emax_mu);
+      D[k] = fx_to_double(Di[k], emax_mu);
+    }
+  }
 #pragma unroll
   for (int k = 1; k <= 9; ++k) {
     const int a = 2 * k - 1;
