@@ -3,10 +3,11 @@
 The oracle cannot step 10.9 M nodes quickly, so the check is split:
 * the library's enumeration and adjacency list equal the oracle's over the
   whole lattice (integer for integer);
-* two AA steps (even + odd, RIA: the bench's timed pair), and two Esoteric
-  Twist steps, from a seeded perturbed state, read back as the canonical
-  state, equal the oracle at 2000 sampled nodes, each computed from its own
-  two-step dependency cone;
+* two AA steps (even + odd, RIA: the bench's timed pair), two OS-NT steps
+  and two Esoteric Twist steps, from a seeded perturbed state, read back as
+  the canonical state, equal the oracle at 2000 sampled nodes, each computed
+  from its own two-step dependency cone (the last 128-node tile is partial:
+  N mod 128 = 58);
 * mass (walls + one periodic axis) is conserved over 20 steps at full size.
 """
 import numpy as np
@@ -50,13 +51,14 @@ def test_fullsize_tables_identical(bed):
 
 
 @pytest.mark.parametrize("form,prec,tol", [("aa", "f64", 1e-12), ("aa", "f64df", 1e-12), ("aa", "f32", 1e-6),
-                                           ("et", "f64", 1e-12), ("et", "f32", 1e-6)])
+                                           ("aa", "f16s", 5e-4), ("osnt", "f64", 1e-12), ("osnt", "f32", 1e-6),
+                                           ("osnt", "f16s", 5e-4), ("et", "f64", 1e-12), ("et", "f32", 1e-6)])
 def test_fullsize_sampled_two_step_parity(bed, form, prec, tol):
     solid, lat, xyz, adj = bed
     N = lat.N
     lat.upload(lbm.LBM_TABLES_ADJ | lbm.LBM_TABLES_RIA | (lbm.LBM_TABLES_ET if form == "et" else 0))
     op = olbm.Params(omega_plus=1.0, magic=3 / 16, g=BED["g"])
-    lp = lbm.Params(omega_plus=1.0, magic=3 / 16, g=BED["g"], shifted=(prec == "f32"))
+    lp = lbm.Params(omega_plus=1.0, magic=3 / 16, g=BED["g"], shifted=(prec in ("f32", "f16s")))
     F0 = _state(N, 5)
     solver = lbm.Solver(lat, prec, lp, form=form, ria=True)
     solver.load(F0.cuda())
