@@ -127,6 +127,45 @@ __device__ __forceinline__ size_t at(int dir, uint32_t npad, int node) {
   return static_cast<unsigned long long>(static_cast<unsigned>(dir)) * npad + static_cast<unsigned>(node);
 }
 
+// ---- L2 eviction priority of the index tables ------------------------------------------
+// The index tables (run words, run slots, adjacency runs) are read again every
+// step, while the PDF grids stream through L2 once per step and do not fit in
+// it.  Index loads carry an evict-last hint, so the tables stay in L2 across
+// steps as far as it holds them.  Measured on the 256^3 bed (GFLUP/s, no hint
+// -> hint): FP16S OS-NT-R 41.2 -> 44.1, AA-R 56.1 -> 56.9; FP32 OS-NT-R 34.7
+// -> 35.2, AA-R 37.7 -> 37.9; FP64 unchanged.  An evict-first hint on the PDF
+// loads as well was slower in every form (AA-R FP16S 40.4, FP32 29.1): the AA
+// steps write back to the lines they read.  The plain adjacency list (785 MB
+// on the bed) and the Esoteric Twist tables gained nothing from the hint
+// (within +-0.7 %) and load without it.
+#ifndef LBM_L2_HINTS
+#define LBM_L2_HINTS 1
+#endif
+__device__ __forceinline__ unsigned long long l2_keep() {
+  // volatile: one policy per load instead of a 64-bit value held live across
+  // the kernel (which made the FP16 / FP32 odd steps spill)
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ int ldg_keep(const int* p) {
+  int v;
+  asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(l2_keep()));
+  return v;
+}
+__device__ __forceinline__ unsigned ldg_keep(const unsigned* p) {
+  unsigned v;
+  asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(l2_keep()));
+  return v;
+}
+// an index-table word
+template <class T> __device__ __forceinline__ T ld_idx(const T* p) {
+  if constexpr (LBM_L2_HINTS != 0)
+    return ldg_keep(p);
+  else
+    return __ldg(p);
+}
+
 // ---- neighbour addressing --------------------------------------------------------------
 // m[i-1] for i = 1..18: the adjacency entry of node n (node index or marker).
 // Plain form: one coalesced int32 load per direction (D_idx = 72 B/node).
@@ -147,15 +186,16 @@ struct RiaCursor {
   int off;   // node - first node of the run
 };
 
+template <bool KEEP = true>
 __device__ __forceinline__ RiaCursor ria_locate_in(const uint32_t* head_bits, const int32_t* warp_run0,
                                                    const int32_t* warp_head0, int n) {
   const int w = n >> 5;
   const unsigned lane = unsigned(n) & 31u;
-  const unsigned bits = __ldg(head_bits + w);
+  const unsigned bits = KEEP ? ld_idx(head_bits + w) : __ldg(head_bits + w);
   const unsigned le = bits & (0xffffffffu >> (31u - lane));  // heads at lanes 0..lane
   RiaCursor c;
-  c.r = __ldg(warp_run0 + w) + __popc(le) - int(bits & 1u);
-  const int head = le ? (w << 5) + (31 - __clz(le)) : __ldg(warp_head0 + w);
+  c.r = (KEEP ? ld_idx(warp_run0 + w) : __ldg(warp_run0 + w)) + __popc(le) - int(bits & 1u);
+  const int head = le ? (w << 5) + (31 - __clz(le)) : KEEP ? ld_idx(warp_head0 + w) : __ldg(warp_head0 + w);
   c.off = n - head;
   return c;
 }
@@ -167,7 +207,7 @@ __device__ __forceinline__ RiaCursor ria_locate(const DevTables& t, int n) {
 __device__ __forceinline__ void nbr_ria(const DevTables& t, RiaCursor c, int (&m)[18]) {
 #pragma unroll
   for (int i = 0; i < 18; ++i) {
-    const int a = __ldg(t.run_adj + at(i, t.rpad, c.r));
+    const int a = ld_idx(t.run_adj + at(i, t.rpad, c.r));
     m[i] = a >= 0 ? a + c.off : a;
   }
 }
@@ -581,7 +621,7 @@ __global__ void __launch_bounds__(kBlock, MinCtasOsnt<PREC, RIA>::value) k_osnt(
     d[0] = ld_step<PREC>(src + n, kp.inv_scale);
 #pragma unroll
     for (int i = 1; i < kQ; ++i)
-      d[i] = ld_step<PREC>(src + static_cast<unsigned>(__ldg(t.run_slot_osnt + at(i - 1, t.rpad, cur.r)) + cur.off),
+      d[i] = ld_step<PREC>(src + static_cast<unsigned>(ld_idx(t.run_slot_osnt + at(i - 1, t.rpad, cur.r)) + cur.off),
                            kp.inv_scale);
     const R sn = DRAG ? R(__ldg(s + n)) : R(0);
     collide<R, FORCE, DRAG, LP1, kScaled<PREC>>(d, c, sn);
@@ -681,7 +721,7 @@ __global__ void __launch_bounds__(kBlock, MinCtasOdd<PREC, RIA>::value) k_aa_odd
     unsigned sl[18];
 #pragma unroll
     for (int j = 0; j < 18; ++j) {
-      sl[j] = static_cast<unsigned>(__ldg(t.run_slot + at(j, t.rpad, cur.r)) + cur.off);
+      sl[j] = static_cast<unsigned>(ld_idx(t.run_slot + at(j, t.rpad, cur.r)) + cur.off);
       s_m[j][threadIdx.x] = static_cast<int>(sl[j]);
     }
     if constexpr (PREC == LBM_F64_DF) {
@@ -813,8 +853,8 @@ __global__ void __launch_bounds__(kBlock, LBM_MIN_CTAS_ODD_X2) k_aa_odd_x2(DevTa
     unsigned sl0[18], sl1[18];
 #pragma unroll
     for (int j = 0; j < 18; ++j) {
-      sl0[j] = static_cast<unsigned>(__ldg(t.run_slot + at(j, t.rpad, c0.r)) + c0.off);
-      sl1[j] = static_cast<unsigned>(__ldg(t.run_slot + at(j, t.rpad, c1.r)) + c1.off);
+      sl0[j] = static_cast<unsigned>(ld_idx(t.run_slot + at(j, t.rpad, c0.r)) + c0.off);
+      sl1[j] = static_cast<unsigned>(ld_idx(t.run_slot + at(j, t.rpad, c1.r)) + c1.off);
     }
 #pragma unroll
     for (int j = 0; j < 18; ++j) {
@@ -887,7 +927,7 @@ __device__ __forceinline__ unsigned et_locate(const DevTables& t, int n, int (&l
     et_locations(t, n, loc);
     return __ldg(t.et_mask + n);
   }
-  const RiaCursor c = ria_locate_in(t.et_head_bits, t.et_warp_run0, t.et_warp_head0, n);
+  const RiaCursor c = ria_locate_in<false>(t.et_head_bits, t.et_warp_run0, t.et_warp_head0, n);
   loc[0] = n;
 #pragma unroll
   for (int k = 0; k < 6; ++k) loc[k + 1] = __ldg(t.et_run_nb + at(k, t.et_rpad, c.r)) + c.off;
