@@ -411,6 +411,7 @@ int launch_adjoint_t(const lbm_lattice* L, const KParams& kp, const void* G, con
   auto st = static_cast<cudaStream_t>(stream);
   const auto cc = dev::make_coll<R>(kp);
   const auto ac = dev::make_adj<R>(kp);
+  const unsigned blk = dev::kBlock;
   const unsigned g = grid_of(L->N);
   const T* Gp = static_cast<const T*>(G);
   const LT* ln = static_cast<const LT*>(lam_next);

@@ -36,6 +36,16 @@ __host__ __device__ constexpr int wclass(int i) { return i == 0 ? 0 : (i <= 6 ? 
 __host__ __device__ constexpr double wgt(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
 
 constexpr int kBlock = 128;  // nodes per CTA of the step kernels (one node per thread)
+// The resident-CTA counts below are for 128-thread CTAs; a kernel launched
+// with B threads per CTA takes ctas(n, B) to keep the same threads per SM.
+constexpr int ctas(int n128, int b = kBlock) { return n128 * 128 / b > 0 ? n128 * 128 / b : 1; }
+// CTA size of the FP16S OS-NT step with RIA.  Sweeps on the 256^3 bed:
+// 128 / 192 / 256 / 512 threads gave 44.1 / 47.0 / 49.6 / 47.5 GFLUP/s (at the
+// same threads per SM).  Every other step and precision was flat or slower
+// above 128 (Esoteric Twist at 256: -1.7 % to +3 %).
+#ifndef LBM_OSNT_BLOCK_F16R
+#define LBM_OSNT_BLOCK_F16R 256
+#endif
 // Minimum resident CTAs per SM of the step kernels (caps registers at
 // 65536 / (128 * n)), from sweeps on GB300.  The indirect steps are
 // latency-bound (index words, then gathers, then scattered stores): with RIA
@@ -601,15 +611,19 @@ __device__ __forceinline__ void gather(const typename St<PREC>::T* g, uint32_t n
 }
 
 // ---- kernels -----------------------------------------------------------------------------
+template <int PREC, bool RIA> struct OsntBlock {
+  static constexpr int value = PREC == LBM_F16S && RIA ? LBM_OSNT_BLOCK_F16R : kBlock;
+};
+
 // OS-NT step: pull (indirect) from src, collide, store locally into dst with
 // evict-first stores so the write stream does not push src out of L2.
 template <int PREC, bool RIA, bool FORCE, bool DRAG, bool LP1 = false>
-__global__ void __launch_bounds__(kBlock, MinCtasOsnt<PREC, RIA>::value) k_osnt(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
-                                                 const typename St<PREC>::T* __restrict__ src,
-                                                 typename St<PREC>::T* __restrict__ dst, const float* __restrict__ s,
-                                                 int N) {
+__global__ void __launch_bounds__(OsntBlock<PREC, RIA>::value,
+                                  ctas(MinCtasOsnt<PREC, RIA>::value, OsntBlock<PREC, RIA>::value))
+    k_osnt(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c, const typename St<PREC>::T* __restrict__ src,
+           typename St<PREC>::T* __restrict__ dst, const float* __restrict__ s, int N) {
   using R = typename St<PREC>::R;
-  const int n0 = blockIdx.x * kBlock;
+  const int n0 = blockIdx.x * OsntBlock<PREC, RIA>::value;
   const int n = n0 + threadIdx.x;
   if (RIA && t.run_slot_osnt) {
     // Pre-resolved run slots (no pressure faces; the grid below 2^31 slots):
@@ -648,7 +662,7 @@ __global__ void __launch_bounds__(kBlock, MinCtasOsnt<PREC, RIA>::value) k_osnt(
 // AA even step: direct read of the 19 local PDFs, collide, write to the
 // opposite local slots (no index loads at all).
 template <int PREC, bool FORCE, bool DRAG, bool LP1 = false>
-__global__ void __launch_bounds__(kBlock, MinCtasEven<PREC>::value) k_aa_even(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
+__global__ void __launch_bounds__(kBlock, ctas(MinCtasEven<PREC>::value)) k_aa_even(DevTables t, KParams kp, CollConst<typename St<PREC>::R> c,
                                                     typename St<PREC>::T* __restrict__ A,
                                                     const float* __restrict__ s, int N) {
   using R = typename St<PREC>::R;
@@ -700,7 +714,7 @@ __global__ void __launch_bounds__(kBlock) k_aa_even_h2(DevTables t, KParams kp, 
 // AA odd step: read f_i from the neighbour's opposite slot A[inv i][m_i], collide,
 // write p_i to A[i][m_{inv i}] -- the same 19 slots, so in place and race-free.
 template <int PREC, bool RIA, bool FORCE, bool DRAG, bool LP1 = false>
-__global__ void __launch_bounds__(kBlock, MinCtasOdd<PREC, RIA>::value) k_aa_odd(DevTables t, KParams kp,
+__global__ void __launch_bounds__(kBlock, ctas(MinCtasOdd<PREC, RIA>::value)) k_aa_odd(DevTables t, KParams kp,
                                                                               CollConst<typename St<PREC>::R> c,
                                                                               typename St<PREC>::T* __restrict__ A,
                                                                               const float* __restrict__ s, int N) {
@@ -835,7 +849,7 @@ __global__ void __launch_bounds__(kBlock, MinCtasOdd<PREC, RIA>::value) k_aa_odd
 #define LBM_MIN_CTAS_ODD_X2 8
 #endif
 template <int PREC, bool FORCE, bool DRAG>
-__global__ void __launch_bounds__(kBlock, LBM_MIN_CTAS_ODD_X2) k_aa_odd_x2(DevTables t, KParams kp,
+__global__ void __launch_bounds__(kBlock, ctas(LBM_MIN_CTAS_ODD_X2)) k_aa_odd_x2(DevTables t, KParams kp,
                                                                          CollConst<typename St<PREC>::R> c,
                                                                          typename St<PREC>::T* __restrict__ A,
                                                                          const float* __restrict__ s, int N) {
@@ -935,7 +949,7 @@ __device__ __forceinline__ unsigned et_locate(const DevTables& t, int n, int (&l
 }
 
 template <int PREC, bool RIA, bool ODD, bool FORCE, bool DRAG, bool LP1 = false>
-__global__ void __launch_bounds__(kBlock, MinCtasEt<PREC>::value) k_et(DevTables t, KParams kp,
+__global__ void __launch_bounds__(kBlock, ctas(MinCtasEt<PREC>::value)) k_et(DevTables t, KParams kp,
                                                                           CollConst<typename St<PREC>::R> c,
                                                                           typename St<PREC>::T* __restrict__ A,
                                                                           const float* __restrict__ s, int N) {
@@ -1278,16 +1292,17 @@ inline bool has_force(const KParams& kp) { return kp.g[0] != 0.0 || kp.g[1] != 0
 template <int PREC> constexpr bool kLp1Path = PREC == LBM_F64 || PREC == LBM_F64_DF;
 template <int PREC> inline bool use_lp1(const KParams& kp) { return kLp1Path<PREC> && kp.lp == 1.0; }
 
-// Launch KERNEL<PREC, ARGS..., LP1> with LP1 = lp1 where that instantiation exists.
+// Launch KERNEL<PREC, ARGS..., LP1> with LP1 = lp1 where that instantiation
+// exists, on grid g of blk-thread CTAs.
 #define LBM_LAUNCH_LP1(KERNEL, TARGS, LAUNCH_ARGS)                             \
   do {                                                                         \
     if constexpr (kLp1Path<PREC>) {                                            \
       if (lp1) {                                                               \
-        dev::KERNEL<PREC, TARGS, true><<<g, dev::kBlock, 0, st>>> LAUNCH_ARGS; \
+        dev::KERNEL<PREC, TARGS, true><<<g, blk, 0, st>>> LAUNCH_ARGS;         \
         break;                                                                 \
       }                                                                        \
     }                                                                          \
-    dev::KERNEL<PREC, TARGS, false><<<g, dev::kBlock, 0, st>>> LAUNCH_ARGS;    \
+    dev::KERNEL<PREC, TARGS, false><<<g, blk, 0, st>>> LAUNCH_ARGS;            \
   } while (0)
 #define LBM_TARGS3(A_, B_, C_) A_, B_, C_
 #define LBM_TARGS4(A_, B_, C_, D_) A_, B_, C_, D_
@@ -1298,7 +1313,8 @@ int launch_osnt_t(const lbm_lattice* L, const KParams& kp, const void* src, void
                   void* stream) {
   using T = typename dev::St<PREC>::T;
   auto st = static_cast<cudaStream_t>(stream);
-  const unsigned g = grid_of(L->N);
+  const unsigned blk = ria ? dev::OsntBlock<PREC, true>::value : dev::OsntBlock<PREC, false>::value;
+  const unsigned g = unsigned((L->N + blk - 1) / blk);
   const T* a = static_cast<const T*>(src);
   T* b = static_cast<T*>(dst);
   const int N = int(L->N);
@@ -1327,6 +1343,7 @@ int launch_aa_t(const lbm_lattice* L, const KParams& kp, void* pdf, int parity, 
                 void* stream) {
   using T = typename dev::St<PREC>::T;
   auto st = static_cast<cudaStream_t>(stream);
+  const unsigned blk = dev::kBlock;
   const unsigned g = grid_of(L->N);
   T* A = static_cast<T*>(pdf);
   const int N = int(L->N);
@@ -1376,6 +1393,7 @@ int launch_et_t(const lbm_lattice* L, const KParams& kp, void* pdf, int parity, 
                 void* stream) {
   using T = typename dev::St<PREC>::T;
   auto st = static_cast<cudaStream_t>(stream);
+  const unsigned blk = dev::kBlock;
   const unsigned g = grid_of(L->N);
   T* A = static_cast<T*>(pdf);
   const int N = int(L->N);
