@@ -168,13 +168,15 @@ __device__ __forceinline__ unsigned ldg_keep(const unsigned* p) {
   asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(l2_keep()));
   return v;
 }
-// an index-table word
-template <class T> __device__ __forceinline__ T ld_idx(const T* p) {
-  if constexpr (LBM_L2_HINTS != 0)
+// an index-table word (KEEP = false: a plain load; the double-float OS-NT
+// step with RIA ran at 5.5 instead of 12.8 GFLUP/s on the bed with the hint)
+template <bool KEEP = true, class T> __device__ __forceinline__ T ld_idx(const T* p) {
+  if constexpr (LBM_L2_HINTS != 0 && KEEP)
     return ldg_keep(p);
   else
     return __ldg(p);
 }
+template <int PREC> constexpr bool kKeepIdx = PREC != LBM_F64_DF;
 
 // ---- neighbour addressing --------------------------------------------------------------
 // m[i-1] for i = 1..18: the adjacency entry of node n (node index or marker).
@@ -201,23 +203,23 @@ __device__ __forceinline__ RiaCursor ria_locate_in(const uint32_t* head_bits, co
                                                    const int32_t* warp_head0, int n) {
   const int w = n >> 5;
   const unsigned lane = unsigned(n) & 31u;
-  const unsigned bits = KEEP ? ld_idx(head_bits + w) : __ldg(head_bits + w);
+  const unsigned bits = ld_idx<KEEP>(head_bits + w);
   const unsigned le = bits & (0xffffffffu >> (31u - lane));  // heads at lanes 0..lane
   RiaCursor c;
-  c.r = (KEEP ? ld_idx(warp_run0 + w) : __ldg(warp_run0 + w)) + __popc(le) - int(bits & 1u);
-  const int head = le ? (w << 5) + (31 - __clz(le)) : KEEP ? ld_idx(warp_head0 + w) : __ldg(warp_head0 + w);
+  c.r = ld_idx<KEEP>(warp_run0 + w) + __popc(le) - int(bits & 1u);
+  const int head = le ? (w << 5) + (31 - __clz(le)) : ld_idx<KEEP>(warp_head0 + w);
   c.off = n - head;
   return c;
 }
 
-__device__ __forceinline__ RiaCursor ria_locate(const DevTables& t, int n) {
-  return ria_locate_in(t.head_bits, t.warp_run0, t.warp_head0, n);
+template <bool KEEP = true> __device__ __forceinline__ RiaCursor ria_locate(const DevTables& t, int n) {
+  return ria_locate_in<KEEP>(t.head_bits, t.warp_run0, t.warp_head0, n);
 }
 
-__device__ __forceinline__ void nbr_ria(const DevTables& t, RiaCursor c, int (&m)[18]) {
+template <bool KEEP = true> __device__ __forceinline__ void nbr_ria(const DevTables& t, RiaCursor c, int (&m)[18]) {
 #pragma unroll
   for (int i = 0; i < 18; ++i) {
-    const int a = ld_idx(t.run_adj + at(i, t.rpad, c.r));
+    const int a = ld_idx<KEEP>(t.run_adj + at(i, t.rpad, c.r));
     m[i] = a >= 0 ? a + c.off : a;
   }
 }
@@ -630,12 +632,12 @@ __global__ void __launch_bounds__(OsntBlock<PREC, RIA>::value,
     // P_i (or P_inv(i) through a bounce-back marker) is pulled from slot
     // run_slot_osnt[i][r] + off of the flat source grid.
     if (n >= N) return;
-    const RiaCursor cur = ria_locate(t, n);
+    const RiaCursor cur = ria_locate<kKeepIdx<PREC>>(t, n);
     R d[kQ];
     d[0] = ld_step<PREC>(src + n, kp.inv_scale);
 #pragma unroll
     for (int i = 1; i < kQ; ++i)
-      d[i] = ld_step<PREC>(src + static_cast<unsigned>(ld_idx(t.run_slot_osnt + at(i - 1, t.rpad, cur.r)) + cur.off),
+      d[i] = ld_step<PREC>(src + static_cast<unsigned>(ld_idx<kKeepIdx<PREC>>(t.run_slot_osnt + at(i - 1, t.rpad, cur.r)) + cur.off),
                            kp.inv_scale);
     const R sn = DRAG ? R(__ldg(s + n)) : R(0);
     collide<R, FORCE, DRAG, LP1, kScaled<PREC>>(d, c, sn);
@@ -646,7 +648,7 @@ __global__ void __launch_bounds__(OsntBlock<PREC, RIA>::value,
   int m[18];
   if (RIA) {
     if (n >= N) return;
-    nbr_ria(t, ria_locate(t, n), m);
+    nbr_ria<kKeepIdx<PREC>>(t, ria_locate<kKeepIdx<PREC>>(t, n), m);
   } else {
     if (n >= N) return;
     nbr_adj(t, n, m);
@@ -731,11 +733,11 @@ __global__ void __launch_bounds__(kBlock, ctas(MinCtasOdd<PREC, RIA>::value)) k_
     // Pre-resolved run slots (no pressure faces; the grid below 2^31 slots):
     // f_i is read from slot run_slot[i][r] + off of the flat grid, and P_i
     // goes back to the slot f_inv(i) came from.
-    const RiaCursor cur = ria_locate(t, n);
+    const RiaCursor cur = ria_locate<kKeepIdx<PREC>>(t, n);
     unsigned sl[18];
 #pragma unroll
     for (int j = 0; j < 18; ++j) {
-      sl[j] = static_cast<unsigned>(ld_idx(t.run_slot + at(j, t.rpad, cur.r)) + cur.off);
+      sl[j] = static_cast<unsigned>(ld_idx<kKeepIdx<PREC>>(t.run_slot + at(j, t.rpad, cur.r)) + cur.off);
       s_m[j][threadIdx.x] = static_cast<int>(sl[j]);
     }
     if constexpr (PREC == LBM_F64_DF) {
@@ -771,7 +773,7 @@ __global__ void __launch_bounds__(kBlock, ctas(MinCtasOdd<PREC, RIA>::value)) k_
   {
     int m[18];
     if (RIA) {
-      nbr_ria(t, ria_locate(t, n), m);
+      nbr_ria<kKeepIdx<PREC>>(t, ria_locate<kKeepIdx<PREC>>(t, n), m);
     } else {
       nbr_adj(t, n, m);
     }
