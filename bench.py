@@ -497,16 +497,24 @@ def suite_foam(args, lbm, torch):
 
 def suite_adjoint(args, lbm, torch):
     """Adjoint cost: 128^3 periodic box, Brinkman field, FP32 storage, T steps, checkpoint every K."""
-    n = args.box or 128
-    T, K = args.adj_T, args.adj_K
+    return adjoint_box(lbm, torch, args.box or 128, args.adj_T, args.adj_K, fd=args.fd)
+
+
+ADJ_VARIANTS = (("f32", "f32", True), ("f64df", "f64df", True), ("f64", "f64", True), ("f64_full", "f64", False))
+
+
+def adjoint_box(lbm, torch, n=128, T=2000, K=45, variants=ADJ_VARIANTS, fd=0, fd_h=(1e-4, 2e-4, 4e-4)):
+    """The differentiation configuration: an n^3 periodic box with a Brinkman
+    field (smoothed noise, sigma 3, seed 2), objective the mean x-flux after T
+    steps, checkpoints every K; forward and backward timed per storage, and
+    optionally central differences of the FP64 forward at ``fd`` nodes."""
     solid = geometry.empty_box(n, n, n)
     lat = lbm.Lattice(solid, periodic=(1, 1, 1)).upload()
     s = torch.as_tensor(geometry.smooth_noise(n, n, n, 3.0, 2).reshape(-1), device="cuda")
     out = {"suite": "adjoint", "box": n, "fluid_nodes": lat.N, "T": T, "K": K, "variants": {}}
     # deviation (shifted) storage in every precision, plus FP64 with full-f
     # storage, the form that takes the fixed-point pair update in its forward
-    for name, prec, shifted in (("f32", "f32", True), ("f64df", "f64df", True), ("f64", "f64", True),
-                                ("f64_full", "f64", False)):
+    for name, prec, shifted in variants:
         params = lbm.Params(omega_plus=1.0, magic=3 / 16, g=(1e-5, 0.0, 0.0), shifted=shifted)
         G0 = lat.new_grid(prec)
         lbm.lbm_init_equilibrium(lat, prec, params, G0, lbm.LBM_LAYOUT_OSNT, 1.0)
@@ -527,10 +535,10 @@ def suite_adjoint(args, lbm, torch):
         del ws, G0
         torch.cuda.empty_cache()
     ref = out["variants"]["f64"]["grad"]
-    for name in ("f32", "f64df", "f64_full"):
+    for name in [v[0] for v in variants if v[0] != "f64"]:
         gv = out["variants"][name]["grad"]
         out["variants"][name]["grad_err_max_rel"] = float((gv - ref).abs().max() / ref.abs().max())
-    if args.fd:
+    if fd:
         # central differences of the FP64 forward (shifted storage) at args.fd
         # nodes, at h, 2h and 4h.  Truncation error (O(h^2), below 1e-8 here)
         # is far below round-off, so the spread of the quotients between h and
@@ -542,11 +550,11 @@ def suite_adjoint(args, lbm, torch):
         lbm.lbm_init_equilibrium(lat, "f64", params, G0, lbm.LBM_LAYOUT_OSNT, 1.0)
         nb = lbm.lbm_ckpt_workspace_bytes(lat, "f64", T, K)
         ws = torch.empty((nb + 7) // 8, dtype=torch.float64, device="cuda")
-        nodes = rng.choice(lat.N, args.fd, replace=False)
+        nodes = rng.choice(lat.N, fd, replace=False)
         g = np.array([float(ref[int(nd)]) for nd in nodes])
         gmax = float(ref.abs().max())
         fds = {}
-        for h in (1e-4, 2e-4, 4e-4):
+        for h in fd_h:
             vals = []
             for node in nodes:
                 Jv = []
@@ -557,14 +565,14 @@ def suite_adjoint(args, lbm, torch):
                     Jv.append((float(lbm.lbm_flux_forward(lat, "f64", params, G0, sp, T, K, ws)), hh))
                 vals.append((Jv[0][0] - Jv[1][0]) / (Jv[0][1] - Jv[1][1]))
             fds[h] = np.array(vals)
-        for h, h2 in ((1e-4, 2e-4), (2e-4, 4e-4)):
+        for h, h2 in zip(fd_h[:-1], fd_h[1:]):
             err = np.abs(fds[h] - g) / np.abs(g)
             floor = np.abs(fds[h] - fds[h2]) / np.abs(g)
             out[f"fd_h{h:g}"] = {"max_rel_err": float(err.max()), "median_rel_err": float(np.median(err)),
                                  "noise_floor_max_rel": float(floor.max()),
                                  "noise_floor_median_rel": float(np.median(floor)),
                                  "max_err_over_max_grad": float(np.max(np.abs(fds[h] - g)) / gmax)}
-        out["fd_nodes"] = args.fd
+        out["fd_nodes"] = fd
         out["fd_note"] = ("central differences of the FP64 forward (shifted storage) against the FP64 adjoint "
                           "gradient; noise_floor = |FD(h) - FD(2h)| / |dJ/ds_n|, the round-off spread of the "
                           "quotient (truncation is O(h^2), far below it)")
@@ -1089,11 +1097,18 @@ def main():
                 torch.cuda.empty_cache()
 
     # ---- the metric's comparisons: FP32 / FP16S against FP64, the adjoint's cost, energy -------------
-    vs_f64 = adjoint = energy = None
+    vs_f64 = adjoint = energy = adjoint_cfg = None
     if not args.no_variants:
         vs_f64 = precision_leg(lbm, torch, lat, dev, stream)
         adjoint = adjoint_leg(lbm, torch, solid, dev)
         energy = energy_leg(lbm, torch, lat, dev, stream)
+        # the differentiation configuration itself (128^3 box, T = 2000, K = 45): FP32 and FP64
+        # backward/forward, and FD of the FP64 forward at 6 nodes with the noise floor
+        try:
+            adjoint_cfg = adjoint_box(lbm, torch, 128, 2000, 45, variants=(("f32", "f32", True), ("f64", "f64", True)),
+                                      fd=6, fd_h=(1e-4, 2e-4))
+        except Exception as e:  # reported, never hides the headline
+            adjoint_cfg = {"error": str(e)}
 
     # ---- the production configuration: 768^3 foam, FP32 AA-R, 5000 steps (one GPU only) -------------
     production = None
@@ -1135,7 +1150,7 @@ def main():
         "roofline": roofline, "f64_double_float": companion,
         "variants": variants, "vs_f64": vs_f64, "adjoint": adjoint, "cpu_baseline": cpu,
         "e2e": e2e, "gpu_launches": 2 * K, "clocks": clock_summary, "energy": energy,
-        "production_run": production,
+        "production_run": production, "adjoint_box_128": adjoint_cfg,
         "paper_context": {"what": "the paper's roofline predictions, FP64 on 7 Haswell cores of one ccNUMA domain "
                                   "(Table 4, channel, 2.6 GHz), MFLUP/s; context, not a target",
                           "OS-NT": 63.8, "OS-NT-R": 78.4, "AA": 73.8, "AA-R": 82.2},
