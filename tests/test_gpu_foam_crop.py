@@ -2,10 +2,11 @@
 
 The crop is the corner z, y, x < 64 of the 512^3 Voronoi-edge foam of the
 precision study (400 seeds, strut radius 2.5, seed 3), with pressure faces in
-x (rho = 1 +- 5e-4) and walls elsewhere.  After 200 AA-R steps from rest the
-GPU's canonical state, velocity and pressure drop are compared with the FP64
-oracle's: FP64 and double-float at the 1e-12 bar, FP32 and FP16S storage
-within their stated storage-format bounds.
+x (rho = 1 +- 5e-4) and walls elsewhere.  After 200 AA-R (or OS-NT-R) steps
+from rest the GPU's canonical state, velocity and pressure drop are compared
+with the FP64 oracle's AA run (the two forms agree after an even number of
+steps): FP64 and double-float at the 1e-12 bar, FP32 and FP16S storage within
+their stated storage-format bounds.
 """
 import numpy as np
 import pytest
@@ -38,12 +39,13 @@ def crop():
 
 @pytest.mark.parametrize("prec,tol_f,tol_u,tol_dp", [("f64", 1e-12, 1e-9, 1e-10), ("f64df", 1e-12, 1e-9, 1e-10),
                                                      ("f32", 2e-6, 1e-3, 1e-5), ("f16s", 5e-4, 5e-2, 1e-3)])
-def test_foam_crop_against_oracle(crop, prec, tol_f, tol_u, tol_dp):
+@pytest.mark.parametrize("form", ["aa", "osnt"])
+def test_foam_crop_against_oracle(crop, prec, tol_f, tol_u, tol_dp, form):
     solid, T, F_ref, u_ref, dp_ref = crop
     lat = lbm.Lattice(solid, periodic=(0, 0, 0), x_pressure=True).upload()
     lp = lbm.Params(omega_plus=1.0, magic=3 / 16, rho_in=1.0 + 5e-4, rho_out=1.0 - 5e-4,
                     shifted=prec in ("f32", "f16s"))
-    sv = lbm.Solver(lat, prec, lp, form="aa", ria=True)
+    sv = lbm.Solver(lat, prec, lp, form=form, ria=True)
     sv.init_equilibrium(1.0)
     sv.step(STEPS)
     F = sv.canonical().cpu()
