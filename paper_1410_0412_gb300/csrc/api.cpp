@@ -123,9 +123,9 @@ TableLayout table_layout(const lbm_lattice* L, int which) {
     if (L->run_slot_state == 1) {
       t.run_slot = off;
       t.has_run_slot = true;
-      off = align256(off + size_t(18) * L->Rpad * 4);
+      off = align256(off + run_slot_words(L->Rpad) * 4);
       t.run_slot_osnt = off;
-      off = align256(off + size_t(18) * L->Rpad * 4);
+      off = align256(off + run_slot_words(L->Rpad) * 4);
     }
   }
   if (which & LBM_TABLES_ET) {

@@ -168,6 +168,19 @@ __device__ __forceinline__ unsigned ldg_keep(const unsigned* p) {
   asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(l2_keep()));
   return v;
 }
+__device__ __forceinline__ int4 ldg_keep(const int4* p) {
+  int4 v;
+  asm("ld.global.nc.L2::cache_hint.v4.b32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p), "l"(l2_keep()));
+  return v;
+}
+__device__ __forceinline__ int2 ldg_keep(const int2* p) {
+  int2 v;
+  asm("ld.global.nc.L2::cache_hint.v2.b32 {%0, %1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(l2_keep()));
+  return v;
+}
+
 // an index-table word (KEEP = false: a plain load; the double-float OS-NT
 // step with RIA ran at 5.5 instead of 12.8 GFLUP/s on the bed with the hint)
 template <bool KEEP = true, class T> __device__ __forceinline__ T ld_idx(const T* p) {
@@ -177,6 +190,45 @@ template <bool KEEP = true, class T> __device__ __forceinline__ T ld_idx(const T
     return __ldg(p);
 }
 template <int PREC> constexpr bool kKeepIdx = PREC != LBM_F64_DF;
+
+// The 18 slots of run r of a run slot table (derive_run_slots), each plus
+// off: sl[j] belongs to direction j + 1.  Run-major tables take four 16-byte
+// and one 8-byte load (the row is 80-byte aligned: the table starts on a
+// 256-byte boundary).
+// With a stash column (the AA odd step's [18][kBlock] shared array at this
+// thread's lane), each slot is also parked there as soon as it is formed.
+template <bool KEEP>
+__device__ __forceinline__ void run_slots(const int32_t* tbl, uint32_t rpad, int r, int off, unsigned (&sl)[18],
+                                          int* stash = nullptr) {
+#if LBM_SLOT_AOS
+  const int4* p = reinterpret_cast<const int4*>(tbl + static_cast<size_t>(static_cast<unsigned>(r)) * kSlotStride);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    int w[4];
+    if (q < 4) {
+      const int4 v = ld_idx<KEEP>(p + q);
+      w[0] = v.x, w[1] = v.y, w[2] = v.z, w[3] = v.w;
+    } else {
+      const int2 v = ld_idx<KEEP>(reinterpret_cast<const int2*>(p + 4));
+      w[0] = v.x, w[1] = v.y, w[2] = w[3] = 0;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int j = 4 * q + k;
+      if (j < 18) {
+        sl[j] = static_cast<unsigned>(w[k] + off);
+        if (stash) stash[j * kBlock] = static_cast<int>(sl[j]);
+      }
+    }
+  }
+#else
+#pragma unroll
+  for (int j = 0; j < 18; ++j) {
+    sl[j] = static_cast<unsigned>(ld_idx<KEEP>(tbl + at(j, rpad, r)) + off);
+    if (stash) stash[j * kBlock] = static_cast<int>(sl[j]);
+  }
+#endif
+}
 
 // ---- neighbour addressing --------------------------------------------------------------
 // m[i-1] for i = 1..18: the adjacency entry of node n (node index or marker).
@@ -630,15 +682,15 @@ __global__ void __launch_bounds__(OsntBlock<PREC, RIA>::value,
   if (RIA && t.run_slot_osnt) {
     // Pre-resolved run slots (no pressure faces; the grid below 2^31 slots):
     // P_i (or P_inv(i) through a bounce-back marker) is pulled from slot
-    // run_slot_osnt[i][r] + off of the flat source grid.
+    // run_slot_osnt(i, r) + off of the flat source grid.
     if (n >= N) return;
     const RiaCursor cur = ria_locate<kKeepIdx<PREC>>(t, n);
+    unsigned sl[18];
+    run_slots<kKeepIdx<PREC>>(t.run_slot_osnt, t.rpad, cur.r, cur.off, sl);
     R d[kQ];
     d[0] = ld_step<PREC>(src + n, kp.inv_scale);
 #pragma unroll
-    for (int i = 1; i < kQ; ++i)
-      d[i] = ld_step<PREC>(src + static_cast<unsigned>(ld_idx<kKeepIdx<PREC>>(t.run_slot_osnt + at(i - 1, t.rpad, cur.r)) + cur.off),
-                           kp.inv_scale);
+    for (int i = 1; i < kQ; ++i) d[i] = ld_step<PREC>(src + sl[i - 1], kp.inv_scale);
     const R sn = DRAG ? R(__ldg(s + n)) : R(0);
     collide<R, FORCE, DRAG, LP1, kScaled<PREC>>(d, c, sn);
 #pragma unroll
@@ -731,15 +783,11 @@ __global__ void __launch_bounds__(kBlock, ctas(MinCtasOdd<PREC, RIA>::value)) k_
   R d[kQ];
   if (RIA && t.run_slot) {
     // Pre-resolved run slots (no pressure faces; the grid below 2^31 slots):
-    // f_i is read from slot run_slot[i][r] + off of the flat grid, and P_i
+    // f_i is read from slot run_slot(i, r) + off of the flat grid, and P_i
     // goes back to the slot f_inv(i) came from.
     const RiaCursor cur = ria_locate<kKeepIdx<PREC>>(t, n);
     unsigned sl[18];
-#pragma unroll
-    for (int j = 0; j < 18; ++j) {
-      sl[j] = static_cast<unsigned>(ld_idx<kKeepIdx<PREC>>(t.run_slot + at(j, t.rpad, cur.r)) + cur.off);
-      s_m[j][threadIdx.x] = static_cast<int>(sl[j]);
-    }
+    run_slots<kKeepIdx<PREC>>(t.run_slot, t.rpad, cur.r, cur.off, sl, &s_m[0][threadIdx.x]);
     if constexpr (PREC == LBM_F64_DF) {
       const double* g = reinterpret_cast<const double*>(A);
       double g64[kQ];
@@ -867,11 +915,8 @@ __global__ void __launch_bounds__(kBlock, ctas(LBM_MIN_CTAS_ODD_X2)) k_aa_odd_x2
     const RiaCursor c0 = ria_locate(t, n0);
     const RiaCursor c1 = ria_locate(t, has1 ? n1 : n0);
     unsigned sl0[18], sl1[18];
-#pragma unroll
-    for (int j = 0; j < 18; ++j) {
-      sl0[j] = static_cast<unsigned>(ld_idx(t.run_slot + at(j, t.rpad, c0.r)) + c0.off);
-      sl1[j] = static_cast<unsigned>(ld_idx(t.run_slot + at(j, t.rpad, c1.r)) + c1.off);
-    }
+    run_slots<true>(t.run_slot, t.rpad, c0.r, c0.off, sl0);
+    run_slots<true>(t.run_slot, t.rpad, c1.r, c1.off, sl1);
 #pragma unroll
     for (int j = 0; j < 18; ++j) {
       s_sl[0][j][threadIdx.x] = static_cast<int>(sl0[j]);

@@ -464,7 +464,7 @@ int derive_et_tables(lbm_lattice* L);
 // reads f_i from slot (inv i, run_adj[i][r] + off) when the head pulls from a
 // fluid node, and from its own slot (i, head + off) through a bounce-back
 // marker; as a flat index of the [19][Npad] grid this is
-// run_slot[i][r] + off in both cases, with
+// run_slot(i, r) + off in both cases, with
 //   run_slot[i][r] = inv(i) Npad + run_adj[i][r]   (fluid source)
 //                  = i Npad + run_start[r]          (bounce-back).
 // The step also writes P_i to the slot f_inv(i) came from, so the same entries
@@ -495,23 +495,27 @@ int derive_run_slots(lbm_lattice* L) {
       L->run_slot_state = 0;
       return LBM_OK;
     }
-    L->run_slot.resize(size_t(18) * L->Rpad);
-    L->run_slot_osnt.resize(size_t(18) * L->Rpad);
+    L->run_slot.resize(run_slot_words(L->Rpad));
+    L->run_slot_osnt.resize(run_slot_words(L->Rpad));
+    // element (i, r): run-major r * kSlotStride + i - 1, or direction-major (i - 1) * Rpad + r
+    const size_t rs_r = LBM_SLOT_AOS ? kSlotStride : 1, rs_i = LBM_SLOT_AOS ? 1 : size_t(L->Rpad);
     parallel_for(L->Rpad, [&](int64_t rb, int64_t re) {
-      for (int i = 1; i <= 18; ++i) {
-        const int32_t* ra = L->run_adj.data() + size_t(i - 1) * L->Rpad;
-        int32_t* rs = L->run_slot.data() + size_t(i - 1) * L->Rpad;
-        int32_t* ro = L->run_slot_osnt.data() + size_t(i - 1) * L->Rpad;
-        for (int64_t r = rb; r < re; ++r) {
+      for (int64_t r = rb; r < re; ++r) {
+        for (int i = 1; i <= 18; ++i) {
+          const size_t k = size_t(r) * rs_r + size_t(i - 1) * rs_i;
           if (r >= L->R) {
-            rs[r] = ro[r] = 0;  // padding
+            L->run_slot[k] = L->run_slot_osnt[k] = 0;  // padding
           } else {
-            const int32_t a = ra[r];
+            const int32_t a = L->run_adj[size_t(i - 1) * L->Rpad + size_t(r)];
             const int64_t head = L->run_start[size_t(r)];
-            rs[r] = a >= 0 ? int32_t(int64_t(kInv[i]) * L->Npad + a) : int32_t(int64_t(i) * L->Npad + head);
-            ro[r] = a >= 0 ? int32_t(int64_t(i) * L->Npad + a) : int32_t(int64_t(kInv[i]) * L->Npad + head);
+            L->run_slot[k] = a >= 0 ? int32_t(int64_t(kInv[i]) * L->Npad + a) : int32_t(int64_t(i) * L->Npad + head);
+            L->run_slot_osnt[k] =
+                a >= 0 ? int32_t(int64_t(i) * L->Npad + a) : int32_t(int64_t(kInv[i]) * L->Npad + head);
           }
         }
+        if (LBM_SLOT_AOS)
+          for (int w = 18; w < kSlotStride; ++w)
+            L->run_slot[size_t(r) * kSlotStride + w] = L->run_slot_osnt[size_t(r) * kSlotStride + w] = 0;
       }
     });
   } catch (const std::bad_alloc&) {
