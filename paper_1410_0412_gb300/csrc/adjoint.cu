@@ -172,15 +172,42 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(DevTables t, KParams kp, Col
   using ::fma;
   const int n = blockIdx.x * kBlock + threadIdx.x;
   if (n >= N) return;
-  int m[18];
-  if (RIA) {
-    nbr_ria(t, ria_locate(t, n), m);
+  // F_n (the OS-NT pull gather of G) and mu = S^T lambda_{n+1}: slot (j, n) of
+  // the post-collision state is pulled by node m_{inv j} (fluid) or, through a
+  // marker, by this node's inv j slot (sign -1 for anti-bounce-back).
+  R d[kQ], mu[kQ];
+  if (RIA && t.run_slot) {
+    // Run slots (no pressure faces, the grid below 2^31 slots): the pull slots
+    // of F_n are run_slot_osnt(i, r) + off, and the slot of lambda_{n+1} that
+    // direction j reads is the AA odd table's run_slot(inv j, r) + off.
+    const RiaCursor cur = ria_locate<kKeepIdx<PREC>>(t, n);
+    unsigned sl[18];
+    run_slots<kKeepIdx<PREC>>(t.run_slot_osnt, t.rpad, cur.r, cur.off, sl);
+    d[0] = St<PREC>::ld(G + n, kp.inv_scale);
+#pragma unroll
+    for (int i = 1; i < kQ; ++i) d[i] = St<PREC>::ld(G + sl[i - 1], kp.inv_scale);
+    run_slots<kKeepIdx<PREC>>(t.run_slot, t.rpad, cur.r, cur.off, sl);
+    mu[0] = L::ld(lam_next + n);
+#pragma unroll
+    for (int j = 1; j < kQ; ++j) mu[j] = L::ld(lam_next + sl[inv(j) - 1]);
   } else {
-    nbr_adj(t, n, m);
+    int m[18];
+    if (RIA) {
+      nbr_ria(t, ria_locate(t, n), m);
+    } else {
+      nbr_adj(t, n, m);
+    }
+    gather<PREC, false>(G, t.npad, n, m, d, kp.inv_scale, cc.abb_in, cc.abb_out, t.pressure);
+    mu[0] = L::ld(lam_next + n);
+#pragma unroll
+    for (int j = 1; j < kQ; ++j) {
+      const int mp = m[inv(j) - 1];
+      const int dir = mp >= 0 ? j : inv(j);
+      const int node = mp >= 0 ? mp : n;
+      const R v = L::ld(lam_next + at(dir, t.npad, node));
+      mu[j] = mp < -1 ? -v : v;
+    }
   }
-  // forward quantities of F_n
-  R d[kQ];
-  gather<PREC, false>(G, t.npad, n, m, d, kp.inv_scale, cc.abb_in, cc.abb_out, t.pressure);
   R sa[10], da[10], drho, jx, jy, jz;
   moments<R, false>(d, sa, da, drho, jx, jy, jz);
   const R rho = c.rho_s + drho;
@@ -192,19 +219,6 @@ __global__ void __launch_bounds__(kBlock) k_adjoint(DevTables t, KParams kp, Col
     ux *= kd;
     uy *= kd;
     uz *= kd;
-  }
-  // mu = S^T lambda_{n+1}: slot (j, n) of the post-collision state is pulled by
-  // node m_{inv j} (fluid) or, through a marker, by this node's inv j slot
-  // (sign -1 for anti-bounce-back).
-  R mu[kQ];
-  mu[0] = L::ld(lam_next + n);
-#pragma unroll
-  for (int j = 1; j < kQ; ++j) {
-    const int mp = m[inv(j) - 1];
-    const int dir = mp >= 0 ? j : inv(j);
-    const int node = mp >= 0 ? mp : n;
-    const R v = L::ld(lam_next + at(dir, t.npad, node));
-    mu[j] = mp < -1 ? -v : v;
   }
   R P[10], D[10], M0, M1x, M1y, M1z, Mxx, Myy, Mzz, Mxy, Mxz, Myz;
   int64_t Pi[10], Di[10];
