@@ -51,8 +51,8 @@ COLL_DP_INSTR_UNIT_OMEGA = 31
 # kernel on the 10,896,954-node bed, from an ncu capture of the current kernel
 # version, with the profile that holds it; kernels not listed print null.
 TRAFFIC_PROFILED = {
-    ("aa_odd_ria_f64", 10896954): (1826285312 + 1595764480, "profiles/aa_pair_f64_packed_bed_256.md"),
-    ("aa_even_f64", 10896954): (1656452352 + 1594496256, "profiles/aa_pair_f64_packed_bed_256.md"),
+    ("aa_odd_ria_f64", 10896954): (1845508352 + 1595564544, "profiles/aa_pair_f64_packed_bed_256.md"),
+    ("aa_even_f64", 10896954): (1656480256 + 1594433024, "profiles/aa_pair_f64_packed_bed_256.md"),
 }
 
 WORKLOAD = dict(name="packed_bed_256_rsa_r12", X=256, Y=256, Z=256, radius=12.0, seed=1, rejections=20000,
