@@ -1097,26 +1097,27 @@ def main():
                 torch.cuda.empty_cache()
 
     # ---- the metric's comparisons: FP32 / FP16S against FP64, the adjoint's cost, energy -------------
+    def leg(fn, *a, **k):
+        # a comparison leg is reported, and never hides the headline if it fails
+        try:
+            return fn(*a, **k)
+        except Exception as e:
+            return {"error": f"{type(e).__name__}: {e}"}
+
     vs_f64 = adjoint = energy = adjoint_cfg = None
     if not args.no_variants:
-        vs_f64 = precision_leg(lbm, torch, lat, dev, stream)
-        adjoint = adjoint_leg(lbm, torch, solid, dev)
-        energy = energy_leg(lbm, torch, lat, dev, stream)
+        vs_f64 = leg(precision_leg, lbm, torch, lat, dev, stream)
+        adjoint = leg(adjoint_leg, lbm, torch, solid, dev)
+        energy = leg(energy_leg, lbm, torch, lat, dev, stream)
         # the differentiation configuration itself (128^3 box, T = 2000, K = 45): FP32 and FP64
         # backward/forward, and FD of the FP64 forward at 6 nodes with the noise floor
-        try:
-            adjoint_cfg = adjoint_box(lbm, torch, 128, 2000, 45, variants=(("f32", "f32", True), ("f64", "f64", True)),
-                                      fd=6, fd_h=(1e-4, 2e-4))
-        except Exception as e:  # reported, never hides the headline
-            adjoint_cfg = {"error": str(e)}
+        adjoint_cfg = leg(adjoint_box, lbm, torch, 128, 2000, 45, variants=(("f32", "f32", True), ("f64", "f64", True)),
+                          fd=6, fd_h=(1e-4, 2e-4))
 
     # ---- the production configuration: 768^3 foam, FP32 AA-R, 5000 steps (one GPU only) -------------
     production = None
     if world == 1 and not args.no_variants and not args.no_large and args.box is None:
-        try:
-            production = production_run(lbm, torch)
-        except Exception as e:  # reported, never hides the headline
-            production = {"error": str(e)}
+        production = leg(production_run, lbm, torch)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
