@@ -73,7 +73,7 @@ extern "C" {
 #define LBM_ERR_ALLOC 2        /* host allocation failed                           */
 #define LBM_ERR_CUDA 3         /* a CUDA runtime call or kernel launch failed      */
 #define LBM_ERR_TABLE 4        /* lattice tables violate an invariant             */
-#define LBM_ERR_UNSUPPORTED 5  /* valid request this build does not implement     */
+#define LBM_ERR_UNSUPPORTED 5  /* valid request the library does not implement    */
 #define LBM_ERR_NONFINITE 6    /* a reduction met NaN or Inf                       */
 
 /* ---- enumerations ----------------------------------------------------------- */
