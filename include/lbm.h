@@ -305,6 +305,18 @@ LBM_API int lbm_lattice_info(const lbm_lattice* lat, int64_t* N, int64_t* Npad, 
 LBM_API int lbm_export_tables(const lbm_lattice* lat, int32_t* node_xyz, int32_t* adj,
                       int32_t* run_start, int32_t* run_adj);
 
+/* The run slot tables that the RIA steps read (Sect. 4.1's run table with each
+ * entry resolved to a flat index of the [19][Npad] grid), for bit-exact
+ * comparison on the host.  With r a run, h its first node and a = run_adj[i][r]:
+ *  kind 0 (AA odd step):  slot(i, r) = inv(i) Npad + a  (a >= 0),  i Npad + h (wall)
+ *  kind 1 (OS-NT step):   slot(i, r) = i Npad + a       (a >= 0),  inv(i) Npad + h (wall)
+ * out: host int32 [R][18] (run-major, as the device holds them without the
+ * padding words), entry i - 1 of row r for i = 1..18.  *available is set to 1
+ * when the lattice has the tables, else 0 (pressure markers, or a grid of
+ * 2^31 slots or more: the steps then decode run_adj) and out is left alone.
+ * out may be NULL to ask for availability only. */
+LBM_API int lbm_export_run_slots(lbm_lattice* lat, int kind, int32_t* out, int* available);
+
 /* Adjacency entries of chosen nodes only (lattices too large to export in
  * full).  nodes: host int64 [count] in [0, N); out: host int32 [18][count]. */
 LBM_API int lbm_export_adjacency_rows(const lbm_lattice* lat, const int64_t* nodes, int64_t count, int32_t* out);

@@ -198,6 +198,19 @@ class Lattice:
         check(_lib.load().lbm_export_tables(self._h, p(xyz), p(adj), p(rs), p(ra)), "lbm_export_tables")
         return {"node_xyz": xyz, "adj": adj, "run_start": rs, "run_adj": ra}
 
+    def run_slots(self, kind):
+        """The RIA steps' run slot table [R, 18] (kind 0: AA odd step, 1: OS-NT step),
+        or None where the lattice has none (``lbm_export_run_slots``)."""
+        avail = ctypes.c_int()
+        lib = _lib.load()
+        check(lib.lbm_export_run_slots(self._h, int(kind), None, ctypes.byref(avail)), "lbm_export_run_slots")
+        if not avail.value:
+            return None
+        out = np.empty((self.R, 18), np.int32)
+        check(lib.lbm_export_run_slots(self._h, int(kind), out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(avail)),
+              "lbm_export_run_slots")
+        return out
+
     def validate(self):
         check(_lib.load().lbm_validate_tables(self._h), "lbm_validate_tables")
 

@@ -106,6 +106,7 @@ SIGNATURES = {
     "lbm_step_et": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _P, _I, _P],
     "lbm_run_et": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _I, _P, _I, _P],
     "lbm_export_et_runs": [_P, _PI64, _P, _P, _P],
+    "lbm_export_run_slots": [_P, _I, _P, ctypes.POINTER(ctypes.c_int)],
     "lbm_reduce_workspace_bytes": [_P, _PSZ],
     "lbm_macroscopic": [_P, _I, ctypes.POINTER(lbm_params), _P, _I, _P, _P, _P, _P, _P, _SZ, _P],
     "lbm_bandwidth_kernel": [_I, _P, _P, _I64, _I, _P],

@@ -641,6 +641,20 @@ int lbm_export_et_runs(lbm_lattice* L, int64_t* R, int32_t* run_start, int32_t* 
   return LBM_OK;
 }
 
+int lbm_export_run_slots(lbm_lattice* L, int kind, int32_t* out, int* available) {
+  if (int rc = check_lat(L)) return rc;
+  if (kind != 0 && kind != 1) return set_error(LBM_ERR_ARG, "kind must be 0 (AA odd) or 1 (OS-NT)");
+  if (!available) return set_error(LBM_ERR_ARG, "available is NULL");
+  if (int rc = derive_run_slots(L)) return rc;
+  *available = L->run_slot_state == 1 ? 1 : 0;
+  if (!out || !*available) return LBM_OK;
+  const TableVec& t = kind == 0 ? L->run_slot : L->run_slot_osnt;
+  for (int64_t r = 0; r < L->R; ++r)
+    for (int j = 0; j < 18; ++j)
+      out[r * 18 + j] = LBM_SLOT_AOS ? t[size_t(r) * kSlotStride + j] : t[size_t(j) * L->Rpad + size_t(r)];
+  return LBM_OK;
+}
+
 int lbm_reduce_workspace_bytes(const lbm_lattice* L, size_t* bytes) {
   if (int rc = check_lat(L)) return rc;
   if (!bytes) return set_error(LBM_ERR_ARG, "bytes is NULL");

@@ -139,3 +139,32 @@ def test_tables_do_not_depend_on_host_threads(enum, B, monkeypatch):
             assert np.array_equal(a, b)
         for a, b in zip(out[0][6], other[6]):
             assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("case", [((1, 0, 0), "lex", 1, 0), ((1, 1, 1), "lex", 4, 1), ((0, 0, 0), "hilbert", 1, 2)])
+def test_run_slot_tables_match_the_oracle_tables(case):
+    """The run slot tables the RIA steps read: with h the first node of run r
+    and a its adjacency entry for direction i (oracle tables), the AA odd step's
+    slot is inv(i) Npad + a for a fluid source and i Npad + h through a wall;
+    the OS-NT step's is i Npad + a or inv(i) Npad + h.  Lattices with pressure
+    faces have no such tables."""
+    from oracle.d3q19 import INV
+    periodic, enum, B, seed = case
+    solid = geometry.random_voxels(11, 9, 7, 0.25, 40 + seed)
+    lat = lbm.Lattice(solid, periodic=periodic, enum=enum, B=B)
+    ref = tables.Tables(solid, periodic=periodic, enum=enum, B=B)
+    heads = ref.run_start[:-1].astype(np.int64)
+    Np = lat.Npad
+    want_aa = np.empty((ref.R, 18), np.int64)
+    want_osnt = np.empty((ref.R, 18), np.int64)
+    for i in range(1, 19):
+        a = ref.adj[i - 1, heads].astype(np.int64)
+        fluid = a >= 0
+        want_aa[:, i - 1] = np.where(fluid, int(INV[i]) * Np + a, i * Np + heads)
+        want_osnt[:, i - 1] = np.where(fluid, i * Np + a, int(INV[i]) * Np + heads)
+    assert np.array_equal(lat.run_slots(0), want_aa)
+    assert np.array_equal(lat.run_slots(1), want_osnt)
+    xp = lbm.Lattice(solid, periodic=(0, 1, 1), x_pressure=True)
+    assert xp.run_slots(0) is None and xp.run_slots(1) is None
+    with pytest.raises(lbm.LbmError):
+        lat.run_slots(2)
