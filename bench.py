@@ -355,8 +355,9 @@ class Clocks:
                 "samples": len(rows), "reasons": reasons}
 
 
-def cpu_oracle_sample(solid, steps_pairs=1, zslab=16):
-    """Time the FP64 oracle (AA even + odd) on a z-slab of the same bed; GFLUP/s."""
+def cpu_oracle_sample(solid, steps_pairs=1, zslab=16, form="aa"):
+    """Time the FP64 oracle (AA even + odd, or two OS-NT steps, per pair) on a
+    z-slab of the same bed; GFLUP/s."""
     import torch
     from oracle import lbm as olbm, tables as otables
 
@@ -364,16 +365,20 @@ def cpu_oracle_sample(solid, steps_pairs=1, zslab=16):
     crop = np.ascontiguousarray(solid[:zslab])
     T = otables.Tables(crop, periodic=w["periodic"], enum="lex", B=1)
     p = olbm.Params(omega_plus=w["omega_plus"], magic=w["magic"], g=w["g"])
-    A = olbm.from_canonical(olbm.uniform_state(T.N, p), 1, T.adj, p)
+    A = olbm.from_canonical(olbm.uniform_state(T.N, p), 1 if form == "aa" else 0, T.adj, p)
     adj = torch.as_tensor(T.adj.astype(np.int64))
     t0 = time.perf_counter()
     for _ in range(steps_pairs):
-        A = olbm.aa_even(A, p)
-        A = olbm.aa_odd(A, adj, p)
+        if form == "aa":
+            A = olbm.aa_even(A, p)
+            A = olbm.aa_odd(A, adj, p)
+        else:
+            A = olbm.osnt_step(olbm.osnt_step(A, adj, p), adj, p)
     dt = time.perf_counter() - t0
+    what = "AA even+odd pair(s)" if form == "aa" else "pair(s) of OS-NT steps"
     return {"value": 2 * T.N * steps_pairs / dt / 1e9, "unit": "GFLUP/s", "cores": torch.get_num_threads(),
             "kind": "oracle", "seconds": dt,
-            "sample": f"{steps_pairs} AA even+odd pair(s) of the FP64 oracle on the z < {zslab} slab of the "
+            "sample": f"{steps_pairs} {what} of the FP64 oracle on the z < {zslab} slab of the "
                       f"256^3 bed ({T.N} fluid nodes)"}
 
 
@@ -1126,6 +1131,10 @@ def main():
             _t.set_num_threads(len(os.sched_getaffinity(0)))
             cpu = cpu_oracle_sample(solid, 3, zslab=64)
             cpu.pop("seconds", None)
+            # the same oracle's OS-NT step on the same slab
+            osnt = cpu_oracle_sample(solid, 2, zslab=64, form="osnt")
+            osnt.pop("seconds", None)
+            cpu["osnt"] = osnt
             # the same oracle on one host thread, one pair on a thin slab
             _t.set_num_threads(1)
             one = cpu_oracle_sample(solid, 1, zslab=8)
