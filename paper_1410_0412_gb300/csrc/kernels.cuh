@@ -194,9 +194,10 @@ template <int PREC> constexpr bool kKeepIdx = PREC != LBM_F64_DF;
 // The 18 slots of run r of a run slot table (derive_run_slots), each plus
 // off: sl[j] belongs to direction j + 1.  Run-major tables take four 16-byte
 // and one 8-byte load (the row is 80-byte aligned: the table starts on a
-// 256-byte boundary).
-// With a stash column (the AA odd step's [18][kBlock] shared array at this
-// thread's lane), each slot is also parked there as soon as it is formed.
+// 256-byte boundary).  With a stash column (the AA odd step's [18][kBlock]
+// shared array at this thread's lane), each slot is also parked there as soon
+// as it is formed; parking all 18 after the loads made the FP16 step spill
+// 152 instead of 64 bytes and lose the gain.
 template <bool KEEP>
 __device__ __forceinline__ void run_slots(const int32_t* tbl, uint32_t rpad, int r, int off, unsigned (&sl)[18],
                                           int* stash = nullptr) {
